@@ -1,0 +1,68 @@
+"""Physical constants and the named workloads.
+
+Units are SI throughout.  The paper prints no constants for the PIC cycle; the
+CODATA 2018 values are used.  Each workload names its mesh recipe (from
+``inputs``) and the run parameters.  The SP weight w_sp is a per-simulation
+choice in the paper (Sec. II.B: "determined independently for each
+simulation"); the values below were fixed once per workload from the
+charge-free emission current so that a full box holds about the target SP
+count, and are never recomputed at run time.
+"""
+from __future__ import annotations
+
+from . import inputs
+
+E_CHARGE = 1.602176634e-19      # C (exact)
+M_E = 9.1093837015e-31          # kg
+EPS0 = 8.8541878128e-12         # F/m
+Q_ELECTRON = -E_CHARGE
+Q_OVER_M = Q_ELECTRON / M_E     # C/kg
+
+PREC_FP64, PREC_FP32_IR = 0, 1
+FN_MURPHY_GOOD, FN_ELEMENTARY = 0, 1
+
+
+def params(dt=4e-15, E0=1e10, w_sp=1.0, pcg_rtol=1e-12, pcg_max_iter=20000,
+           fn_model=FN_MURPHY_GOOD, seed=0, capacity=20000, walk_max_steps=4096,
+           quant_bits=32, precision=PREC_FP64, ir_inner_rtol=1e-3):
+    """Run parameters shared by the CUDA library and the oracle."""
+    return dict(dt=float(dt), E0=float(E0), w_sp=float(w_sp), q=Q_ELECTRON,
+                q_over_m=Q_OVER_M, eps0=EPS0, e_charge=E_CHARGE,
+                pcg_rtol=float(pcg_rtol), pcg_max_iter=int(pcg_max_iter),
+                fn_model=int(fn_model), seed=int(seed), capacity=int(capacity),
+                walk_max_steps=int(walk_max_steps), quant_bits=int(quant_bits),
+                precision=int(precision), ir_inner_rtol=float(ir_inner_rtol))
+
+
+# name -> (mesh factory, parameter overrides, steps, target SP count)
+WORKLOADS = {
+    # parallel-plate gap: 100x100x200 nm, 20x20x40 cubes x 6 tets, 10 GV/m,
+    # work function 4.5 eV, 1e4 SPs, 100 steps of 4 fs, FP64
+    "plate_96k": dict(mesh=lambda: inputs.plate_mesh(),
+                      params=dict(dt=4e-15, E0=1e10, w_sp=0.55, capacity=20000,
+                                  precision=PREC_FP64, pcg_rtol=1e-12),
+                      steps=100, target_sp=10_000),
+    # Cu-like nanotip: r = 3 nm, h = 30 nm in a 60x60x230 nm box, ~1M tets,
+    # 10 GV/m, up to 1e6 SPs, FP32 push + FP64-refined PCG to 1e-6, 500 steps
+    "tip_1m": dict(mesh=lambda: inputs.tip_mesh(),
+                   params=dict(dt=4e-15, E0=1e10, w_sp=0.02, capacity=2_000_000,
+                               precision=PREC_FP32_IR, pcg_rtol=1e-6),
+                   steps=500, target_sp=1_000_000),
+    # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, ~8M tets,
+    # 8 GV/m, work function 4.5 +/- 0.1 eV per face, 1e7 SPs, 200 steps
+    "tip_8m": dict(mesh=lambda: inputs.tip_mesh(radius=5e-9, height=90e-9, width=120e-9,
+                                                 box_height=400e-9, h_fine=0.5e-9,
+                                                 lateral_growth=1.12, h_lat_max=3e-9,
+                                                 h_shank=1.0e-9, h_top_max=4e-9,
+                                                 vertical_growth=1.1,
+                                                 work_function_spread=0.1, seed=0),
+                   params=dict(dt=4e-15, E0=8e9, w_sp=0.2, capacity=20_000_000,
+                               precision=PREC_FP32_IR, pcg_rtol=1e-6),
+                   steps=200, target_sp=10_000_000),
+}
+
+
+def workload(name: str, **overrides):
+    w = WORKLOADS[name]
+    p = params(**{**w["params"], **overrides})
+    return w["mesh"](), p, w["steps"]

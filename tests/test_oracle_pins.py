@@ -1,0 +1,526 @@
+"""Pins of the CPU oracle to things other than itself: closed forms, textbook
+special cases, published known-answer values, physical definitions, brute
+force on tiny meshes and invariants.  No GPU needed."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy.integrate import quad
+from scipy.optimize import brentq
+
+from paper_1906_08125_gb300 import configs as K
+from paper_1906_08125_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# CODATA 2018 (exact SI values for e and h)
+E = 1.602176634e-19
+H = 6.62607015e-34
+HBAR = H / (2 * math.pi)
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def _oracle(O, mesh, **kw):
+    o = O.Oracle(mesh, K.params(**kw))
+    return o
+
+
+# --------------------------------------------------------------------------
+# random numbers
+# --------------------------------------------------------------------------
+def test_splitmix64_known_answers(oracle_mod):
+    want = [int(r[0], 16) for r in _golden_rows("splitmix64_seed0.txt")]
+    assert oracle_mod.splitmix64_sequence(0, 3) == want
+
+
+def test_uniform_statistics(oracle_mod):
+    n = 60000
+    u = np.array([oracle_mod.uniform(7, s, q, j, slot)
+                  for s, q, j, slot in zip(np.arange(n) % 13, np.arange(n) // 13,
+                                           np.arange(n) % 5, np.arange(n) % 3)])
+    assert np.all((u >= 0) & (u < 1))
+    hist, _ = np.histogram(u, bins=50, range=(0, 1))
+    chi2 = ((hist - n / 50) ** 2 / (n / 50)).sum()
+    assert chi2 < 100  # 49 dof; p ~ 1e-5
+    # neighbouring slots are uncorrelated
+    a = np.array([oracle_mod.uniform(1, 2, q, 0, 1) for q in range(20000)])
+    b = np.array([oracle_mod.uniform(1, 2, q, 0, 2) for q in range(20000)])
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.03
+
+
+# --------------------------------------------------------------------------
+# Fowler-Nordheim emission (Sec. II.B.3, J_e per quadrangle)
+# --------------------------------------------------------------------------
+def _v_wkb(f, phi=4.5):
+    """Schottky-Nordheim barrier function from its definition: the WKB
+    integral of sqrt(phi - F x - e/(16 pi eps0 x)) over the barrier, divided
+    by the same integral for the exact triangular barrier, (2/3) phi^1.5 / F."""
+    cS2 = E / (4 * math.pi * EPS0) * 1e9
+    q_img = cS2 / 4.0
+    F = f * phi ** 2 / cS2
+    M = lambda x: phi - F * x - q_img / x
+    xm = math.sqrt(q_img / F)
+    x1 = brentq(M, 1e-14, xm)
+    x2 = brentq(M, xm, 2 * phi / F)
+    integral, _ = quad(lambda x: math.sqrt(max(M(x), 0.0)), x1, x2, limit=400)
+    return integral / ((2.0 / 3.0) * phi ** 1.5 / F)
+
+
+def test_fn_constants_from_codata():
+    g = {r[0]: float(r[1]) for r in _golden_rows("fn_constants.txt")}
+    a = E ** 2 / (8 * math.pi * H)
+    b = (8 * math.pi / 3) * math.sqrt(2 * ME * E) / H * 1e-9
+    cS2 = E / (4 * math.pi * EPS0) * 1e9
+    assert a == pytest.approx(g["a"], rel=2e-6)
+    assert b == pytest.approx(g["b"], rel=2e-6)
+    assert cS2 == pytest.approx(g["cS2"], rel=2e-6)
+
+
+@pytest.mark.parametrize("F_V_nm", [3.0, 5.0, 8.0, 12.0])
+def test_fn_murphy_good_against_wkb_definition(oracle_mod, F_V_nm):
+    phi = 4.5
+    cS2 = E / (4 * math.pi * EPS0) * 1e9
+    f = cS2 * F_V_nm / phi ** 2
+    v = _v_wkb(f, phi)
+    dv = (_v_wkb(f * 1.001, phi) - _v_wkb(f * 0.999, phi)) / (0.002 * f)
+    t = v - (4.0 / 3.0) * f * dv          # t(f) = v(f) - (4/3) f dv/df
+    a = E ** 2 / (8 * math.pi * H)
+    b = (8 * math.pi / 3) * math.sqrt(2 * ME * E) / H * 1e-9
+    J = a * F_V_nm ** 2 / (phi * t * t) * math.exp(-v * b * phi ** 1.5 / F_V_nm) * 1e18
+    Jo = oracle_mod.fn_current(F_V_nm * 1e9, phi, oracle_mod.FN_MURPHY_GOOD)
+    # Forbes' approximation of v is good to ~0.33 % (relative); that error is
+    # amplified by the exponent b phi^1.5 / F, so bound the log of the ratio
+    tol = 0.005 * v * b * phi ** 1.5 / F_V_nm + 0.01
+    assert abs(math.log(Jo / J)) < tol
+
+
+def test_fn_elementary_and_barrier_top(oracle_mod):
+    phi = 4.5
+    a = E ** 2 / (8 * math.pi * H)
+    b = (8 * math.pi / 3) * math.sqrt(2 * ME * E) / H * 1e-9
+    # FN plot: ln(J/F^2) is linear in 1/F with slope -b phi^1.5 (elementary)
+    Fs = np.array([2.0, 4.0, 8.0])
+    lj = [math.log(oracle_mod.fn_current(F * 1e9, phi, oracle_mod.FN_ELEMENTARY) / (F * F))
+          for F in Fs]
+    slope = (lj[2] - lj[0]) / (1 / Fs[2] - 1 / Fs[0])
+    assert slope == pytest.approx(-b * phi ** 1.5, rel=1e-5)
+    assert math.exp(lj[0] + b * phi ** 1.5 / Fs[0]) * 1e-18 == pytest.approx(a / phi, rel=1e-5)
+    # beyond the barrier top (f >= 1): v = 0, t = 10/9, J = a F^2 / (phi t^2)
+    cS2 = E / (4 * math.pi * EPS0) * 1e9
+    Ftop = phi ** 2 / cS2
+    for F in (Ftop * 1.5, Ftop * 7.0):
+        Jo = oracle_mod.fn_current(F * 1e9, phi, oracle_mod.FN_MURPHY_GOOD)
+        assert Jo == pytest.approx(a * F * F / (phi * (10 / 9) ** 2) * 1e18, rel=1e-5)
+    assert oracle_mod.fn_current(0.0, phi) == 0.0
+    assert oracle_mod.fn_current(-1e9, phi) == 0.0
+
+
+# --------------------------------------------------------------------------
+# P1 geometry and stiffness (App. B)
+# --------------------------------------------------------------------------
+def test_reference_tet_stiffness(oracle_mod):
+    Kref = np.array([[float(x) for x in r] for r in _golden_rows("reference_tet_stiffness.txt")]) / 6
+    x = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    assert np.allclose(oracle_mod.element_stiffness(x), Kref, atol=1e-15)
+    # invariance under rotation + translation, linear scaling with size
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    y = (x * 2.5) @ Q.T + np.array([1.0, -2.0, 0.5])
+    assert np.allclose(oracle_mod.element_stiffness(y), 2.5 * Kref, atol=1e-13)
+
+
+def test_geometry_against_numpy_inverse(oracle_mod, tip_small):
+    o = _oracle(oracle_mod, tip_small)
+    jinv, x0, vol = o.geometry()
+    P = tip_small.xyz[tip_small.tet]
+    J = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    Jn = np.linalg.inv(J)
+    scale = np.abs(Jn).max(axis=(1, 2))
+    assert np.all(np.abs(jinv.reshape(-1, 3, 3) - Jn).max(axis=(1, 2)) <= 1e-12 * scale)
+    assert np.allclose(vol, np.linalg.det(J) / 6, rtol=1e-12)
+    assert np.all(vol > 0)
+    assert np.array_equal(x0, P[:, 0])
+    # barycentrics reproduce the vertices and sum to one
+    for t in (0, tip_small.n_tets // 2, tip_small.n_tets - 1):
+        for i in range(4):
+            lam = o.barycentric(t, P[t, i])
+            e = np.zeros(4)
+            e[i] = 1
+            assert np.allclose(lam, e, atol=1e-12)
+        lam = o.barycentric(t, P[t].mean(0) + 1e-10)
+        assert lam.sum() == pytest.approx(1.0, abs=1e-14)
+
+
+def _independent_system(mesh, E0):
+    """Stiffness and Neumann load assembled from the definitions with numpy:
+    gradients from np.linalg.inv, duplicates summed by scipy.sparse."""
+    P = mesh.xyz[mesh.tet]
+    J = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    Ji = np.linalg.inv(J)
+    g = np.concatenate([-Ji.sum(axis=1, keepdims=True), Ji], axis=1)  # (T,4,3)
+    vol = np.linalg.det(J) / 6
+    Ke = vol[:, None, None] * np.einsum("tik,tjk->tij", g, g)
+    rows = np.repeat(mesh.tet, 4, axis=1).ravel()
+    cols = np.tile(mesh.tet, (1, 4)).ravel()
+    N = mesh.n_nodes
+    Mfull = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(N, N)).tocsr()
+    free = np.nonzero(mesh.dirichlet == 0)[0]
+    M = Mfull[free][:, free]
+    # top faces
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    tt, kk = np.nonzero(mesh.nbr == -1)
+    fnodes = mesh.tet[tt[:, None], loc[kk]]
+    A = 0.5 * np.linalg.norm(np.cross(mesh.xyz[fnodes[:, 1]] - mesh.xyz[fnodes[:, 0]],
+                                      mesh.xyz[fnodes[:, 2]] - mesh.xyz[fnodes[:, 0]]), axis=1)
+    fNfull = np.bincount(fnodes.ravel(), weights=np.repeat(E0 * A / 3, 3), minlength=N)
+    return M, fNfull[free], free, Mfull, A.sum()
+
+
+def test_matrix_against_independent_assembly(oracle_mod, tip_small):
+    o = _oracle(oracle_mod, tip_small, E0=1e10)
+    dof, rowptr, col, val, fN = o.matrix()
+    M, fN_ind, free, Mfull, top_area = _independent_system(tip_small, 1e10)
+    Mo = sp.csr_matrix((val, col, rowptr), shape=(len(free), len(free)))
+    assert np.array_equal(np.nonzero(dof >= 0)[0], free)
+    diff = abs(Mo - M).max()
+    assert diff <= 1e-12 * abs(M).max()
+    assert abs(Mo - Mo.T).max() == 0.0
+    assert np.allclose(fN, fN_ind, rtol=1e-12, atol=0)
+    assert fN.sum() == pytest.approx(1e10 * top_area, rel=1e-12)
+    # the full (undirichleted) P1 stiffness annihilates constants
+    assert abs(Mfull @ np.ones(tip_small.n_nodes)).max() < 1e-12 * abs(Mfull).max()
+
+
+def test_matrix_positive_definite(oracle_mod, plate_small):
+    o = _oracle(oracle_mod, plate_small)
+    dof, rowptr, col, val, fN = o.matrix()
+    n = len(rowptr) - 1
+    Md = sp.csr_matrix((val, col, rowptr), shape=(n, n)).toarray()
+    w = np.linalg.eigvalsh(Md)
+    assert w.min() > 0
+
+
+# --------------------------------------------------------------------------
+# Poisson solve (eqs. poisson, poisson_bc, poisson_mat)
+# --------------------------------------------------------------------------
+def test_p1_exact_for_parallel_plate(oracle_mod):
+    mesh = inputs.plate_mesh()   # 96k tets, the plate workload
+    o = _oracle(oracle_mod, mesh, E0=1e10, pcg_rtol=1e-13)
+    o.init_potential()
+    phi = o.potential()
+    exact = 1e10 * mesh.xyz[:, 2]
+    assert np.abs(phi - exact).max() <= 1e-10 * exact.max()
+    Ef = o.field()
+    assert np.abs(Ef[:, 2] + 1e10).max() <= 1e-8 * 1e10
+    assert np.abs(Ef[:, :2]).max() <= 1e-8 * 1e10
+
+
+def test_pcg_against_direct_solve(oracle_mod, tip_small):
+    S = 32
+    o = _oracle(oracle_mod, tip_small, E0=5e9, w_sp=50.0, pcg_rtol=1e-13, capacity=5000)
+    r, v, cell, pid = inputs.random_particles(tip_small, 3000, seed=5)
+    o.set_particles(r, v, cell, pid)
+    W = o.deposit()
+    o.poisson_solve()
+    phi = o.potential()
+    M, fN, free, _, _ = _independent_system(tip_small, 5e9)
+    coef = (K.Q_ELECTRON * 50.0) / K.EPS0
+    f = coef * W[free].astype(np.float64) * 2.0 ** -S + fN
+    x = spla.spsolve(M.tocsc(), f)
+    assert np.abs(phi[free] - x).max() <= 1e-9 * np.abs(x).max()
+    assert np.all(phi[tip_small.dirichlet == 1] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# walk relocation (Sec. II.B.2): brute force on tiny meshes
+# --------------------------------------------------------------------------
+def _bary_np(mesh, t, r):
+    P = mesh.xyz[mesh.tet[t]]
+    J = np.stack([P[..., 1, :] - P[..., 0, :], P[..., 2, :] - P[..., 0, :],
+                  P[..., 3, :] - P[..., 0, :]], axis=-1)
+    l123 = np.linalg.solve(J, (r - P[..., 0, :])[..., None])[..., 0]
+    return np.concatenate([1 - l123.sum(-1, keepdims=True), l123], axis=-1)
+
+
+def test_walk_against_brute_force(oracle_mod, plate_small):
+    mesh = plate_small
+    o = _oracle(oracle_mod, mesh)
+    rng = np.random.default_rng(11)
+    n = 400
+    lo, hi = mesh.box_lo, mesh.box_hi
+    pts = lo + rng.uniform(0.001, 0.999, size=(n, 3)) * (hi - lo)
+    start = rng.integers(0, mesh.n_tets, n).astype(np.int32)
+    r, cell, fate, wl = o.locate(pts, start)
+    assert np.all(fate == oracle_mod.FATE_ALIVE)
+    assert np.array_equal(r, pts)
+    lam = _bary_np(mesh, cell, pts)
+    assert lam.min() >= -1e-12
+    # brute force: every tet containing the point; the walk found one of them
+    all_lam = _bary_np(mesh, np.arange(mesh.n_tets)[None, :].repeat(n, 0), pts[:, None, :])
+    inside = (all_lam >= -1e-12).all(-1)
+    assert np.all(inside[np.arange(n), cell])
+    # points beyond the top are collected, below the cathode absorbed
+    up = pts.copy()
+    up[:, 2] = hi[2] + 1e-9
+    _, _, fate_up, _ = o.locate(up[:50], start[:50])
+    assert np.all(fate_up == oracle_mod.FATE_COLLECTED)
+    down = pts.copy()
+    down[:, 2] = lo[2] - 1e-9
+    _, _, fate_dn, _ = o.locate(down[:50], start[:50])
+    assert np.all(fate_dn == oracle_mod.FATE_ABSORBED)
+
+
+def test_walk_periodic_wrap(oracle_mod, plate_small):
+    mesh = plate_small
+    o = _oracle(oracle_mod, mesh)
+    L = mesh.box_hi - mesh.box_lo
+    rng = np.random.default_rng(2)
+    n = 100
+    pts = mesh.box_lo + rng.uniform(0.1, 0.9, size=(n, 3)) * L
+    shifted = pts.copy()
+    shifted[:, 0] += L[0]          # one box width beyond x_max
+    shifted[: n // 2, 1] -= L[1]   # and half of them below y_min too
+    start = rng.integers(0, mesh.n_tets, n).astype(np.int32)
+    r, cell, fate, _ = o.locate(shifted, start)
+    assert np.all(fate == oracle_mod.FATE_ALIVE)
+    assert np.allclose(r, pts, rtol=0, atol=1e-20 + 1e-15 * L.max())
+    assert (_bary_np(mesh, cell, r) >= -1e-12).all()
+
+
+def test_walk_into_metal_is_absorbed(oracle_mod, tip_small):
+    mesh = tip_small
+    o = _oracle(oracle_mod, mesh)
+    # points on the tip axis, inside the metal, reached from just above the apex
+    zc = mesh.xyz[mesh.tet].mean(1)
+    apex = 12e-9
+    above = np.nonzero((np.abs(zc[:, 0]) < 1.5e-9) & (np.abs(zc[:, 1]) < 1.5e-9) &
+                       (zc[:, 2] > apex) & (zc[:, 2] < apex + 3e-9))[0]
+    assert above.size > 0
+    pts = np.array([[0.2e-9, -0.1e-9, z] for z in np.linspace(2e-9, apex - 1e-9, 20)])
+    start = np.full(20, above[0], np.int32)
+    _, _, fate, _ = o.locate(pts, start)
+    assert np.all(fate == oracle_mod.FATE_ABSORBED)
+
+
+# --------------------------------------------------------------------------
+# deposit (eq. poisson_rhs): exact charge conservation
+# --------------------------------------------------------------------------
+def test_deposit_conservation(oracle_mod, tip_small):
+    S = 32
+    o = _oracle(oracle_mod, tip_small, capacity=10000)
+    r, v, cell, pid = inputs.random_particles(tip_small, 7777, seed=4)
+    o.set_particles(r, v, cell, pid)
+    W = o.deposit()
+    assert int(W.sum()) == 7777 * 2 ** S
+    # an SP on vertex i of its tet deposits 2^S to node i only; one at the
+    # centroid deposits 2^(S-2) to each node
+    t = 17
+    P = tip_small.xyz[tip_small.tet[t]]
+    for i in range(4):
+        o.set_particles(P[i][None], np.zeros((1, 3)), np.array([t]), np.array([0]))
+        W = o.deposit()
+        assert W[tip_small.tet[t, i]] == 2 ** S and np.count_nonzero(W) == 1
+    o.set_particles(P.mean(0)[None] * 1.0, np.zeros((1, 3)), np.array([t]), np.array([0]))
+    W = o.deposit()
+    lam = o.barycentric(t, P.mean(0))
+    assert np.all(np.abs(W[tip_small.tet[t]] - 2 ** (S - 2)) <= 1 + 2 ** S * np.abs(lam - 0.25).max())
+    assert int(W.sum()) == 2 ** S
+
+
+# --------------------------------------------------------------------------
+# push (eqs. newton, leapfrog1-3): closed-form motion in a uniform field
+# --------------------------------------------------------------------------
+def test_uniform_field_motion_closed_form(oracle_mod, plate_small):
+    mesh = plate_small
+    dt, E0 = 4e-15, 2e8
+    o = _oracle(oracle_mod, mesh, dt=dt, E0=E0, w_sp=1e-30, pcg_rtol=1e-13, capacity=10)
+    o.set_work_function(np.full(mesh.n_faces, 1000.0))   # no emission
+    o.init_potential()
+    L = mesh.box_hi - mesh.box_lo
+    r0 = np.array([[15e-9, 15e-9, 5e-9]])
+    v0 = np.array([[2.0e6, -1.5e6, 0.0]])   # crosses the periodic sides
+    _, c0, _, _ = o.locate(r0, np.array([0], np.int32))
+    o.set_particles(r0, v0, c0, np.array([0]))
+    a = K.Q_OVER_M * np.array([0.0, 0.0, -E0])
+    k = 6
+    st = o.step(k)
+    r, v, cell, pid = o.particles()
+    expect = r0[0] + k * dt * v0[0] + a * dt * dt * k * (k + 1) / 2
+    wrapped = expect.copy()
+    wrapped[:2] = mesh.box_lo[:2] + np.mod(expect[:2] - mesh.box_lo[:2], L[:2])
+    assert sum(s.wrapped for s in st) >= 1
+    assert np.allclose(r[0], wrapped, rtol=0, atol=1e-9 * np.abs(expect).max())
+    assert np.allclose(v[0], v0[0] + k * a * dt, rtol=1e-9)
+    # collection time of a cathode-born SP at rest: z_k = z0 + a dt^2 k(k+1)/2
+    E0 = 1e9
+    a = K.Q_OVER_M * np.array([0.0, 0.0, -E0])
+    o2 = _oracle(oracle_mod, mesh, dt=dt, E0=E0, w_sp=1e-30, pcg_rtol=1e-13, capacity=10)
+    o2.set_work_function(np.full(mesh.n_faces, 1000.0))
+    o2.init_potential()
+    z0 = 0.5e-9
+    p0 = np.array([[12e-9, 13e-9, z0]])
+    _, c, _, _ = o2.locate(p0, np.array([0], np.int32))
+    o2.set_particles(p0, np.zeros((1, 3)), c, np.array([0]))
+    az = a[2]
+    kk = next(k for k in range(1, 1000) if z0 + az * dt * dt * k * (k + 1) / 2 > L[2])
+    stats = o2.step(kk + 1)
+    got = next(i + 1 for i, s in enumerate(stats) if s.collected)
+    assert got == kk
+
+
+# --------------------------------------------------------------------------
+# injection (eqs. nsp, rnd_nsp, sp_velocity, sp_displacement; App. E)
+# --------------------------------------------------------------------------
+def test_injection_statistics(oracle_mod, plate_small):
+    mesh = plate_small
+    dt, E0 = 4e-15, 1e10
+    J = oracle_mod.fn_current(E0, 4.5)
+    Aq = (5e-9 * 5e-9 / 2) / 3
+    target = 1.3
+    w_sp = J * Aq * dt / (K.E_CHARGE * target)
+    o = _oracle(oracle_mod, mesh, dt=dt, E0=E0, w_sp=w_sp, pcg_rtol=1e-13, capacity=200000)
+    o.init_potential()
+    F, Jq, nsp = o.quad_emission()
+    assert np.allclose(nsp, target, rtol=1e-9)
+    nq = 3 * mesh.n_faces
+    counts = []
+    pts, vz, zz, quads = [], [], [], []
+    for step in range(40):
+        o.set_particles(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.int32), np.zeros(0, np.int64))
+        n = o.inject(step)
+        r, v, cell, pid = o.particles()
+        q = (pid >> 18) & ((1 << 24) - 1)
+        counts.append(np.bincount(q, minlength=nq))
+        pts.append(r)
+        vz.append(v[:, 2])
+        quads.append(q)
+        assert np.all((pid >> 42) == step)
+        assert np.array_equal(cell, mesh.face_tet[q // 3])
+    counts = np.concatenate(counts)
+    m = counts.mean()
+    assert set(np.unique(counts)) <= {1, 2}
+    sigma = math.sqrt(0.3 * 0.7 / counts.size)
+    assert abs(m - target) < 4 * sigma
+    assert counts.var() == pytest.approx(0.3 * 0.7, rel=0.1)
+    r = np.concatenate(pts)
+    vz = np.concatenate(vz)
+    q = np.concatenate(quads)
+    # v0 = (q/m) E dt (1/2 + R): R uniform on [0, 1)
+    R = vz / (K.Q_OVER_M * (-E0) * dt) - 0.5
+    assert R.min() >= 0 and R.max() < 1
+    assert abs(R.mean() - 0.5) < 4 * math.sqrt(1 / 12 / R.size)
+    # displacement dr = v0 dt R, from the face at z = 0
+    assert np.allclose(r[:, 2], vz * dt * R, rtol=1e-9, atol=0)
+    # the point lies in its quadrangle and is uniform there: triangle
+    # barycentrics with lambda_V >= the other two; P(lambda_V >= 0.6) = 0.48
+    f = q // 3
+    vtx = q % 3
+    fn = mesh.face_nodes[f]
+    A_ = mesh.xyz[fn[np.arange(len(f)), vtx]][:, :2]
+    B_ = mesh.xyz[fn[np.arange(len(f)), (vtx + 1) % 3]][:, :2]
+    C_ = mesh.xyz[fn[np.arange(len(f)), (vtx + 2) % 3]][:, :2]
+    M2 = np.stack([B_ - A_, C_ - A_], axis=2)
+    lbc = np.linalg.solve(M2, (r[:, :2] - A_)[..., None])[..., 0]
+    lv = 1 - lbc.sum(1)
+    assert np.all(lv >= lbc[:, 0] - 1e-9) and np.all(lv >= lbc[:, 1] - 1e-9)
+    frac = np.mean(lv >= 0.6)
+    assert abs(frac - 0.48) < 4 * math.sqrt(0.48 * 0.52 / len(lv))
+    half = np.mean(lbc[:, 0] >= lbc[:, 1])
+    assert abs(half - 0.5) < 4 * math.sqrt(0.25 / len(lv))
+
+
+# --------------------------------------------------------------------------
+# the whole cycle: steady planar space-charge-limited emission
+# --------------------------------------------------------------------------
+def test_planar_diode_steady_state(oracle_mod):
+    """1D planar diode with emitted current J = J_FN(F), Phi(0) = 0,
+    Phi'(0) = F, Phi'(d) = E0: integrating Phi'' = (J/eps0) sqrt(m/(2 e Phi))
+    gives d = (E0 - F)^2 (E0 + 2F) / (12 k^2), k = (J/eps0) sqrt(m/(2e)).
+    The PIC steady-state current must match within the discretisation error
+    (the paper reports 1.9 % RMS against its semianalytical curve, Sec. IV.A.1)."""
+    d, E0, dt, w_sp = 200e-9, 1e10, 1e-15, 0.09
+    mesh = inputs.plate_mesh(nx=4, ny=4, nz=80)
+    o = _oracle(oracle_mod, mesh, dt=dt, E0=E0, w_sp=w_sp, pcg_rtol=1e-10, capacity=100000)
+    o.init_potential()
+    A = 100e-9 * 100e-9
+    Js = []
+    for s in range(150):
+        st = o.step(1)[0]
+        if s >= 75:
+            Js.append(st.injected * K.E_CHARGE * w_sp / (A * dt))
+
+    def gap(F):
+        J = oracle_mod.fn_current(F, 4.5)
+        k = (J / K.EPS0) * math.sqrt(K.M_E / (2 * K.E_CHARGE))
+        return (E0 - F) ** 2 * (E0 + 2 * F) / (12 * k * k) - d
+
+    F = brentq(gap, 1e9, E0 * (1 - 1e-6))
+    J_sa = oracle_mod.fn_current(F, 4.5)
+    assert np.mean(Js) == pytest.approx(J_sa, rel=0.08)
+
+
+# --------------------------------------------------------------------------
+# failure paths and resume
+# --------------------------------------------------------------------------
+def test_error_paths(oracle_mod, plate_small):
+    O = oracle_mod
+    mesh = plate_small
+    o = _oracle(O, mesh, capacity=10)
+    o.init_potential()
+    with pytest.raises(O.OracleError, match="-4"):
+        o.inject(0)
+    o = _oracle(O, mesh, walk_max_steps=1)
+    far = np.array([[25e-9, 25e-9, 50e-9]])
+    with pytest.raises(O.OracleError, match="-5"):
+        o.locate(far, np.array([0], np.int32))
+    o = _oracle(O, mesh, pcg_max_iter=1, pcg_rtol=1e-14)
+    with pytest.raises(O.OracleError, match="-6"):
+        o.init_potential()
+    bad = inputs.plate_mesh(nx=3, ny=3, nz=3)
+    bad.tet[5, [1, 2]] = bad.tet[5, [2, 1]]
+    with pytest.raises(O.OracleError, match="-3"):
+        O.Oracle(bad, K.params())
+    bad = inputs.plate_mesh(nx=3, ny=3, nz=3)
+    k = int(np.nonzero(bad.nbr[7] >= 0)[0][0])
+    bad.nbr[7, k] = (bad.nbr[7, k] + 40) % bad.n_tets   # neighbour that does not point back
+    with pytest.raises(O.OracleError, match="-3"):
+        O.Oracle(bad, K.params())
+    bad = inputs.plate_mesh(nx=3, ny=3, nz=3)
+    bad.work_function[0] = np.nan
+    with pytest.raises(O.OracleError, match="-1"):
+        O.Oracle(bad, K.params())
+
+
+def test_resume_is_bit_identical(oracle_mod, plate_small):
+    kw = dict(w_sp=0.02, capacity=50000, pcg_rtol=1e-12)
+    a = _oracle(oracle_mod, plate_small, **kw)
+    a.init_potential()
+    a.step(8)
+    b = _oracle(oracle_mod, plate_small, **kw)
+    b.init_potential()
+    b.step(4)
+    phi, parts, k = b.potential(), b.particles(), b.step_index
+    c = _oracle(oracle_mod, plate_small, **kw)
+    c.set_potential(phi)
+    c.set_particles(*parts)
+    c.step_index = k
+    c.step(4)
+    for x, y in zip(a.particles(), c.particles()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.potential(), c.potential())
