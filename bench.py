@@ -1,0 +1,407 @@
+"""Benchmark of the GB300 FEM-PIC cycle: PIC cycles/s and particle pushes/s
+on the 1M-tetrahedron nanotip workload, with the HBM-roofline fraction of the
+dominant kernel, the plain FP64 form beside it, an end-to-end figure through
+the C ABI with host buffers, and the CPU oracle as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full PIC cycle (injection, push, walk, deposit, Poisson solve).
+Every timed step is preceded by an L2 flush (a 256 MB write, outside the
+step's events) and bracketed by CUDA events on the library's stream.
+Several GPUs run independent replicas (the cycle does not shard; the
+ensemble of runs does), each seeded by its rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PIC cycles/s"
+WORKLOAD = "tip_1m"
+STAT_DTYPE = np.dtype([("injected", "<i8"), ("collected", "<i8"), ("absorbed", "<i8"),
+                       ("wrapped", "<i8"), ("crossings", "<i8"), ("alive", "<i8"),
+                       ("max_walk", "<i4"), ("pcg_iters", "<i4"), ("pcg_relres", "<f8"),
+                       ("collected_charge", "<f8"), ("pcg_outer", "<i4"), ("reserved", "<i4")])
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=12)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1906_08125_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_sha():
+        return None
+    if e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.lines = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                       "-lms", "200", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bench_population(mesh, n, seed):
+    from paper_1906_08125_gb300 import inputs
+    return inputs.random_particles(mesh, n, seed=seed, v_scale=3e6, v_up=1.5e7)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (the byte model is stated in the design doc)
+# ---------------------------------------------------------------------------
+def bytes_step_fused(st_prev_alive, st, s, rec):
+    n_old = st_prev_alive
+    n_new = int(st["injected"])
+    alive = int(st["alive"])
+    X = int(st["crossings"])
+    state = 6 * s + 12
+    return (n_old * state + alive * state + (n_old + n_new + X) * rec + n_old * 4 * s
+            + alive * 16 + n_new * 64)
+
+
+def bytes_pcg(st, info, fp64):
+    n, nnz = info["n_free"], info["nnz"]
+    it, outer = int(st["pcg_iters"]), int(st["pcg_outer"])
+    if fp64:
+        return it * (12 * nnz + 96 * n) + (12 * nnz + 76 * n) + 20 * n
+    return it * (8 * nnz + 48 * n) + (outer + 1) * (12 * nnz + 24 * n) + outer * 76 * n \
+        + 28 * n + 20 * n
+
+
+def bytes_field(info, s, rec):
+    return info["n_tets"] * (rec + 16 + 4 * s) + 8 * info["n_nodes"]
+
+
+def bytes_inject_count(info, s):
+    return 3 * info["n_faces"] * (4 * s + 3 * 8 + 8 + 8 + 4 + 4)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True):
+    import torch
+
+    from paper_1906_08125_gb300 import configs as K
+    from paper_1906_08125_gb300 import picfem
+
+    prec = K.PREC_FP32_IR if precision == "fp32_ir" else K.PREC_FP64
+    mesh, p, _ = K.workload(args.workload, precision=prec, seed=rank)
+    if prec == K.PREC_FP64:
+        p = dict(p, pcg_rtol=1e-6)
+    target = K.WORKLOADS[args.workload]["target_sp"]
+    stream = torch.cuda.current_stream()
+    ctx = picfem.Context(p, stream=stream).mesh_load(mesh)
+    info = ctx.info()
+    ctx.init_potential()
+    r, v, cell, pid = bench_population(mesh, target, seed=1000 + rank)
+    ctx.set_particles(r, v, cell, pid)
+    dev = torch.cuda.current_device()
+    for _ in range(warmup):
+        ctx.step(1, stats=False)
+    ctx.sync()
+    n0 = ctx.num_particles()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    dstats = torch.zeros(timed_steps * STAT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(timed_steps)]
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.6)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    L = ctx.L
+    launches0 = ctx.launch_count()
+    if with_profile:
+        ctx.profile(True)
+    base = dstats.data_ptr()
+    for k in range(timed_steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        rc = L.pic_step(ctx.h, 1, picfem.C.cast(picfem.C.c_void_p(base + k * STAT_DTYPE.itemsize),
+                                                picfem.C.POINTER(picfem.StepStats)))
+        ev[k][1].record(stream)
+        if rc != 0:
+            ctx._check(rc)
+    torch.cuda.synchronize()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read() if with_profile else {}
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = np.frombuffer(dstats.cpu().numpy().tobytes(), dtype=STAT_DTYPE)
+    prev = np.concatenate([[n0], st["alive"][:-1]])
+    pushes = int((prev + st["injected"]).sum())
+    res = dict(ctx=ctx, mesh=mesh, params=p, info=info, step_ms=step_ms, total_ms=total_ms,
+               stats=st, prev_alive=prev, pushes=pushes, launches=launches, prof=prof,
+               clocks=clk, n0=n0)
+    return res
+
+
+def roofline(res, fp64):
+    info, st, prof = res["info"], res["stats"], res["prof"]
+    s = 8 if fp64 else 4
+    rec = 128 if fp64 else 64
+    alg = {
+        "step_fused": sum(bytes_step_fused(int(pa), row, s, rec)
+                          for pa, row in zip(res["prev_alive"], st)),
+        "pcg": sum(bytes_pcg(row, info, fp64) for row in st),
+        "field": len(st) * bytes_field(info, s, rec),
+        "inject_count": len(st) * bytes_inject_count(info, s),
+    }
+    peak, kind = peaks()
+    kernels = {}
+    for name, (n, ms) in prof.items():
+        kernels[name] = {"launches": int(n), "ms": ms}
+    total = sum(k["ms"] for k in kernels.values()) or 1.0
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    out_k = {}
+    for name, k in kernels.items():
+        gbs = alg[name] / (k["ms"] * 1e-3) / 1e9 if name in alg and k["ms"] > 0 else None
+        out_k[name] = {"launches": k["launches"], "ms_total": round(k["ms"], 4),
+                       "share": round(k["ms"] / total, 4),
+                       "alg_bytes_per_launch": int(alg[name] / k["launches"]) if name in alg else None,
+                       "achieved_gbs": round(gbs, 1) if gbs else None}
+    a = out_k[dom]["achieved_gbs"]
+    traffic = ncu_traffic(dom, WORKLOAD)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": peak, "unit": "GB/s",
+            "frac": round(a / peak, 4) if a else None, "traffic": traffic,
+            "peak_source": kind}
+    return roof, out_k
+
+
+def run_e2e(res, steps):
+    """The same metric through the C ABI with host buffers: per step the
+    per-face work function goes host->device, one cycle runs, and the step
+    statistics and the node potential come back device->host."""
+    import torch
+    from paper_1906_08125_gb300 import picfem
+    ctx, mesh = res["ctx"], res["mesh"]
+    wf = torch.from_numpy(np.ascontiguousarray(mesh.work_function, np.float64)).pin_memory()
+    phi = torch.empty(mesh.n_nodes, dtype=torch.float64).pin_memory()
+    stats = (picfem.StepStats * 1)()
+    L = ctx.L
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx._check(L.pic_set_work_function(ctx.h, wf.data_ptr()))
+        ctx._check(L.pic_step(ctx.h, 1, stats))
+        ctx._check(L.pic_get_potential(ctx.h, phi.data_ptr()))
+    dt = time.perf_counter() - t0
+    return {"value": round(steps / dt, 3), "unit": "PIC cycles/s",
+            "h2d_bytes_per_step": 8 * mesh.n_faces,
+            "d2h_bytes_per_step": picfem.C.sizeof(picfem.StepStats) + 8 * mesh.n_nodes}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def run_oracle(workload, steps, seed=0):
+    from oracle import oracle as O
+    from paper_1906_08125_gb300 import configs as K
+    mesh, p, _ = K.workload(workload)
+    target = K.WORKLOADS[workload]["target_sp"]
+    p = dict(p, precision=K.PREC_FP64)
+    orc = O.Oracle(mesh, p)
+    orc.init_potential()
+    r, v, cell, pid = bench_population(mesh, target, seed=1000 + seed)
+    orc.set_particles(r, v, cell, pid)
+    t0 = time.perf_counter()
+    orc.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(steps / dt, 5), "unit": "PIC cycles/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{steps} full PIC steps of the {workload} workload (FP64 oracle, one "
+                       f"thread), from the seeded synthetic population of {target} SPs that "
+                       f"the GPU arm starts from; mesh build and charge-free solve untimed"),
+            "seconds": round(dt, 2)}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, args.cpu_steps))
+    cb = run_oracle(args.workload, steps)
+    line = {"metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": round(1e3 / cb["value"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "ref": "CPU oracle (plain FP64 C)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    fp64 = args.precision == "fp64"
+    res = run_gpu(args, rank, world, args.precision, args.steps, max(3, args.warmup))
+    roof, kernels = roofline(res, fp64)
+    K = args.steps
+    value = world * K / (res["total_ms"] * 1e-3)
+    pushes = res["pushes"]
+    if world > 1:
+        t = torch.tensor([pushes], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        pushes = float(t.item())
+    push_rate = pushes / (res["total_ms"] * 1e-3)
+    e2e = run_e2e(res, args.e2e_steps)
+    st = res["stats"]
+    cfg = {"workload": args.workload, "tets": res["info"]["n_tets"],
+           "nodes": res["info"]["n_nodes"], "free_dofs": res["info"]["n_free"],
+           "nnz": res["info"]["nnz"], "emitting_faces": res["info"]["n_faces"],
+           "sp_in_flight_mean": int(st["alive"].mean()), "target_sp": int(res["n0"]),
+           "dt_fs": 4.0, "precision": args.precision, "pcg_rtol": res["params"]["pcg_rtol"],
+           "l2": "flushed before every timed step (256 MB write)", "parallelism":
+           f"replicas x{world}"}
+    extra = {"pushes_per_s": round(push_rate, 1),
+             "pcg_iters_mean": round(float(st["pcg_iters"].mean()), 1),
+             "pcg_outer_mean": round(float(st["pcg_outer"].mean()), 2),
+             "crossings_per_sp": round(float(st["crossings"].sum()) / max(1, res["pushes"]), 1),
+             "kernels": kernels}
+    launches, clocks = res["launches"], res["clocks"]
+    res["ctx"].close()
+    del res
+    fp64_cmp = None
+    if not args.no_fp64_compare and not fp64:
+        r64 = run_gpu(args, rank, world, "fp64", max(5, K // 3), max(3, args.warmup))
+        fp64_cmp = {"value": round(world * len(r64["step_ms"]) / (r64["total_ms"] * 1e-3), 3),
+                    "unit": METRIC,
+                    "ms_per_step": round(r64["total_ms"] / len(r64["step_ms"]), 3),
+                    "pushes_per_s": round(r64["pushes"] / (r64["total_ms"] * 1e-3), 1),
+                    "pcg_iters_mean": round(float(r64["stats"]["pcg_iters"].mean()), 1)}
+        r64["ctx"].close()
+        del r64
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_oracle(args.workload, args.cpu_steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "PIC cycles/s",
+                "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
+                "ms_per_step": round(world * 1e3 / value, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp, **extra}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

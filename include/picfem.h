@@ -1,0 +1,252 @@
+/*
+ * picfem.h -- C ABI of libpicfem, the GB300 (sm_103a) electrostatic FEM-PIC
+ * cycle of Veske et al., "Dynamic coupling between particle-in-cell and
+ * atomistic simulations", Phys. Rev. E 101, 053307 (arXiv 1906.08125).
+ *
+ * One PIC step (Sec. II.B, eqs. leapfrog1-3 and Fig. 3):
+ *   inject        field-emission injection from the cathode quadrangles
+ *                 (Sec. II.B.3, eqs. nsp, rnd_nsp, sp_velocity,
+ *                 sp_displacement; App. E eq. rnd_point)
+ *   push_relocate leapfrog kick with E_k = -grad Phi_k (P1, constant per
+ *                 tetrahedron), drift, and relocation by walking tetrahedron
+ *                 neighbours; absorption at Gamma_1 / Gamma_3, periodic wrap
+ *                 on Gamma_2 (Sec. II.B.1-2)
+ *   deposit       charge to mesh nodes with the same P1 shape functions,
+ *                 as int64 fixed point (Sec. II.B.2, eq. poisson_rhs)
+ *   poisson_solve preconditioned CG on the P1 stiffness matrix (eqs. poisson,
+ *                 poisson_bc; App. B eq. poisson_mat) -> Phi_{k+1}
+ * pic_step runs the four in that order, n times, with fused kernels.
+ *
+ * Conventions for every entry point:
+ *  - Return value: PIC_OK (0) or a negative PIC_ERR_* code; the message is
+ *    available from pic_last_error().  No exception crosses the ABI.
+ *  - Host input arrays are copied; the caller keeps ownership.
+ *  - "device" pointers are CUDA device (or managed) memory on the context's
+ *    device, e.g. torch.Tensor.data_ptr(); the copy is queued on the
+ *    context's stream and is complete when the call returns unless stated
+ *    otherwise.  "host or device" pointers may be either (CUDA unified
+ *    addressing decides the direction).
+ *  - Calls that return host scalars synchronise the context's stream.
+ *  - The context owns all internal device buffers (freed by pic_destroy).
+ *  - Units are SI: m, s, V, V/m, C, kg.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef PICFEM_H
+#define PICFEM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIC_OK 0
+#define PIC_ERR_ARG (-1)             /* bad argument or non-finite input     */
+#define PIC_ERR_CUDA (-2)            /* a CUDA runtime call failed            */
+#define PIC_ERR_MESH (-3)            /* inconsistent or inverted mesh         */
+#define PIC_ERR_CAPACITY (-4)        /* more SPs than particle_capacity       */
+#define PIC_ERR_WALK_LIMIT (-5)      /* an SP walked more than walk_max_steps */
+#define PIC_ERR_NOT_CONVERGED (-6)   /* PCG reached pcg_max_iter              */
+#define PIC_ERR_NOT_IMPLEMENTED (-7)
+#define PIC_ERR_TIMEOUT (-8)         /* a device-side wait ran out            */
+
+/* neighbour-table boundary codes (nbr[t*4+k] < 0; face k is opposite vertex k) */
+#define PIC_BND_TOP (-1)      /* Gamma_1: far-field Neumann face, SPs collected */
+#define PIC_BND_CATHODE (-2)  /* Gamma_3: Dirichlet Phi = 0, SPs absorbed       */
+#define PIC_BND_SIDE (-3)     /* Gamma_2: laterally periodic for SPs            */
+
+/* arithmetic of the push and of the Poisson solve */
+#define PIC_PREC_FP64 0     /* FP64 throughout (bit-exact with the FP64 oracle)   */
+#define PIC_PREC_FP32_IR 1  /* FP32 push/SpMV; PCG wrapped in FP64 iterative
+                               refinement (FP64 residual, dot products, update) */
+
+/* Fowler-Nordheim model for the emission current density J_e */
+#define PIC_FN_MURPHY_GOOD 0  /* Murphy-Good with Forbes' 2006 v(f), t(f)   */
+#define PIC_FN_ELEMENTARY 1   /* v = t = 1                                    */
+
+typedef struct pic_ctx_s *pic_ctx;
+
+typedef struct {
+    double dt;             /* PIC time step Delta t [s] (eqs. leapfrog1-3)      */
+    double E0;             /* applied field on Gamma_1 [V/m] (eq. poisson_bc)   */
+    double w_sp;           /* SP weight (real particles per SP)                 */
+    double q;              /* charge of one real particle [C], -e for electrons */
+    double q_over_m;       /* charge-to-mass ratio [C/kg] (eq. newton)          */
+    double eps0;           /* permittivity [F/m] (eq. poisson)                  */
+    double e_charge;       /* elementary charge [C] (eq. nsp)                   */
+    double pcg_rtol;       /* stop when ||f - M Phi||_2 <= rtol ||f||_2         */
+    int32_t pcg_max_iter;  /* PCG iteration cap -> PIC_ERR_NOT_CONVERGED        */
+    int32_t fn_model;      /* PIC_FN_*                                          */
+    uint64_t seed;         /* key of the counter-based random numbers           */
+    int64_t capacity;      /* maximum SPs in flight -> PIC_ERR_CAPACITY         */
+    int32_t walk_max_steps;/* face crossings per SP per step -> PIC_ERR_WALK_LIMIT */
+    int32_t quant_bits;    /* S: deposit weights in units of 2^-S, 1 <= S <= 40 */
+    int32_t precision;     /* PIC_PREC_*                                        */
+    int32_t reserved;
+    double ir_inner_rtol;  /* FP32_IR: inner FP32 PCG reduces its residual by
+                              this factor per refinement (e.g. 1e-3)           */
+} pic_params;
+
+typedef struct {
+    int64_t injected;         /* SPs injected in the step                      */
+    int64_t collected;        /* SPs that left through Gamma_1                 */
+    int64_t absorbed;         /* SPs that left through Gamma_3                 */
+    int64_t wrapped;          /* periodic crossings of Gamma_2                 */
+    int64_t crossings;        /* face crossings of all SPs in the walk         */
+    int64_t alive;            /* SPs in flight after the step                  */
+    int32_t max_walk;         /* longest walk (face crossings) of one SP       */
+    int32_t pcg_iters;        /* CG iterations (FP32_IR: inner iterations)     */
+    double pcg_relres;        /* final ||f - M Phi|| / ||f||                    */
+    double collected_charge;  /* q * w_sp * collected [C]                      */
+    int32_t pcg_outer;        /* FP32_IR refinements (FP64: 0)                 */
+    int32_t reserved;
+} pic_step_stats;
+
+typedef struct {
+    int32_t n_nodes, n_tets, n_faces, n_free;
+    int64_t nnz;              /* nonzeros of the stiffness matrix on free DOFs  */
+    int64_t sell_len;         /* stored entries incl. slice padding            */
+    int32_t pcg_grid;         /* blocks of the persistent PCG launch           */
+    int32_t particle_grid;    /* blocks of the particle kernels                */
+    double box_lo[3], box_hi[3];
+} pic_info;
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream) on which every kernel and copy is queued. */
+int pic_create(pic_ctx *out, const pic_params *p, void *stream);
+int pic_destroy(pic_ctx ctx);
+/* Message of the last failed call on ctx (static storage when ctx is NULL). */
+const char *pic_last_error(pic_ctx ctx);
+/* Library version string. */
+const char *pic_version(void);
+
+/*
+ * mesh_load: the vacuum domain Omega_1 as P1 tetrahedra (Sec. II.A, App. B).
+ * All pointers are HOST arrays and are copied.
+ *   xyz[n_nodes*3]         node coordinates [m]
+ *   tet[n_tets*4]          node indices, positively oriented
+ *                          (det[x1-x0, x2-x0, x3-x0] > 0, else PIC_ERR_MESH)
+ *   nbr[n_tets*4]          tetrahedron across the face opposite vertex k, or a
+ *                          PIC_BND_* code; interior entries must be mutual
+ *   periodic_nbr[n_tets*4] partner across a PIC_BND_SIDE face (nullable when
+ *                          there are none); the side faces must lie on the
+ *                          bounding-box planes x = min/max or y = min/max
+ *   node_dirichlet[n_nodes] 1 for nodes on Gamma_3 (Phi = 0)
+ *   face_nodes[n_faces*3]  emitting cathode triangles (A, B, C) with
+ *                          (B-A)x(C-A) pointing into the vacuum; each gives
+ *                          three quadrangles, one per vertex (Sec. II.B.3)
+ *   face_tet[n_faces]      tetrahedron on the vacuum side of each face
+ *   work_function_eV[n_faces] > 0
+ * Builds the per-tetrahedron walk records, the stiffness matrix (sliced
+ * ELLPACK), the Neumann load E0 A/3 per top-face vertex, and resets the
+ * state (no SPs, Phi = 0, step 0).
+ */
+int mesh_load(pic_ctx ctx, int32_t n_nodes, const double *xyz, int32_t n_tets,
+              const int32_t *tet, const int32_t *nbr, const int32_t *periodic_nbr,
+              const uint8_t *node_dirichlet, int32_t n_faces, const int32_t *face_nodes,
+              const int32_t *face_tet, const double *work_function_eV);
+
+/* Sizes of the loaded mesh and of the launches (info: HOST). */
+int pic_mesh_info(pic_ctx ctx, pic_info *info);
+
+/* Charge-free potential: Phi_0 from M Phi = f_Neumann (W = 0). */
+int pic_init_potential(pic_ctx ctx, int32_t *iters, double *rel_res);
+
+/*
+ * inject: for every quadrangle q of every emitting face, F = max(0, -E.n),
+ * J_e = J_FN(F, phi_face) (closed form; the paper uses GETELEC),
+ * n_sp = J_e A_q dt / (e w_sp), stochastically rounded with R0 (eq. rnd_nsp);
+ * each new SP gets a uniform point of the quadrangle by rejection from the
+ * parallelogram (App. E), v0 = (q/m) E dt (1/2 + R3) and r = point + v0 dt R3
+ * (eqs. sp_velocity, sp_displacement).  New SPs are appended and marked
+ * fresh: the next push_relocate drifts them without the kick.
+ * SP ids: (step << 42) | (quad << 18) | j.
+ * n_injected: HOST, nullable (non-NULL synchronises).
+ */
+int inject(pic_ctx ctx, int64_t step, int64_t *n_injected);
+
+/*
+ * push_relocate: v += (q/m) dt E_cell for non-fresh SPs (the closing half kick
+ * of the previous step merged with the opening half kick, eqs. leapfrog3 +
+ * leapfrog1), then r += dt v for all, then the neighbour walk to the
+ * containing tetrahedron; SPs leaving through Gamma_1 / Gamma_3 are removed,
+ * through Gamma_2 wrapped.  out: HOST, nullable (non-NULL synchronises).
+ */
+int push_relocate(pic_ctx ctx, int64_t step, pic_step_stats *out);
+
+/*
+ * deposit: W_i = sum over SPs of the fixed-point weight of node i (eq.
+ * poisson_rhs; w = rint(lambda 2^S) for three vertices, the fourth takes the
+ * remainder, so every SP adds exactly 2^S).  node_charge_fx: DEVICE int64
+ * [n_nodes], nullable; receives W.
+ */
+int deposit(pic_ctx ctx, int64_t *node_charge_fx);
+
+/*
+ * poisson_solve: f = (q w_sp / eps0) W 2^-S + f_Neumann on the free nodes;
+ * Jacobi-PCG warm-started from the current Phi (precision per pic_params);
+ * updates Phi and E.  phi: DEVICE double [n_nodes], nullable; iters and
+ * rel_res: HOST, nullable (non-NULL synchronises).
+ */
+int poisson_solve(pic_ctx ctx, double *phi, int32_t *iters, double *rel_res);
+
+/*
+ * pic_step: n_steps full PIC steps from the current state (inject, push,
+ * walk, deposit, solve), step index advancing by one each.  stats: host or
+ * device array [n_steps], nullable.  A host array synchronises at the end
+ * (and reports device-side errors); a device array is filled asynchronously
+ * (collected_charge left 0) and errors surface at the next pic_sync.
+ */
+int pic_step(pic_ctx ctx, int64_t n_steps, pic_step_stats *stats);
+
+/*
+ * pic_adjoint: d(collected charge)/d(E0) and d/d(work function per face)
+ * over n_steps with checkpoints every ckpt_every steps.  Not built yet:
+ * returns PIC_ERR_NOT_IMPLEMENTED.
+ */
+int pic_adjoint(pic_ctx ctx, int64_t n_steps, int32_t ckpt_every, double *dQ_dE0,
+                double *dQ_dphi);
+
+/* ---- state (checkpoint / resume, parity) ---- */
+int pic_get_step(pic_ctx ctx, int64_t *step);
+int pic_set_step(pic_ctx ctx, int64_t step);
+/* phi: host or device double [n_nodes]; Dirichlet nodes read/write as 0 */
+int pic_get_potential(pic_ctx ctx, double *phi);
+int pic_set_potential(pic_ctx ctx, const double *phi);
+/* E: host or device double [n_tets*3], the field of the current Phi */
+int pic_get_field(pic_ctx ctx, double *E);
+/* W of the last deposit: host or device int64 [n_nodes] */
+int pic_get_charge(pic_ctx ctx, int64_t *W);
+/* number of SPs in flight (synchronises) */
+int pic_num_particles(pic_ctx ctx, int64_t *n);
+/* r, v: host or device double [n*3] (xyz interleaved); cell: int32 [n];
+ * id: int64 [n]; n = pic_num_particles; any pointer nullable.  The order of
+ * SPs is unspecified (sort by id to compare). */
+int pic_get_particles(pic_ctx ctx, double *r, double *v, int32_t *cell, int64_t *id);
+/* replace the SPs (none fresh); cell must hold the tetrahedron containing r */
+int pic_set_particles(pic_ctx ctx, int64_t n, const double *r, const double *v,
+                      const int32_t *cell, const int64_t *id);
+/* work function per emitting face: host or device double [n_faces] */
+int pic_set_work_function(pic_ctx ctx, const double *work_function_eV);
+
+/* ---- counters ---- */
+/* Number of this library's kernel launches since the context was created. */
+int pic_launch_count(pic_ctx ctx, int64_t *launches);
+/* Per-kernel device time recorded with CUDA events on the context's stream
+ * while profiling is enabled.  names[i] points to static strings. */
+#define PIC_PROF_MAX 16
+typedef struct {
+    int32_t n;
+    const char *name[PIC_PROF_MAX];
+    int64_t launches[PIC_PROF_MAX];
+    double ms[PIC_PROF_MAX];
+} pic_profile_report;
+int pic_profile_enable(pic_ctx ctx, int32_t enable);  /* also clears */
+int pic_profile_read(pic_ctx ctx, pic_profile_report *out); /* synchronises */
+/* Wait for all queued work; returns the first device-side error, if any. */
+int pic_sync(pic_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

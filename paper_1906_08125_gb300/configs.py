@@ -5,8 +5,10 @@ CODATA 2018 values are used.  Each workload names its mesh recipe (from
 ``inputs``) and the run parameters.  The SP weight w_sp is a per-simulation
 choice in the paper (Sec. II.B: "determined independently for each
 simulation"); the values below were fixed once per workload from the
-charge-free emission current so that a full box holds about the target SP
-count, and are never recomputed at run time.
+oracle (``oracle/derive_wsp.py``): in the space-charge-limited regime the
+number of SPs in flight scales as 1/w_sp, so a short oracle run at a trial
+weight is rescaled to the target count.  They are never recomputed at run
+time.
 """
 from __future__ import annotations
 
@@ -39,13 +41,13 @@ WORKLOADS = {
     # parallel-plate gap: 100x100x200 nm, 20x20x40 cubes x 6 tets, 10 GV/m,
     # work function 4.5 eV, 1e4 SPs, 100 steps of 4 fs, FP64
     "plate_96k": dict(mesh=lambda: inputs.plate_mesh(),
-                      params=dict(dt=4e-15, E0=1e10, w_sp=0.55, capacity=20000,
+                      params=dict(dt=4e-15, E0=1e10, w_sp=0.09, capacity=20000,
                                   precision=PREC_FP64, pcg_rtol=1e-12),
                       steps=100, target_sp=10_000),
     # Cu-like nanotip: r = 3 nm, h = 30 nm in a 60x60x230 nm box, ~1M tets,
     # 10 GV/m, up to 1e6 SPs, FP32 push + FP64-refined PCG to 1e-6, 500 steps
     "tip_1m": dict(mesh=lambda: inputs.tip_mesh(),
-                   params=dict(dt=4e-15, E0=1e10, w_sp=0.02, capacity=2_000_000,
+                   params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=2_000_000,
                                precision=PREC_FP32_IR, pcg_rtol=1e-6),
                    steps=500, target_sp=1_000_000),
     # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, ~8M tets,

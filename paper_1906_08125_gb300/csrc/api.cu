@@ -1,0 +1,1343 @@
+// api.cu -- the C ABI of libpicfem (include/picfem.h): context, mesh loading
+// (validation, topology tables and the sparsity pattern are built on the
+// host; geometry and matrix values are computed by kernels), state access and
+// the orchestration of one PIC step on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace pf;
+
+namespace {
+
+enum KernelId {
+    K_FIELD,
+    K_INJECT_COUNT,
+    K_INJECT_SCAN,
+    K_INJECT_EMIT,
+    K_PUSH_RELOCATE,
+    K_DEPOSIT,
+    K_STEP_FUSED,
+    K_PCG,
+    K_UTIL,
+    K_NUM
+};
+const char *const kKernelNames[K_NUM] = {"field",          "inject_count", "inject_scan",
+                                         "inject_emit",    "push_relocate", "deposit",
+                                         "step_fused",     "pcg",          "util"};
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct pic_ctx_s {
+    pic_params p{};
+    cudaStream_t s = nullptr;
+    int dev = 0, num_sms = 0;
+    std::string err;
+    // sizes
+    int N = 0, T = 0, F = 0, NQ = 0, n_free = 0, n_pad = 0, n_slices = 0;
+    long long sell_len = 0, nnz = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    bool loaded = false;
+    std::vector<void *> allocs;  // mesh-lifetime device buffers
+    // mesh
+    double *xyz = nullptr;
+    int4 *tet4 = nullptr;
+    TetRec64 *rec64 = nullptr;
+    TetRec32 *rec32 = nullptr;
+    double *det = nullptr;
+    unsigned char *dir = nullptr;
+    int *face_nodes = nullptr, *face_tet = nullptr;
+    double *wf = nullptr, *fnhat = nullptr, *farea = nullptr;
+    int *dof_node = nullptr, *slice_ptr = nullptr, *col = nullptr;
+    double *val64 = nullptr, *dinv64 = nullptr, *fN = nullptr;
+    float *val32 = nullptr, *dinv32 = nullptr;
+    // state
+    double *phi = nullptr, *x = nullptr;
+    void *E = nullptr;
+    unsigned long long *W = nullptr;
+    void *pbuf[2][6] = {{nullptr}};
+    int *cell[2] = {nullptr, nullptr};
+    long long *id[2] = {nullptr, nullptr};
+    int a = 0;
+    DevState *st = nullptr;
+    int *qcount = nullptr;
+    long long *qoff = nullptr;
+    // pcg
+    double *f = nullptr, *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *ap = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32_0 = nullptr, *p32_1 = nullptr, *ap32 = nullptr,
+          *dx32 = nullptr;
+    double *partials = nullptr;
+    PcgLaunch plan{};
+    pic_step_stats *dstats = nullptr;  // per-step stats of pic_step
+    long long dstats_cap = 0;
+    pic_step_stats *sstats = nullptr;  // scratch stats of the split calls
+    // staging
+    void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t stage_sz[4] = {0, 0, 0, 0};
+    int64_t step = 0;
+    long long launches = 0;
+    int pgrid = 0;
+    // profiling
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[K_NUM] = {0};
+    long long prof_n[K_NUM] = {0};
+};
+
+namespace {
+
+std::string g_err;
+
+int fail(pic_ctx c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(c, PIC_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+cudaEvent_t take_event(pic_ctx c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    pic_ctx c;
+    int kid;
+    cudaEvent_t a = nullptr;
+    ProfScope(pic_ctx c_, int k) : c(c_), kid(k)
+    {
+        if (c->prof) {
+            a = take_event(c);
+            cudaEventRecord(a, c->s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->s);
+            c->prof_recs.push_back({kid, a, b});
+        }
+    }
+};
+
+#define LAUNCH(kid, call)                                                                  \
+    do {                                                                                   \
+        ProfScope ps_(c, kid);                                                             \
+        cudaError_t e_ = (call);                                                           \
+        ++c->launches;                                                                     \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(c, PIC_ERR_CUDA, "launch %s: %s", kKernelNames[kid],               \
+                        cudaGetErrorString(e_));                                           \
+    } while (0)
+
+template <typename T> cudaError_t dalloc(pic_ctx c, T **p, size_t n)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n ? n * sizeof(T) : 16);
+    if (e == cudaSuccess) {
+        c->allocs.push_back(q);
+        *p = (T *)q;
+    }
+    return e;
+}
+
+void free_mesh(pic_ctx c)
+{
+    for (void *q : c->allocs)
+        cudaFree(q);
+    c->allocs.clear();
+    c->loaded = false;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t stage(pic_ctx c, int slot, size_t bytes, void **out)
+{
+    if (c->stage_sz[slot] < bytes) {
+        if (c->stage[slot])
+            cudaFree(c->stage[slot]);
+        c->stage[slot] = nullptr;
+        c->stage_sz[slot] = 0;
+        cudaError_t e = cudaMalloc(&c->stage[slot], bytes);
+        if (e != cudaSuccess)
+            return e;
+        c->stage_sz[slot] = bytes;
+    }
+    *out = c->stage[slot];
+    return cudaSuccess;
+}
+
+int check_device_error(pic_ctx c)
+{
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (h.err) {
+        const char *what = h.err == PIC_ERR_CAPACITY        ? "particle capacity exceeded"
+                           : h.err == PIC_ERR_WALK_LIMIT    ? "an SP exceeded walk_max_steps"
+                           : h.err == PIC_ERR_NOT_CONVERGED ? "PCG reached pcg_max_iter"
+                           : h.err == PIC_ERR_TIMEOUT       ? "device-side wait timed out"
+                           : h.err == PIC_ERR_ARG           ? "injection rejection limit"
+                                                            : "device error";
+        int code = h.err;
+        int zero = 0;
+        cudaMemcpy(&c->st->err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        return fail(c, code, "%s (device status %d)", what, code);
+    }
+    return PIC_OK;
+}
+
+bool fp64(pic_ctx c) { return c->p.precision == PIC_PREC_FP64; }
+
+template <typename R> Particles<R> parts(pic_ctx c, int b)
+{
+    Particles<R> P;
+    P.x = (R *)c->pbuf[b][0];
+    P.y = (R *)c->pbuf[b][1];
+    P.z = (R *)c->pbuf[b][2];
+    P.vx = (R *)c->pbuf[b][3];
+    P.vy = (R *)c->pbuf[b][4];
+    P.vz = (R *)c->pbuf[b][5];
+    P.cell = c->cell[b];
+    P.id = c->id[b];
+    return P;
+}
+
+template <typename R> MeshView<R> view(pic_ctx c)
+{
+    MeshView<R> m;
+    if constexpr (sizeof(R) == 8)
+        m.rec = (const typename Rec<R>::type *)c->rec64;
+    else
+        m.rec = (const typename Rec<R>::type *)c->rec32;
+    m.tet = c->tet4;
+    m.E = (const typename Rec<R>::vec4 *)c->E;
+    m.face_nodes = c->face_nodes;
+    m.face_tet = c->face_tet;
+    m.face_nhat = c->fnhat;
+    m.face_area = c->farea;
+    m.wf = c->wf;
+    m.xyz = c->xyz;
+    m.n_faces = c->F;
+    m.Lx = c->hi[0] - c->lo[0];
+    m.Ly = c->hi[1] - c->lo[1];
+    return m;
+}
+
+RunConst run_const(pic_ctx c)
+{
+    RunConst k;
+    k.dt = c->p.dt;
+    k.qmdt = c->p.q_over_m * c->p.dt;
+    k.w_sp = c->p.w_sp;
+    k.e_charge = c->p.e_charge;
+    k.scale = std::ldexp(1.0, c->p.quant_bits);
+    k.seed = c->p.seed;
+    k.capacity = c->p.capacity;
+    k.fn_model = c->p.fn_model;
+    k.walk_max = c->p.walk_max_steps;
+    return k;
+}
+
+__global__ void k_phi_to_x(int n, const int *dof_node, const double *phi, double *x)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < n)
+        x[d] = phi[dof_node[d]];
+}
+__global__ void k_zero_dirichlet(int N, const unsigned char *dir, double *phi)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N && dir[i])
+        phi[i] = 0.0;
+}
+
+int refresh_field(pic_ctx c)
+{
+    if (fp64(c))
+        LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, c->phi, (double4 *)c->E));
+    else
+        LAUNCH(K_FIELD, launch_field<float>(c->s, c->T, c->rec32, c->tet4, c->phi, (float4 *)c->E));
+    return PIC_OK;
+}
+
+int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
+{
+    PcgArgs g{};
+    g.n = c->n_free;
+    g.n_pad = c->n_pad;
+    g.n_slices = c->n_slices;
+    g.slice_ptr = c->slice_ptr;
+    g.col = c->col;
+    g.val64 = c->val64;
+    g.val32 = c->val32;
+    g.dinv64 = c->dinv64;
+    g.dinv32 = c->dinv32;
+    g.fN = c->fN;
+    g.W = c->W;
+    g.dof_node = c->dof_node;
+    g.coef = (c->p.q * c->p.w_sp) / c->p.eps0;
+    g.wscale = std::ldexp(1.0, -c->p.quant_bits);
+    g.x = c->x;
+    g.phi = c->phi;
+    g.f = c->f;
+    g.r = c->r;
+    g.z = c->z;
+    g.p0 = c->p0;
+    g.p1 = c->p1;
+    g.ap = c->ap;
+    g.r32 = c->r32;
+    g.z32 = c->z32;
+    g.p32_0 = c->p32_0;
+    g.p32_1 = c->p32_1;
+    g.ap32 = c->ap32;
+    g.dx32 = c->dx32;
+    g.partials = c->partials;
+    g.st = c->st;
+    g.stats = stats;
+    g.alive = alive;
+    g.rtol = c->p.pcg_rtol;
+    g.inner_rtol = c->p.ir_inner_rtol;
+    g.max_iter = c->p.pcg_max_iter;
+    g.precision = c->p.precision;
+    CK(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->s));
+    LAUNCH(K_PCG, launch_pcg(c->s, c->plan, g));
+    return PIC_OK;
+}
+
+int ensure_dstats(pic_ctx c, long long n)
+{
+    if (c->dstats_cap < n) {
+        if (c->dstats)
+            cudaFree(c->dstats);
+        c->dstats = nullptr;
+        c->dstats_cap = 0;
+        CK(cudaMalloc(&c->dstats, sizeof(pic_step_stats) * (size_t)n));
+        c->dstats_cap = n;
+    }
+    return PIC_OK;
+}
+
+#define REQUIRE_MESH()                                                                   \
+    do {                                                                                 \
+        if (!c)                                                                          \
+            return fail(nullptr, PIC_ERR_ARG, "null context");                           \
+        if (!c->loaded)                                                                  \
+            return fail(c, PIC_ERR_ARG, "mesh_load has not been called");               \
+        CK(cudaSetDevice(c->dev));                                                       \
+    } while (0)
+
+}  // namespace
+
+// ===========================================================================
+// context
+// ===========================================================================
+extern "C" const char *pic_version(void) { return "libpicfem 0.1 (sm_103a)"; }
+
+extern "C" const char *pic_last_error(pic_ctx c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
+{
+    pic_ctx c = nullptr;
+    if (!out || !p)
+        return fail(nullptr, PIC_ERR_ARG, "pic_create: null argument");
+    const pic_params &q = *p;
+    if (!(q.dt > 0) || !std::isfinite(q.dt) || !std::isfinite(q.E0) || !(q.w_sp > 0) ||
+        !std::isfinite(q.w_sp) || !std::isfinite(q.q) || !std::isfinite(q.q_over_m) ||
+        !(q.eps0 > 0) || !(q.e_charge > 0) || !(q.pcg_rtol >= 0) || q.pcg_max_iter < 0 ||
+        q.capacity < 1 || q.walk_max_steps < 1 || q.quant_bits < 1 || q.quant_bits > 40 ||
+        (q.precision != PIC_PREC_FP64 && q.precision != PIC_PREC_FP32_IR) ||
+        (q.fn_model != PIC_FN_MURPHY_GOOD && q.fn_model != PIC_FN_ELEMENTARY) ||
+        (q.precision == PIC_PREC_FP32_IR && !(q.ir_inner_rtol > 0 && q.ir_inner_rtol < 1)))
+        return fail(nullptr, PIC_ERR_ARG, "pic_create: invalid parameters");
+    c = new pic_ctx_s();
+    c->p = q;
+    c->s = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, PIC_ERR_CUDA, "pic_create: no CUDA device");
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev);
+    if (!coop) {
+        delete c;
+        return fail(nullptr, PIC_ERR_CUDA, "pic_create: device lacks cooperative launch");
+    }
+    c->pgrid = c->num_sms * 8;
+    *out = c;
+    return PIC_OK;
+}
+
+extern "C" int pic_destroy(pic_ctx c)
+{
+    if (!c)
+        return PIC_OK;
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->s);
+    free_mesh(c);
+    for (int i = 0; i < 4; ++i)
+        if (c->stage[i])
+            cudaFree(c->stage[i]);
+    if (c->dstats)
+        cudaFree(c->dstats);
+    for (auto &r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->ev_pool)
+        cudaEventDestroy(e);
+    delete c;
+    return PIC_OK;
+}
+
+// ===========================================================================
+// mesh
+// ===========================================================================
+extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, const int32_t *tet,
+                         const int32_t *nbr, const int32_t *pnbr, const uint8_t *dir,
+                         int32_t F, const int32_t *face_nodes, const int32_t *face_tet,
+                         const double *wf)
+{
+    if (!c)
+        return fail(nullptr, PIC_ERR_ARG, "null context");
+    CK(cudaSetDevice(c->dev));
+    if (N < 4 || T < 1 || F < 0 || !xyz || !tet || !nbr || !dir ||
+        (F > 0 && (!face_nodes || !face_tet || !wf)))
+        return fail(c, PIC_ERR_ARG, "mesh_load: bad sizes or null arrays");
+    if ((long long)F * 3 >= (1LL << 24) || T >= (1 << 27))
+        return fail(c, PIC_ERR_ARG, "mesh_load: mesh too large for the id / neighbour packing");
+    CK(cudaStreamSynchronize(c->s));
+    free_mesh(c);
+
+    // ---- validation --------------------------------------------------------
+    for (long long i = 0; i < 3LL * N; ++i)
+        if (!std::isfinite(xyz[i]))
+            return fail(c, PIC_ERR_ARG, "mesh_load: non-finite node coordinate");
+    for (long long t = 0; t < T; ++t)
+        for (int k = 0; k < 4; ++k) {
+            int v = tet[4 * t + k], b = nbr[4 * t + k];
+            if (v < 0 || v >= N)
+                return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld node out of range", t);
+            if (b >= T || b < PIC_BND_SIDE)
+                return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld bad neighbour %d", t, b);
+            if (b >= 0) {
+                int back = 0;
+                for (int m = 0; m < 4; ++m)
+                    back += nbr[4LL * b + m] == t;
+                if (back != 1)
+                    return fail(c, PIC_ERR_MESH, "mesh_load: neighbours of %lld not mutual", t);
+            }
+            if (b == PIC_BND_SIDE && (!pnbr || pnbr[4 * t + k] < 0 || pnbr[4 * t + k] >= T))
+                return fail(c, PIC_ERR_MESH, "mesh_load: side face of %lld has no partner", t);
+        }
+    for (long long f = 0; f < F; ++f) {
+        if (face_tet[f] < 0 || face_tet[f] >= T)
+            return fail(c, PIC_ERR_MESH, "mesh_load: face %lld bad tetrahedron", f);
+        if (!(wf[f] > 0) || !std::isfinite(wf[f]))
+            return fail(c, PIC_ERR_ARG, "mesh_load: face %lld bad work function", f);
+        for (int k = 0; k < 3; ++k)
+            if (face_nodes[3 * f + k] < 0 || face_nodes[3 * f + k] >= N)
+                return fail(c, PIC_ERR_MESH, "mesh_load: face %lld node out of range", f);
+    }
+    // orientation (sign only; the exact geometry is computed on the device)
+    for (long long t = 0; t < T; ++t) {
+        const double *X[4];
+        for (int k = 0; k < 4; ++k)
+            X[k] = xyz + 3LL * tet[4 * t + k];
+        double a[3], b[3], d[3];
+        for (int i = 0; i < 3; ++i) {
+            a[i] = X[1][i] - X[0][i];
+            b[i] = X[2][i] - X[0][i];
+            d[i] = X[3][i] - X[0][i];
+        }
+        double det = a[0] * (b[1] * d[2] - b[2] * d[1]) - a[1] * (b[0] * d[2] - b[2] * d[0]) +
+                     a[2] * (b[0] * d[1] - b[1] * d[0]);
+        if (!(det > 0))
+            return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld not positively oriented", t);
+    }
+    for (int i = 0; i < 3; ++i)
+        c->lo[i] = c->hi[i] = xyz[i];
+    for (long long n = 0; n < N; ++n)
+        for (int i = 0; i < 3; ++i) {
+            c->lo[i] = std::min(c->lo[i], xyz[3 * n + i]);
+            c->hi[i] = std::max(c->hi[i], xyz[3 * n + i]);
+        }
+
+    // ---- packed neighbour table --------------------------------------------
+    auto face_vertex = [&](long long t, int k, int m) {  // m-th node of face k
+        int idx = m + (m >= k ? 1 : 0);
+        return tet[4 * t + idx];
+    };
+    std::vector<signed char> side_code(4 * (size_t)T, -1);
+    for (long long t = 0; t < T; ++t)
+        for (int k = 0; k < 4; ++k) {
+            if (nbr[4 * t + k] != PIC_BND_SIDE)
+                continue;
+            int code = -1;
+            for (int ax = 0; ax < 2 && code < 0; ++ax) {
+                bool at_lo = true, at_hi = true;
+                for (int m = 0; m < 3; ++m) {
+                    double q = xyz[3LL * face_vertex(t, k, m) + ax];
+                    at_lo = at_lo && q == c->lo[ax];
+                    at_hi = at_hi && q == c->hi[ax];
+                }
+                if (at_lo)
+                    code = 2 * ax;      // +L
+                else if (at_hi)
+                    code = 2 * ax + 1;  // -L
+            }
+            if (code < 0)
+                return fail(c, PIC_ERR_MESH, "mesh_load: side face of %lld not on a box plane", t);
+            side_code[4 * t + k] = (signed char)code;
+        }
+    std::vector<int4> nb4((size_t)T);
+    for (long long t = 0; t < T; ++t) {
+        int out[4];
+        for (int k = 0; k < 4; ++k) {
+            int b = nbr[4 * t + k];
+            if (b >= 0) {
+                int m = 0;
+                while (nbr[4LL * b + m] != t)
+                    ++m;
+                out[k] = (b << 2) | m;
+            } else if (b == PIC_BND_TOP) {
+                out[k] = NB_TOP;
+            } else if (b == PIC_BND_CATHODE) {
+                out[k] = NB_CATHODE;
+            } else {
+                int p = pnbr[4 * t + k], sc = side_code[4 * t + k], want = sc ^ 1, m = -1;
+                for (int q = 0; q < 4 && m < 0; ++q)
+                    if (nbr[4LL * p + q] == PIC_BND_SIDE && pnbr[4LL * p + q] == t &&
+                        side_code[4LL * p + q] == want)
+                        m = q;
+                if (m < 0)
+                    return fail(c, PIC_ERR_MESH, "mesh_load: periodic partner of %lld does not match", t);
+                out[k] = NB_SIDE - ((p << 4) | (sc << 2) | m);
+            }
+        }
+        nb4[t] = make_int4(out[0], out[1], out[2], out[3]);
+    }
+
+    // ---- free DOFs and the stiffness pattern --------------------------------
+    std::vector<int> dof((size_t)N);
+    int nf = 0;
+    for (int n = 0; n < N; ++n)
+        dof[n] = dir[n] ? -1 : nf++;
+    if (nf == 0)
+        return fail(c, PIC_ERR_MESH, "mesh_load: no free nodes");
+    std::vector<long long> rs((size_t)nf + 1, 0);
+    for (long long t = 0; t < T; ++t)
+        for (int i = 0; i < 4; ++i) {
+            int di = dof[tet[4 * t + i]];
+            if (di < 0)
+                continue;
+            for (int j = 0; j < 4; ++j)
+                if (dof[tet[4 * t + j]] >= 0)
+                    rs[di + 1]++;
+        }
+    for (int i = 0; i < nf; ++i)
+        rs[i + 1] += rs[i];
+    std::vector<int> raw((size_t)rs[nf]);
+    {
+        std::vector<long long> fill(rs.begin(), rs.end() - 1);
+        for (long long t = 0; t < T; ++t)
+            for (int i = 0; i < 4; ++i) {
+                int di = dof[tet[4 * t + i]];
+                if (di < 0)
+                    continue;
+                for (int j = 0; j < 4; ++j) {
+                    int dj = dof[tet[4 * t + j]];
+                    if (dj >= 0)
+                        raw[fill[di]++] = dj;
+                }
+            }
+    }
+    std::vector<long long> rowptr((size_t)nf + 1, 0);
+    std::vector<int> colv;
+    colv.reserve((size_t)rs[nf] / 3);
+    for (int i = 0; i < nf; ++i) {
+        auto b = raw.begin() + rs[i], e = raw.begin() + rs[i + 1];
+        std::sort(b, e);
+        auto u = std::unique(b, e);
+        colv.insert(colv.end(), b, u);
+        rowptr[i + 1] = (long long)colv.size();
+    }
+    std::vector<int>().swap(raw);
+    const long long nnz = rowptr[nf];
+    auto slot_of = [&](int row, int cl) -> long long {
+        auto b = colv.begin() + rowptr[row], e = colv.begin() + rowptr[row + 1];
+        return (long long)(std::lower_bound(b, e, cl) - colv.begin());
+    };
+    // contributions of each nonzero in increasing element order
+    std::vector<long long> cptr((size_t)nnz + 1, 0);
+    for (long long t = 0; t < T; ++t)
+        for (int i = 0; i < 4; ++i) {
+            int di = dof[tet[4 * t + i]];
+            if (di < 0)
+                continue;
+            for (int j = 0; j < 4; ++j) {
+                int dj = dof[tet[4 * t + j]];
+                if (dj >= 0)
+                    cptr[slot_of(di, dj) + 1]++;
+            }
+        }
+    for (long long s = 0; s < nnz; ++s)
+        cptr[s + 1] += cptr[s];
+    std::vector<int> contrib((size_t)cptr[nnz]);
+    {
+        std::vector<long long> fill(cptr.begin(), cptr.end() - 1);
+        for (long long t = 0; t < T; ++t)
+            for (int i = 0; i < 4; ++i) {
+                int di = dof[tet[4 * t + i]];
+                if (di < 0)
+                    continue;
+                for (int j = 0; j < 4; ++j) {
+                    int dj = dof[tet[4 * t + j]];
+                    if (dj >= 0)
+                        contrib[fill[slot_of(di, dj)]++] = (int)((t << 4) | (i << 2) | j);
+                }
+            }
+    }
+    // sliced ELLPACK, 32 rows per slice, padding rows/entries point at their own row
+    const int n_pad = (nf + 31) & ~31, n_slices = n_pad / 32;
+    std::vector<int> sptr((size_t)n_slices + 1, 0);
+    for (int s = 0; s < n_slices; ++s) {
+        long long w = 0;
+        for (int l = 0; l < 32; ++l) {
+            int row = s * 32 + l;
+            if (row < nf)
+                w = std::max(w, rowptr[row + 1] - rowptr[row]);
+        }
+        if ((long long)sptr[s] + 32 * w >= (1LL << 31))
+            return fail(c, PIC_ERR_ARG, "mesh_load: matrix too large");
+        sptr[s + 1] = sptr[s] + (int)(32 * w);
+    }
+    const long long sell_len = sptr[n_slices];
+    std::vector<int> scol((size_t)sell_len);
+    std::vector<long long> spos((size_t)nnz);
+    std::vector<int> srow((size_t)nnz), scl((size_t)nnz);
+    for (int s = 0; s < n_slices; ++s) {
+        int w = (sptr[s + 1] - sptr[s]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            int row = s * 32 + l;
+            long long len = row < nf ? rowptr[row + 1] - rowptr[row] : 0;
+            for (int k = 0; k < w; ++k) {
+                long long pos = sptr[s] + (long long)k * 32 + l;
+                if (k < len) {
+                    long long slot = rowptr[row] + k;
+                    scol[pos] = colv[slot];
+                    spos[slot] = pos;
+                    srow[slot] = row;
+                    scl[slot] = colv[slot];
+                } else {
+                    scol[pos] = row;
+                }
+            }
+        }
+    }
+    // Neumann contributions per free DOF in increasing (tet, face) order
+    std::vector<int> fptr((size_t)nf + 1, 0), fcon;
+    {
+        std::vector<std::pair<int, int>> pairs;  // (dof, tet<<2|face)
+        for (long long t = 0; t < T; ++t)
+            for (int k = 0; k < 4; ++k) {
+                if (nbr[4 * t + k] != PIC_BND_TOP)
+                    continue;
+                for (int m = 0; m < 3; ++m) {
+                    int d = dof[face_vertex(t, k, m)];
+                    if (d >= 0)
+                        pairs.push_back({d, (int)((t << 2) | k)});
+                }
+            }
+        std::stable_sort(pairs.begin(), pairs.end(),
+                         [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+                             return x.first < y.first;
+                         });
+        fcon.resize(pairs.size());
+        for (size_t i = 0; i < pairs.size(); ++i) {
+            fptr[pairs[i].first + 1]++;
+            fcon[i] = pairs[i].second;
+        }
+        for (int i = 0; i < nf; ++i)
+            fptr[i + 1] += fptr[i];
+    }
+    std::vector<int> dof_node((size_t)n_pad, -1);
+    for (int n = 0; n < N; ++n)
+        if (dof[n] >= 0)
+            dof_node[dof[n]] = n;
+
+    // ---- device buffers ------------------------------------------------------
+    c->N = N;
+    c->T = T;
+    c->F = F;
+    c->NQ = 3 * F;
+    c->n_free = nf;
+    c->n_pad = n_pad;
+    c->n_slices = n_slices;
+    c->sell_len = sell_len;
+    c->nnz = nnz;
+    const bool d64 = fp64(c);
+    const size_t cap = (size_t)c->p.capacity;
+    const size_t rsz = d64 ? 8 : 4;
+    int4 *d_nb = nullptr;
+    long long *d_cptr = nullptr, *d_spos = nullptr;
+    int *d_contrib = nullptr, *d_srow = nullptr, *d_scl = nullptr, *d_fptr = nullptr, *d_fcon = nullptr;
+    std::vector<int4> tet4((size_t)T);
+    for (long long t = 0; t < T; ++t)
+        tet4[t] = make_int4(tet[4 * t], tet[4 * t + 1], tet[4 * t + 2], tet[4 * t + 3]);
+
+    CK(dalloc(c, &c->xyz, 3 * (size_t)N));
+    CK(dalloc(c, &c->tet4, (size_t)T));
+    CK(dalloc(c, &c->rec64, (size_t)T));
+    if (!d64)
+        CK(dalloc(c, &c->rec32, (size_t)T));
+    CK(dalloc(c, &c->det, (size_t)T));
+    CK(dalloc(c, &c->dir, (size_t)N));
+    CK(dalloc(c, &c->face_nodes, 3 * (size_t)F + 3));
+    CK(dalloc(c, &c->face_tet, (size_t)F + 1));
+    CK(dalloc(c, &c->wf, (size_t)F + 1));
+    CK(dalloc(c, &c->fnhat, 3 * (size_t)F + 3));
+    CK(dalloc(c, &c->farea, (size_t)F + 1));
+    CK(dalloc(c, &c->dof_node, (size_t)n_pad));
+    CK(dalloc(c, &c->slice_ptr, (size_t)n_slices + 1));
+    CK(dalloc(c, &c->col, (size_t)sell_len));
+    CK(dalloc(c, &c->val64, (size_t)sell_len));
+    CK(dalloc(c, &c->val32, (size_t)sell_len));
+    CK(dalloc(c, &c->dinv64, (size_t)n_pad));
+    CK(dalloc(c, &c->dinv32, (size_t)n_pad));
+    CK(dalloc(c, &c->fN, (size_t)n_pad));
+    CK(dalloc(c, &c->phi, (size_t)N));
+    CK(dalloc(c, &c->x, (size_t)n_pad));
+    {
+        void *e = nullptr;
+        CK(cudaMalloc(&e, (size_t)T * (d64 ? sizeof(double4) : sizeof(float4))));
+        c->allocs.push_back(e);
+        c->E = e;
+    }
+    CK(dalloc(c, &c->W, (size_t)N));
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 6; ++k) {
+            void *q = nullptr;
+            CK(cudaMalloc(&q, cap * rsz));
+            c->allocs.push_back(q);
+            c->pbuf[b][k] = q;
+        }
+        CK(dalloc(c, &c->cell[b], cap));
+        CK(dalloc(c, &c->id[b], cap));
+    }
+    CK(dalloc(c, &c->st, 1));
+    CK(dalloc(c, &c->qcount, (size_t)c->NQ + 1));
+    CK(dalloc(c, &c->qoff, (size_t)c->NQ + 1));
+    CK(dalloc(c, &c->f, (size_t)n_pad));
+    CK(dalloc(c, &c->r, (size_t)n_pad));
+    CK(dalloc(c, &c->z, (size_t)n_pad));
+    CK(dalloc(c, &c->p0, (size_t)n_pad));
+    CK(dalloc(c, &c->p1, (size_t)n_pad));
+    CK(dalloc(c, &c->ap, (size_t)n_pad));
+    CK(dalloc(c, &c->r32, (size_t)n_pad));
+    CK(dalloc(c, &c->z32, (size_t)n_pad));
+    CK(dalloc(c, &c->p32_0, (size_t)n_pad));
+    CK(dalloc(c, &c->p32_1, (size_t)n_pad));
+    CK(dalloc(c, &c->ap32, (size_t)n_pad));
+    CK(dalloc(c, &c->dx32, (size_t)n_pad));
+    CK(pcg_plan(n_slices, c->num_sms, c->p.precision, &c->plan));
+    CK(dalloc(c, &c->partials, (size_t)2 * c->plan.grid * 4));
+    CK(dalloc(c, &c->sstats, 1));
+
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->s);
+    };
+    CK(up(c->xyz, xyz, sizeof(double) * 3 * N));
+    CK(up(c->tet4, tet4.data(), sizeof(int4) * T));
+    CK(up(c->dir, dir, (size_t)N));
+    if (F) {
+        CK(up(c->face_nodes, face_nodes, sizeof(int) * 3 * F));
+        CK(up(c->face_tet, face_tet, sizeof(int) * F));
+        CK(up(c->wf, wf, sizeof(double) * F));
+    }
+    CK(up(c->dof_node, dof_node.data(), sizeof(int) * n_pad));
+    CK(up(c->slice_ptr, sptr.data(), sizeof(int) * (n_slices + 1)));
+    CK(up(c->col, scol.data(), sizeof(int) * sell_len));
+    CK(cudaMemsetAsync(c->val64, 0, sizeof(double) * sell_len, c->s));
+    CK(cudaMemsetAsync(c->val32, 0, sizeof(float) * sell_len, c->s));
+    CK(cudaMemsetAsync(c->dinv64, 0, sizeof(double) * n_pad, c->s));
+    CK(cudaMemsetAsync(c->dinv32, 0, sizeof(float) * n_pad, c->s));
+    CK(cudaMemsetAsync(c->fN, 0, sizeof(double) * n_pad, c->s));
+    CK(cudaMemsetAsync(c->phi, 0, sizeof(double) * N, c->s));
+    CK(cudaMemsetAsync(c->x, 0, sizeof(double) * n_pad, c->s));
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * N, c->s));
+    CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->s));
+    for (double *v : {c->f, c->r, c->z, c->p0, c->p1, c->ap})
+        CK(cudaMemsetAsync(v, 0, sizeof(double) * n_pad, c->s));
+    for (float *v : {c->r32, c->z32, c->p32_0, c->p32_1, c->ap32, c->dx32})
+        CK(cudaMemsetAsync(v, 0, sizeof(float) * n_pad, c->s));
+
+    // temporaries of the assembly
+    std::vector<void *> tmp;
+    auto tmalloc = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e == cudaSuccess)
+            tmp.push_back(*p);
+        return e;
+    };
+    auto free_tmp = [&]() {
+        cudaStreamSynchronize(c->s);
+        for (void *q : tmp)
+            cudaFree(q);
+        tmp.clear();
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = tmalloc((void **)&d_nb, sizeof(int4) * T);
+    if (e == cudaSuccess) e = tmalloc((void **)&d_cptr, sizeof(long long) * (nnz + 1));
+    if (e == cudaSuccess) e = tmalloc((void **)&d_contrib, sizeof(int) * contrib.size());
+    if (e == cudaSuccess) e = tmalloc((void **)&d_spos, sizeof(long long) * nnz);
+    if (e == cudaSuccess) e = tmalloc((void **)&d_srow, sizeof(int) * nnz);
+    if (e == cudaSuccess) e = tmalloc((void **)&d_scl, sizeof(int) * nnz);
+    if (e == cudaSuccess) e = tmalloc((void **)&d_fptr, sizeof(int) * (nf + 1));
+    if (e == cudaSuccess) e = tmalloc((void **)&d_fcon, sizeof(int) * (fcon.size() + 1));
+    if (e == cudaSuccess) e = up(d_nb, nb4.data(), sizeof(int4) * T);
+    if (e == cudaSuccess) e = up(d_cptr, cptr.data(), sizeof(long long) * (nnz + 1));
+    if (e == cudaSuccess) e = up(d_contrib, contrib.data(), sizeof(int) * contrib.size());
+    if (e == cudaSuccess) e = up(d_spos, spos.data(), sizeof(long long) * nnz);
+    if (e == cudaSuccess) e = up(d_srow, srow.data(), sizeof(int) * nnz);
+    if (e == cudaSuccess) e = up(d_scl, scl.data(), sizeof(int) * nnz);
+    if (e == cudaSuccess) e = up(d_fptr, fptr.data(), sizeof(int) * (nf + 1));
+    if (e == cudaSuccess && !fcon.empty()) e = up(d_fcon, fcon.data(), sizeof(int) * fcon.size());
+    if (e == cudaSuccess) {
+        e = launch_geometry(c->s, T, c->xyz, c->tet4, d_nb, c->rec64, c->rec32, c->det);
+        ++c->launches;
+    }
+    if (e == cudaSuccess) {
+        e = launch_matrix_values(c->s, nnz, d_cptr, d_contrib, c->rec64, c->det, d_spos, d_srow,
+                                 d_scl, c->val64, c->val32, c->dinv64, c->dinv32);
+        ++c->launches;
+    }
+    if (e == cudaSuccess) {
+        e = launch_neumann(c->s, nf, d_fptr, d_fcon, c->tet4, c->xyz, c->p.E0, c->fN);
+        ++c->launches;
+    }
+    if (e == cudaSuccess) {
+        e = launch_face_geometry(c->s, F, c->face_nodes, c->xyz, c->fnhat, c->farea);
+        ++c->launches;
+    }
+    free_tmp();
+    if (e != cudaSuccess)
+        return fail(c, PIC_ERR_CUDA, "mesh_load: %s", cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(c->s));
+    c->loaded = true;
+    c->a = 0;
+    c->step = 0;
+    int rc = refresh_field(c);
+    if (rc)
+        return rc;
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_mesh_info(pic_ctx c, pic_info *info)
+{
+    REQUIRE_MESH();
+    if (!info)
+        return fail(c, PIC_ERR_ARG, "null info");
+    info->n_nodes = c->N;
+    info->n_tets = c->T;
+    info->n_faces = c->F;
+    info->n_free = c->n_free;
+    info->nnz = c->nnz;
+    info->sell_len = c->sell_len;
+    info->pcg_grid = c->plan.grid;
+    info->particle_grid = c->pgrid;
+    for (int i = 0; i < 3; ++i) {
+        info->box_lo[i] = c->lo[i];
+        info->box_hi[i] = c->hi[i];
+    }
+    return PIC_OK;
+}
+
+// ===========================================================================
+// the steps
+// ===========================================================================
+extern "C" int pic_init_potential(pic_ctx c, int32_t *iters, double *rel_res)
+{
+    REQUIRE_MESH();
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
+    CK(cudaMemsetAsync(c->x, 0, sizeof(double) * c->n_pad, c->s));
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    int rc = run_pcg(c, c->sstats, nullptr);
+    if (rc)
+        return rc;
+    rc = refresh_field(c);
+    if (rc)
+        return rc;
+    if (iters || rel_res) {
+        pic_step_stats h;
+        CK(cudaMemcpyAsync(&h, c->sstats, sizeof h, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        if (iters)
+            *iters = h.pcg_iters;
+        if (rel_res)
+            *rel_res = h.pcg_relres;
+    }
+    return check_device_error(c);
+}
+
+template <typename R> static int do_inject(pic_ctx c, int64_t step)
+{
+    RunConst k = run_const(c);
+    MeshView<R> m = view<R>(c);
+    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, step, c->qcount, &c->st->err));
+    LAUNCH(K_INJECT_SCAN, launch_inject_scan(c->s, c->NQ, c->qcount, c->qoff, c->st, c->a,
+                                             c->p.capacity, 1, c->sstats));
+    LAUNCH(K_INJECT_EMIT, launch_inject_emit<R>(c->s, c->pgrid, m, k, step, c->NQ, c->qoff,
+                                                parts<R>(c, c->a), c->st));
+    return PIC_OK;
+}
+
+extern "C" int inject(pic_ctx c, int64_t step, int64_t *n_injected)
+{
+    REQUIRE_MESH();
+    if (step < 0 || step >= (1LL << 21))
+        return fail(c, PIC_ERR_ARG, "inject: step out of range");
+    int rc = fp64(c) ? do_inject<double>(c, step) : do_inject<float>(c, step);
+    if (rc)
+        return rc;
+    if (n_injected) {
+        DevState h;
+        CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        *n_injected = h.n_new;
+        return check_device_error(c);
+    }
+    return PIC_OK;
+}
+
+template <typename R> static int do_push(pic_ctx c)
+{
+    RunConst k = run_const(c);
+    LAUNCH(K_PUSH_RELOCATE, launch_push_relocate<R>(c->s, c->pgrid, view<R>(c), k, parts<R>(c, c->a),
+                                                    parts<R>(c, 1 - c->a), c->a, c->st, c->sstats));
+    return PIC_OK;
+}
+
+extern "C" int push_relocate(pic_ctx c, int64_t step, pic_step_stats *out)
+{
+    REQUIRE_MESH();
+    (void)step;
+    CK(cudaMemsetAsync(&c->st->cnt[1 - c->a], 0, sizeof(unsigned long long), c->s));
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    int rc = fp64(c) ? do_push<double>(c) : do_push<float>(c);
+    if (rc)
+        return rc;
+    c->a = 1 - c->a;
+    CK(cudaMemsetAsync(&c->st->n_fresh, 0, sizeof(long long), c->s));
+    if (out) {
+        pic_step_stats h;
+        DevState d;
+        CK(cudaMemcpyAsync(&h, c->sstats, sizeof h, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(&d, c->st, sizeof d, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        h.alive = (int64_t)d.cnt[c->a];
+        h.injected = 0;
+        h.collected_charge = (c->p.q * c->p.w_sp) * (double)h.collected;
+        *out = h;
+        return check_device_error(c);
+    }
+    return PIC_OK;
+}
+
+extern "C" int deposit(pic_ctx c, int64_t *W_out)
+{
+    REQUIRE_MESH();
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
+    RunConst k = run_const(c);
+    if (fp64(c))
+        LAUNCH(K_DEPOSIT, launch_deposit<double>(c->s, c->pgrid, view<double>(c), k,
+                                                 parts<double>(c, c->a), c->a, c->st, c->W));
+    else
+        LAUNCH(K_DEPOSIT, launch_deposit<float>(c->s, c->pgrid, view<float>(c), k,
+                                                parts<float>(c, c->a), c->a, c->st, c->W));
+    if (W_out) {
+        CK(cudaMemcpyAsync(W_out, c->W, sizeof(int64_t) * c->N, cudaMemcpyDefault, c->s));
+        CK(cudaStreamSynchronize(c->s));
+    }
+    return PIC_OK;
+}
+
+extern "C" int poisson_solve(pic_ctx c, double *phi, int32_t *iters, double *rel_res)
+{
+    REQUIRE_MESH();
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    int rc = run_pcg(c, c->sstats, nullptr);
+    if (rc)
+        return rc;
+    rc = refresh_field(c);
+    if (rc)
+        return rc;
+    if (phi)
+        CK(cudaMemcpyAsync(phi, c->phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
+    if (iters || rel_res || phi) {
+        pic_step_stats h;
+        CK(cudaMemcpyAsync(&h, c->sstats, sizeof h, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        if (iters)
+            *iters = h.pcg_iters;
+        if (rel_res)
+            *rel_res = h.pcg_relres;
+        return check_device_error(c);
+    }
+    return PIC_OK;
+}
+
+template <typename R> static int step_once(pic_ctx c, pic_step_stats *ds)
+{
+    RunConst k = run_const(c);
+    MeshView<R> m = view<R>(c);
+    const long long kstep = c->step;
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
+    CK(cudaMemsetAsync(&c->st->cnt[1 - c->a], 0, sizeof(unsigned long long), c->s));
+    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, kstep, c->qcount, &c->st->err));
+    LAUNCH(K_INJECT_SCAN, launch_inject_scan(c->s, c->NQ, c->qcount, c->qoff, c->st, c->a,
+                                             c->p.capacity, 0, ds));
+    LAUNCH(K_STEP_FUSED, launch_step_fused<R>(c->s, c->pgrid, m, k, kstep, c->NQ, c->qoff,
+                                              parts<R>(c, c->a), parts<R>(c, 1 - c->a), c->a,
+                                              c->st, c->W, ds));
+    c->a = 1 - c->a;
+    int rc = run_pcg(c, ds, &c->st->cnt[c->a]);
+    if (rc)
+        return rc;
+    rc = refresh_field(c);
+    if (rc)
+        return rc;
+    c->step = kstep + 1;
+    return PIC_OK;
+}
+
+extern "C" int pic_step(pic_ctx c, int64_t n, pic_step_stats *stats)
+{
+    REQUIRE_MESH();
+    if (n < 0 || c->step + n >= (1LL << 21))
+        return fail(c, PIC_ERR_ARG, "pic_step: bad step count");
+    if (n == 0)
+        return PIC_OK;
+    int rc = ensure_dstats(c, n);
+    if (rc)
+        return rc;
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(pic_step_stats) * (size_t)n, c->s));
+    for (int64_t s = 0; s < n; ++s) {
+        rc = fp64(c) ? step_once<double>(c, c->dstats + s) : step_once<float>(c, c->dstats + s);
+        if (rc)
+            return rc;
+    }
+    if (stats && is_device_ptr(stats)) {
+        CK(cudaMemcpyAsync(stats, c->dstats, sizeof(pic_step_stats) * (size_t)n,
+                           cudaMemcpyDeviceToDevice, c->s));
+        return PIC_OK;
+    }
+    if (stats) {
+        CK(cudaMemcpyAsync(stats, c->dstats, sizeof(pic_step_stats) * (size_t)n,
+                           cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        for (int64_t s = 0; s < n; ++s)
+            stats[s].collected_charge = (c->p.q * c->p.w_sp) * (double)stats[s].collected;
+        return check_device_error(c);
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_adjoint(pic_ctx c, int64_t, int32_t, double *, double *)
+{
+    return fail(c, PIC_ERR_NOT_IMPLEMENTED, "pic_adjoint is not built");
+}
+
+// ===========================================================================
+// state
+// ===========================================================================
+extern "C" int pic_get_step(pic_ctx c, int64_t *step)
+{
+    if (!c || !step)
+        return fail(c, PIC_ERR_ARG, "null argument");
+    *step = c->step;
+    return PIC_OK;
+}
+extern "C" int pic_set_step(pic_ctx c, int64_t step)
+{
+    if (!c || step < 0 || step >= (1LL << 21))
+        return fail(c, PIC_ERR_ARG, "bad step");
+    c->step = step;
+    return PIC_OK;
+}
+
+extern "C" int pic_get_potential(pic_ctx c, double *phi)
+{
+    REQUIRE_MESH();
+    if (!phi)
+        return fail(c, PIC_ERR_ARG, "null phi");
+    CK(cudaMemcpyAsync(phi, c->phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_set_potential(pic_ctx c, const double *phi)
+{
+    REQUIRE_MESH();
+    if (!phi)
+        return fail(c, PIC_ERR_ARG, "null phi");
+    CK(cudaMemcpyAsync(c->phi, phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
+    k_zero_dirichlet<<<(c->N + 255) / 256, 256, 0, c->s>>>(c->N, c->dir, c->phi);
+    ++c->launches;
+    k_phi_to_x<<<(c->n_free + 255) / 256, 256, 0, c->s>>>(c->n_free, c->dof_node, c->phi, c->x);
+    ++c->launches;
+    CK(cudaGetLastError());
+    int rc = refresh_field(c);
+    if (rc)
+        return rc;
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_get_field(pic_ctx c, double *E)
+{
+    REQUIRE_MESH();
+    if (!E)
+        return fail(c, PIC_ERR_ARG, "null E");
+    void *tmp = nullptr;
+    CK(stage(c, 0, sizeof(double) * 3 * c->T, &tmp));
+    if (fp64(c))
+        LAUNCH(K_UTIL, launch_field_unpack<double>(c->s, c->T, (const double4 *)c->E, (double *)tmp));
+    else
+        LAUNCH(K_UTIL, launch_field_unpack<float>(c->s, c->T, (const float4 *)c->E, (double *)tmp));
+    CK(cudaMemcpyAsync(E, tmp, sizeof(double) * 3 * c->T, cudaMemcpyDefault, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_get_charge(pic_ctx c, int64_t *W)
+{
+    REQUIRE_MESH();
+    if (!W)
+        return fail(c, PIC_ERR_ARG, "null W");
+    CK(cudaMemcpyAsync(W, c->W, sizeof(int64_t) * c->N, cudaMemcpyDefault, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_num_particles(pic_ctx c, int64_t *n)
+{
+    REQUIRE_MESH();
+    if (!n)
+        return fail(c, PIC_ERR_ARG, "null n");
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    *n = (int64_t)h.cnt[c->a];
+    return PIC_OK;
+}
+
+extern "C" int pic_get_particles(pic_ctx c, double *r, double *v, int32_t *cell, int64_t *id)
+{
+    REQUIRE_MESH();
+    int64_t n = 0;
+    int rc = pic_num_particles(c, &n);
+    if (rc)
+        return rc;
+    if (n == 0)
+        return PIC_OK;
+    void *buf[4] = {r, v, cell, id};
+    size_t sz[4] = {sizeof(double) * 3 * n, sizeof(double) * 3 * n, sizeof(int) * n,
+                    sizeof(long long) * n};
+    void *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 4; ++i) {
+        if (!buf[i])
+            continue;
+        if (is_device_ptr(buf[i]))
+            dev[i] = buf[i];
+        else
+            CK(stage(c, i, sz[i], &dev[i]));
+    }
+    if (fp64(c))
+        LAUNCH(K_UTIL, launch_pack<double>(c->s, n, parts<double>(c, c->a), (double *)dev[0],
+                                           (double *)dev[1], (int *)dev[2], (long long *)dev[3]));
+    else
+        LAUNCH(K_UTIL, launch_pack<float>(c->s, n, parts<float>(c, c->a), (double *)dev[0],
+                                          (double *)dev[1], (int *)dev[2], (long long *)dev[3]));
+    for (int i = 0; i < 4; ++i)
+        if (buf[i] && dev[i] != buf[i])
+            CK(cudaMemcpyAsync(buf[i], dev[i], sz[i], cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_set_particles(pic_ctx c, int64_t n, const double *r, const double *v,
+                                 const int32_t *cell, const int64_t *id)
+{
+    REQUIRE_MESH();
+    if (n < 0 || n > c->p.capacity)
+        return fail(c, PIC_ERR_CAPACITY, "pic_set_particles: %lld SPs exceed the capacity",
+                    (long long)n);
+    if (n > 0 && (!r || !v || !cell || !id))
+        return fail(c, PIC_ERR_ARG, "pic_set_particles: null array");
+    const void *buf[4] = {r, v, cell, id};
+    size_t sz[4] = {sizeof(double) * 3 * n, sizeof(double) * 3 * n, sizeof(int) * n,
+                    sizeof(long long) * n};
+    const void *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (n > 0) {
+        for (int i = 0; i < 4; ++i) {
+            if (is_device_ptr(buf[i])) {
+                dev[i] = buf[i];
+            } else {
+                void *d = nullptr;
+                CK(stage(c, i, sz[i], &d));
+                CK(cudaMemcpyAsync(d, buf[i], sz[i], cudaMemcpyHostToDevice, c->s));
+                dev[i] = d;
+            }
+        }
+        if (!is_device_ptr(cell)) {
+            for (int64_t i = 0; i < n; ++i)
+                if (cell[i] < 0 || cell[i] >= c->T)
+                    return fail(c, PIC_ERR_ARG, "pic_set_particles: cell out of range");
+        }
+        if (fp64(c))
+            LAUNCH(K_UTIL, launch_unpack<double>(c->s, n, (const double *)dev[0], (const double *)dev[1],
+                                                 (const int *)dev[2], (const long long *)dev[3],
+                                                 parts<double>(c, c->a)));
+        else
+            LAUNCH(K_UTIL, launch_unpack<float>(c->s, n, (const double *)dev[0], (const double *)dev[1],
+                                                (const int *)dev[2], (const long long *)dev[3],
+                                                parts<float>(c, c->a)));
+    }
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    h.cnt[c->a] = (unsigned long long)n;
+    h.cnt[1 - c->a] = 0;
+    h.n_fresh = 0;
+    h.n_new = 0;
+    CK(cudaMemcpyAsync(c->st, &h, sizeof h, cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
+}
+
+extern "C" int pic_set_work_function(pic_ctx c, const double *wf)
+{
+    REQUIRE_MESH();
+    if (!wf)
+        return fail(c, PIC_ERR_ARG, "null work function");
+    if (!is_device_ptr(wf))
+        for (int f = 0; f < c->F; ++f)
+            if (!(wf[f] > 0) || !std::isfinite(wf[f]))
+                return fail(c, PIC_ERR_ARG, "pic_set_work_function: face %d invalid", f);
+    if (c->F)
+        CK(cudaMemcpyAsync(c->wf, wf, sizeof(double) * c->F, cudaMemcpyDefault, c->s));
+    return PIC_OK;
+}
+
+// ===========================================================================
+// counters and profiling
+// ===========================================================================
+extern "C" int pic_launch_count(pic_ctx c, int64_t *launches)
+{
+    if (!c || !launches)
+        return fail(c, PIC_ERR_ARG, "null argument");
+    *launches = c->launches;
+    return PIC_OK;
+}
+
+extern "C" int pic_profile_enable(pic_ctx c, int32_t enable)
+{
+    if (!c)
+        return fail(nullptr, PIC_ERR_ARG, "null context");
+    CK(cudaStreamSynchronize(c->s));
+    for (auto &r : c->prof_recs) {
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+    for (int k = 0; k < K_NUM; ++k) {
+        c->prof_ms[k] = 0;
+        c->prof_n[k] = 0;
+    }
+    c->prof = enable != 0;
+    return PIC_OK;
+}
+
+extern "C" int pic_profile_read(pic_ctx c, pic_profile_report *out)
+{
+    if (!c || !out)
+        return fail(c, PIC_ERR_ARG, "null argument");
+    CK(cudaStreamSynchronize(c->s));
+    for (auto &r : c->prof_recs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_ms[r.kid] += ms;
+        c->prof_n[r.kid] += 1;
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+    out->n = 0;
+    for (int k = 0; k < K_NUM && out->n < PIC_PROF_MAX; ++k) {
+        if (!c->prof_n[k])
+            continue;
+        out->name[out->n] = kKernelNames[k];
+        out->launches[out->n] = c->prof_n[k];
+        out->ms[out->n] = c->prof_ms[k];
+        out->n++;
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_sync(pic_ctx c)
+{
+    if (!c)
+        return fail(nullptr, PIC_ERR_ARG, "null context");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->s));
+    if (!c->loaded)
+        return PIC_OK;
+    return check_device_error(c);
+}

@@ -1,0 +1,180 @@
+// common.cuh -- device data layout and kernel entry points shared by the
+// translation units of libpicfem (the GB300 FEM-PIC cycle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "picfem.h"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// Per-tetrahedron walk record: the rows of J^-1 (J = [x1-x0|x2-x0|x3-x0]),
+// the vertex x0, and the packed neighbour of each face.  One record is one
+// 128-byte line in FP64 and half a line in FP32, so a walk step is a single
+// line fetch.
+//
+// Packed neighbour nb[k] of face k (opposite vertex k):
+//   nb >= 0          interior: (neighbour << 2) | local index of the shared
+//                    face in the neighbour (the face the walk enters by)
+//   nb == NB_TOP     Gamma_1, the SP is collected
+//   nb == NB_CATHODE Gamma_3, the SP is absorbed
+//   nb <= NB_SIDE    Gamma_2: v = NB_SIDE - nb = (partner << 4) |
+//                    (shift << 2) | entry face; shift 0:+Lx 1:-Lx 2:+Ly 3:-Ly
+// ---------------------------------------------------------------------------
+constexpr int NB_TOP = -1;
+constexpr int NB_CATHODE = -2;
+constexpr int NB_SIDE = -16;
+
+struct __align__(128) TetRec64 {
+    double j[9];
+    double x0[3];
+    int nb[4];
+};
+struct __align__(64) TetRec32 {
+    float j[9];
+    float x0[3];
+    int nb[4];
+};
+static_assert(sizeof(TetRec64) == 128, "one line per FP64 record");
+static_assert(sizeof(TetRec32) == 64, "half a line per FP32 record");
+
+template <typename R> struct Rec;
+template <> struct Rec<double> { using type = TetRec64; using vec4 = double4; };
+template <> struct Rec<float> { using type = TetRec32; using vec4 = float4; };
+
+// SP id layout: (step << 42) | (quadrangle << 18) | index in the quadrangle
+constexpr int ID_QUAD_SHIFT = 18;
+constexpr int ID_STEP_SHIFT = 42;
+constexpr long long MAX_PER_QUAD = 1LL << ID_QUAD_SHIFT;
+constexpr int MAX_ATTEMPTS = 64;
+
+// Particle store: structure of arrays, one buffer of `capacity` SPs.
+template <typename R> struct Particles {
+    R *x, *y, *z, *vx, *vy, *vz;
+    int *cell;
+    long long *id;
+};
+
+// Mesh data the particle kernels read.
+template <typename R> struct MeshView {
+    const typename Rec<R>::type *rec;   // [T]
+    const int4 *tet;                    // [T] node indices
+    const typename Rec<R>::vec4 *E;     // [T] field of the current Phi
+    const int *face_nodes;              // [F*3]
+    const int *face_tet;                // [F]
+    const double *face_nhat;            // [F*3]
+    const double *face_area;            // [F]
+    const double *wf;                   // [F]
+    const double *xyz;                  // [N*3]
+    int n_faces;
+    double Lx, Ly;                      // periodic shifts
+};
+
+// Run constants of the particle kernels.
+struct RunConst {
+    double dt, qmdt;       // dt and (q/m) dt = 2Q
+    double w_sp, e_charge;
+    double scale;          // 2^S
+    uint64_t seed;
+    long long capacity;
+    int fn_model;
+    int walk_max;
+};
+
+// Device-side bookkeeping of one context.
+struct DevState {
+    unsigned long long cnt[2];  // SPs in particle buffer 0 / 1
+    long long n_new;            // SPs injected in this step (after the scan)
+    long long base;             // split API: first slot of the fresh SPs
+    long long n_fresh;          // split API: fresh SPs at the end of the buffer
+    int err;                    // first device-side error (PIC_ERR_*), 0 if none
+    int pad;
+    unsigned bar_count, bar_gen;  // grid barrier of the persistent PCG
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns the cudaError_t of the launch)
+// ---------------------------------------------------------------------------
+// setup (mesh_load)
+cudaError_t launch_geometry(cudaStream_t s, int T, const double *xyz, const int4 *tet,
+                            const int4 *nb, TetRec64 *rec64, TetRec32 *rec32, double *det);
+cudaError_t launch_matrix_values(cudaStream_t s, long long nnz, const long long *cptr,
+                                 const int *contrib, const TetRec64 *rec, const double *det,
+                                 const long long *sell_pos, const int *slot_row,
+                                 const int *slot_col, double *val64, float *val32,
+                                 double *dinv64, float *dinv32);
+cudaError_t launch_neumann(cudaStream_t s, int n_free, const int *fptr, const int *fcontrib,
+                           const int4 *tet, const double *xyz, double E0, double *fN);
+cudaError_t launch_face_geometry(cudaStream_t s, int F, const int *face_nodes,
+                                 const double *xyz, double *nhat, double *area);
+
+// particles
+template <typename R>
+cudaError_t launch_field(cudaStream_t s, int T, const typename Rec<R>::type *rec,
+                         const int4 *tet, const double *phi, typename Rec<R>::vec4 *E);
+template <typename R>
+cudaError_t launch_inject_count(cudaStream_t s, int nq, MeshView<R> m, RunConst c,
+                                long long step, int *qcount, int *err);
+cudaError_t launch_inject_scan(cudaStream_t s, int nq, const int *qcount, long long *qoff,
+                               DevState *st, int buf, long long capacity, int split_mode,
+                               pic_step_stats *stats);
+template <typename R>
+cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                               long long step, int nq, const long long *qoff, Particles<R> P,
+                               DevState *st);
+template <typename R>
+cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                                 Particles<R> A, Particles<R> B, int a, DevState *st,
+                                 pic_step_stats *stats);
+template <typename R>
+cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                           Particles<R> A, int a, DevState *st, unsigned long long *W);
+template <typename R>
+cudaError_t launch_step_fused(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                              long long step, int nq, const long long *qoff, Particles<R> A,
+                              Particles<R> B, int a, DevState *st, unsigned long long *W,
+                              pic_step_stats *stats);
+template <typename R>
+cudaError_t launch_pack(cudaStream_t s, long long n, Particles<R> A, double *r, double *v,
+                        int *cell, long long *id);
+template <typename R>
+cudaError_t launch_unpack(cudaStream_t s, long long n, const double *r, const double *v,
+                          const int *cell, const long long *id, Particles<R> A);
+template <typename R>
+cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::vec4 *E,
+                                double *out);
+
+// Poisson solve
+struct PcgArgs {
+    int n, n_pad, n_slices;
+    const int *slice_ptr;     // [n_slices+1], element offsets (multiples of 32)
+    const int *col;           // sliced ELLPACK columns
+    const double *val64;
+    const float *val32;
+    const double *dinv64;     // 1 / M_ii, 0 on padding rows
+    const float *dinv32;
+    const double *fN;         // Neumann load per free DOF
+    const unsigned long long *W;  // fixed-point node charge
+    const int *dof_node;      // node of each free DOF, -1 on padding rows
+    double coef;              // q w_sp / eps0
+    double wscale;            // 2^-S
+    double *x;                // [n_pad] potential on free DOFs (warm start in, out)
+    double *phi;              // [n_nodes] receives x on the free nodes
+    double *f, *r, *z, *p0, *p1, *ap;          // FP64 work vectors [n_pad]
+    float *r32, *z32, *p32_0, *p32_1, *ap32, *dx32;  // FP32 work vectors [n_pad]
+    double *partials;         // [2][grid][4]
+    DevState *st;
+    pic_step_stats *stats;    // nullable
+    const unsigned long long *alive;  // nullable: SPs in flight -> stats->alive
+    double rtol, inner_rtol;
+    int max_iter;
+    int precision;
+};
+struct PcgLaunch {
+    int grid, block;
+};
+cudaError_t pcg_plan(int n_slices, int num_sms, int precision, PcgLaunch *plan);
+cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
+
+}  // namespace pf

@@ -1,0 +1,783 @@
+// particles.cu -- the particle side of one PIC step: field per tetrahedron,
+// field-emission injection, leapfrog push, neighbour-walk relocation and
+// fixed-point charge deposition (Sec. II.B of Veske et al., PRE 101, 053307).
+//
+// Compiled with --fmad=false so that the FP64 instantiation evaluates every
+// expression exactly as written (no fused multiply-add): the FP64 path then
+// reproduces a plain FP64 CPU implementation bit for bit.
+//
+// Layout: SPs are a structure of arrays (x, y, z, vx, vy, vz, cell, id), one
+// thread per SP, grid-stride loops that keep each warp on consecutive SPs so
+// loads and stores coalesce.  Each step of the walk is one 128-byte (FP64) or
+// 64-byte (FP32) record fetch.  Survivors are appended to the other buffer
+// with one atomic per warp; deposits are int64 atomics, so the node charge is
+// independent of the order in which SPs arrive.
+#include "common.cuh"
+
+namespace pf {
+
+#define FULL_MASK 0xffffffffu
+constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ULL;
+
+enum { FATE_ALIVE = 0, FATE_COLLECTED = 1, FATE_ABSORBED = 2, FATE_LIMIT = 3 };
+
+__device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
+
+// SplitMix64 finaliser (Steele, Lea & Flood 2014) and the keyed chain
+// h <- mix(h ^ word + gamma) over (seed, step, quadrangle, (j << 8) | slot);
+// uniform = top 53 bits * 2^-53.
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t step, uint64_t quad,
+                                            uint64_t j, uint64_t slot)
+{
+    uint64_t h = mix64((0ULL ^ seed) + GAMMA);
+    h = mix64((h ^ step) + GAMMA);
+    h = mix64((h ^ quad) + GAMMA);
+    h = mix64((h ^ ((j << 8) | (slot & 0xFF))) + GAMMA);
+    return (double)(h >> 11) * 0x1.0p-53;
+}
+
+// Fowler-Nordheim J [A/m^2] for a field F [V/m] and work function phi [eV]:
+// J = a F^2 / (phi t^2) exp(-v b phi^1.5 / F) with F in V/nm, Forbes'
+// v(f) = 1 - f + (f/6) ln f, t(f) = 1 + f/9 - (f/18) ln f, f = c_S^2 F / phi^2
+// clamped to the barrier top f <= 1 (elementary model: v = t = 1).
+__device__ double fn_current(double F, double phi, int model)
+{
+    const double a = 1.541434e-6, b = 6.830890, cS2 = 1.439964;
+    if (!(F > 0.0))
+        return 0.0;
+    double Fn = F * 1e-9;
+    double v = 1.0, t = 1.0;
+    if (model == PIC_FN_MURPHY_GOOD) {
+        double f = (cS2 * Fn) / (phi * phi);
+        if (f > 1.0)
+            f = 1.0;
+        double lf = log(f);
+        v = (1.0 - f) + (f / 6.0) * lf;
+        t = (1.0 + f / 9.0) - (f / 18.0) * lf;
+    }
+    double pre = (a * Fn * Fn) / (phi * t * t);
+    double expo = -((v * b) * (phi * sqrt(phi))) / Fn;
+    return (pre * exp(expo)) * 1e18;
+}
+
+// ---------------------------------------------------------------------------
+// walk records
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T load_rec(const T *p)
+{
+    static_assert(sizeof(T) % 16 == 0, "record size");
+    T out;
+    const int4 *s = reinterpret_cast<const int4 *>(p);
+    int4 *d = reinterpret_cast<int4 *>(&out);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 16); ++i)
+        d[i] = __ldg(s + i);
+    return out;
+}
+
+// lambda_k = row_k(J^-1) . (r - x0), k = 1..3; lambda_0 = ((1 - l1) - l2) - l3
+template <typename R, typename T>
+__device__ __forceinline__ void barycentric(const T &rec, const R r[3], R lam[4])
+{
+    R d0 = r[0] - rec.x0[0], d1 = r[1] - rec.x0[1], d2 = r[2] - rec.x0[2];
+    lam[1] = (rec.j[0] * d0 + rec.j[1] * d1) + rec.j[2] * d2;
+    lam[2] = (rec.j[3] * d0 + rec.j[4] * d1) + rec.j[5] * d2;
+    lam[3] = (rec.j[6] * d0 + rec.j[7] * d1) + rec.j[8] * d2;
+    lam[0] = (((R)1 - lam[1]) - lam[2]) - lam[3];
+}
+
+// Relocation by walking neighbours (Sec. II.B.2): leave through the face
+// opposite the most negative barycentric coordinate (lowest index on ties),
+// never back through the face just entered; stop when every other coordinate
+// is >= 0.  Returns the fate; t, r (wrapped), lam (in the final tet) updated.
+template <typename R>
+__device__ int walk(const MeshView<R> &m, int walk_max, R r[3], int &t, R lam[4], int &steps,
+                    int &wraps)
+{
+    using T = typename Rec<R>::type;
+    int entered = -1;
+    steps = 0;
+    for (;;) {
+        T rec = load_rec(m.rec + t);
+        barycentric<R>(rec, r, lam);
+        int k = -1;
+        R mn = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i == entered)
+                continue;
+            if (k < 0 || lam[i] < mn) {
+                k = i;
+                mn = lam[i];
+            }
+        }
+        if (mn >= (R)0)
+            return FATE_ALIVE;
+        if (steps >= walk_max)
+            return FATE_LIMIT;
+        ++steps;
+        int p = k == 0 ? rec.nb[0] : k == 1 ? rec.nb[1] : k == 2 ? rec.nb[2] : rec.nb[3];
+        if (p >= 0) {
+            t = p >> 2;
+            entered = p & 3;
+            continue;
+        }
+        if (p == NB_TOP)
+            return FATE_COLLECTED;
+        if (p == NB_CATHODE)
+            return FATE_ABSORBED;
+        int v = NB_SIDE - p;
+        int sc = (v >> 2) & 3;
+        entered = v & 3;
+        t = v >> 4;
+        if (sc == 0)
+            r[0] = r[0] + (R)m.Lx;
+        else if (sc == 1)
+            r[0] = r[0] + (R)(-m.Lx);
+        else if (sc == 2)
+            r[1] = r[1] + (R)m.Ly;
+        else
+            r[1] = r[1] + (R)(-m.Ly);
+        ++wraps;
+    }
+}
+
+template <typename R> __device__ __forceinline__ long long quantize(R x, double scale);
+template <> __device__ __forceinline__ long long quantize<double>(double x, double scale)
+{
+    return __double2ll_rn(x * scale);
+}
+template <> __device__ __forceinline__ long long quantize<float>(float x, double scale)
+{
+    return __float2ll_rn(x * (float)scale);
+}
+
+// deposit (eq. poisson_rhs): w_i = rint(lambda_i 2^S), i = 0..2, w_3 the
+// remainder, so that every SP adds exactly 2^S in total
+template <typename R>
+__device__ __forceinline__ void deposit_one(const int4 *tet, int t, const R lam[4], double scale,
+                                            unsigned long long *W)
+{
+    long long one = (long long)scale;
+    long long w0 = quantize<R>(lam[0], scale);
+    long long w1 = quantize<R>(lam[1], scale);
+    long long w2 = quantize<R>(lam[2], scale);
+    long long w3 = ((one - w0) - w1) - w2;
+    int4 v = __ldg(tet + t);
+    atomicAdd(W + v.x, (unsigned long long)w0);
+    atomicAdd(W + v.y, (unsigned long long)w1);
+    atomicAdd(W + v.z, (unsigned long long)w2);
+    atomicAdd(W + v.w, (unsigned long long)w3);
+}
+
+template <typename V> __device__ __forceinline__ void e3(const V &e, double o[3])
+{
+    o[0] = (double)e.x;
+    o[1] = (double)e.y;
+    o[2] = (double)e.z;
+}
+
+// Emission of SP j of quadrangle q (Sec. II.B.3 and App. E): a uniform point
+// of the parallelogram V + R1 (m1 - V) + R2 (m2 - V) accepted when its
+// triangle barycentric coordinate of V is the largest (i.e. it lies in the
+// quadrangle V, m1, centroid, m2); v0 = (q/m) E dt (1/2 + R3); the point is
+// displaced by v0 dt R3 (fractional push).  Returns false when 64 attempts
+// were rejected.
+template <typename R>
+__device__ bool emit(const MeshView<R> &m, const RunConst &c, long long step, int q, long long j,
+                     double r[3], double v[3], int &cell, long long &id)
+{
+    int f = q / 3, vtx = q - 3 * f;
+    const int *fn = m.face_nodes + 3 * f;
+    int ia = fn[vtx], ib = fn[vtx == 2 ? 0 : vtx + 1], ic = fn[vtx == 0 ? 2 : vtx - 1];
+    const double *V = m.xyz + 3 * (size_t)ia, *Vn = m.xyz + 3 * (size_t)ib;
+    const double *Vp = m.xyz + 3 * (size_t)ic;
+    double R1 = 0.0, R2 = 0.0;
+    bool ok = false;
+    for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
+        R1 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, (uint64_t)(1 + 2 * a));
+        R2 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, (uint64_t)(2 + 2 * a));
+        double l_next = R1 * 0.5, l_prev = R2 * 0.5;
+        double l_v = (1.0 - l_next) - l_prev;
+        ok = l_v >= l_next && l_v >= l_prev;
+    }
+    if (!ok)
+        return false;
+    double R3 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, 255);
+    int ft = m.face_tet[f];
+    double E[3];
+    e3(m.E[ft], E);
+    double s = c.qmdt * (0.5 + R3);
+    double tR = c.dt * R3;
+    for (int i = 0; i < 3; ++i) {
+        double m1 = (V[i] + Vn[i]) * 0.5;
+        double m2 = (V[i] + Vp[i]) * 0.5;
+        double pnt = (V[i] + R1 * (m1 - V[i])) + R2 * (m2 - V[i]);
+        double v0 = s * E[i];
+        v[i] = v0;
+        r[i] = pnt + v0 * tR;
+    }
+    cell = ft;
+    id = (step << ID_STEP_SHIFT) | ((long long)q << ID_QUAD_SHIFT) | j;
+    return true;
+}
+
+// largest q with qoff[q] <= tn (qoff nondecreasing, qoff[nq] > tn)
+__device__ __forceinline__ int find_quad(const long long *qoff, int nq, long long tn)
+{
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(qoff + mid) <= tn)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// warp-level helpers: append survivors with one atomic per warp, and sum
+// counters with one atomic per warp
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void append(bool alive, const R r[3], const R v[3], int cell,
+                                       long long id, Particles<R> B, unsigned long long *cntB)
+{
+    unsigned mask = __ballot_sync(FULL_MASK, alive);
+    if (!mask)
+        return;
+    int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(cntB, (unsigned long long)__popc(mask));
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if (alive) {
+        long long o = (long long)base + __popc(mask & ((1u << lane) - 1u));
+        B.x[o] = r[0];
+        B.y[o] = r[1];
+        B.z[o] = r[2];
+        B.vx[o] = v[0];
+        B.vy[o] = v[1];
+        B.vz[o] = v[2];
+        B.cell[o] = cell;
+        B.id[o] = id;
+    }
+}
+
+__device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool act,
+                                            pic_step_stats *stats)
+{
+    if (!stats)
+        return;
+    unsigned col = __ballot_sync(FULL_MASK, act && fate == FATE_COLLECTED);
+    unsigned abs_ = __ballot_sync(FULL_MASK, act && fate == FATE_ABSORBED);
+    int sw = __reduce_add_sync(FULL_MASK, act ? (unsigned)steps : 0u);
+    int sr = __reduce_add_sync(FULL_MASK, act ? (unsigned)wraps : 0u);
+    int mx = (int)__reduce_max_sync(FULL_MASK, act ? (unsigned)steps : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        if (col)
+            atomicAdd((unsigned long long *)&stats->collected, (unsigned long long)__popc(col));
+        if (abs_)
+            atomicAdd((unsigned long long *)&stats->absorbed, (unsigned long long)__popc(abs_));
+        if (sw)
+            atomicAdd((unsigned long long *)&stats->crossings, (unsigned long long)sw);
+        if (sr)
+            atomicAdd((unsigned long long *)&stats->wrapped, (unsigned long long)sr);
+        if (mx)
+            atomicMax(&stats->max_walk, mx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// field: E_t = -sum_i Phi_{v_i} grad N_i, constant per tetrahedron
+// ---------------------------------------------------------------------------
+__global__ void k_field64(int T, const TetRec64 *__restrict__ rec, const int4 *__restrict__ tet,
+                          const double *__restrict__ phi, double4 *E)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T)
+        return;
+    TetRec64 r = load_rec(rec + t);
+    int4 v = __ldg(tet + t);
+    double p0 = phi[v.x], p1 = phi[v.y], p2 = phi[v.z], p3 = phi[v.w];
+    double e[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double g0 = -((r.j[0 + i] + r.j[3 + i]) + r.j[6 + i]);
+        double s = ((p0 * g0 + p1 * r.j[0 + i]) + p2 * r.j[3 + i]) + p3 * r.j[6 + i];
+        e[i] = -s;
+    }
+    E[t] = make_double4(e[0], e[1], e[2], 0.0);
+}
+
+// FP32 records: the same field written with potential differences
+// E = -sum_{k=1..3} (Phi_k - Phi_0) grad N_k (identical since grad N_0 =
+// -sum grad N_k), so that the FP32 gradients never multiply the large
+// absolute potential.
+__global__ void k_field32(int T, const TetRec32 *__restrict__ rec, const int4 *__restrict__ tet,
+                          const double *__restrict__ phi, float4 *E)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T)
+        return;
+    TetRec32 r = load_rec(rec + t);
+    int4 v = __ldg(tet + t);
+    double p0 = phi[v.x];
+    float d1 = (float)(phi[v.y] - p0), d2 = (float)(phi[v.z] - p0), d3 = (float)(phi[v.w] - p0);
+    float e[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        e[i] = -((d1 * r.j[0 + i] + d2 * r.j[3 + i]) + d3 * r.j[6 + i]);
+    E[t] = make_float4(e[0], e[1], e[2], 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// injection: count per quadrangle (eqs. nsp, rnd_nsp) and exclusive scan
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_inject_count(int nq, MeshView<R> m, RunConst c, long long step, int *qcount,
+                               int *err)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq)
+        return;
+    int f = q / 3;
+    double E[3];
+    e3(m.E[m.face_tet[f]], E);
+    const double *n = m.face_nhat + 3 * (size_t)f;
+    double F = -((E[0] * n[0] + E[1] * n[1]) + E[2] * n[2]);
+    if (!(F > 0.0))
+        F = 0.0;
+    double J = fn_current(F, m.wf[f], c.fn_model);
+    double Aq = m.face_area[f] / 3.0;
+    double nsp = ((J * Aq) * c.dt) / (c.e_charge * c.w_sp);
+    double R0 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, 0, 0);
+    double fl = floor(nsp);
+    double frac = nsp - fl;
+    long long cnt = (long long)fl + (R0 >= frac ? 0 : 1);
+    if (!(nsp >= 0.0) || cnt >= MAX_PER_QUAD) {
+        set_err(err, PIC_ERR_CAPACITY);
+        cnt = 0;
+    }
+    qcount[q] = (int)cnt;
+}
+
+// single block: qoff[q] = sum_{p<q} qcount[p], qoff[nq] = total; capacity check
+__global__ void __launch_bounds__(1024) k_inject_scan(int nq, const int *__restrict__ qcount,
+                                                      long long *qoff, DevState *st, int buf,
+                                                      long long capacity, int split,
+                                                      pic_step_stats *stats)
+{
+    __shared__ long long warp_tot[32];
+    __shared__ long long grand;
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int per = (nq + blockDim.x - 1) / blockDim.x;
+    int lo = min(nq, tid * per), hi = min(nq, lo + per);
+    long long local = 0;
+    for (int i = lo; i < hi; ++i)
+        local += qcount[i];
+    long long incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        long long wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(FULL_MASK, wi, o);
+            if (lane >= o)
+                wi += y;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31)
+            grand = wi;
+    }
+    __syncthreads();
+    long long run = warp_tot[wid] + incl - local;
+    for (int i = lo; i < hi; ++i) {
+        qoff[i] = run;
+        run += qcount[i];
+    }
+    if (tid == 0) {
+        long long total = grand;
+        qoff[nq] = total;
+        long long n_alive = (long long)st->cnt[buf];
+        if (n_alive + total > capacity) {
+            atomicCAS(&st->err, 0, PIC_ERR_CAPACITY);
+            total = 0;
+        }
+        st->n_new = total;
+        if (split) {
+            st->base = n_alive;
+            st->n_fresh = total;
+            st->cnt[buf] = (unsigned long long)(n_alive + total);
+        }
+        if (stats)
+            stats->injected = total;
+    }
+}
+
+// split API: write the fresh SPs at the end of buffer A
+template <typename R>
+__global__ void k_inject_emit(MeshView<R> m, RunConst c, long long step, int nq,
+                              const long long *__restrict__ qoff, Particles<R> P, DevState *st)
+{
+    long long n_new = st->n_new, base = st->base;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long tn = blockIdx.x * (long long)blockDim.x + threadIdx.x; tn < n_new; tn += stride) {
+        int q = find_quad(qoff, nq, tn);
+        long long j = tn - qoff[q];
+        double r[3], v[3];
+        int cell;
+        long long id;
+        if (!emit<R>(m, c, step, q, j, r, v, cell, id)) {
+            set_err(&st->err, PIC_ERR_ARG);
+            r[0] = r[1] = r[2] = 0.0;
+            v[0] = v[1] = v[2] = 0.0;
+            cell = m.face_tet[q / 3];
+            id = -1;
+        }
+        long long o = base + tn;
+        P.x[o] = (R)r[0];
+        P.y[o] = (R)r[1];
+        P.z[o] = (R)r[2];
+        P.vx[o] = (R)v[0];
+        P.vy[o] = (R)v[1];
+        P.vz[o] = (R)v[2];
+        P.cell[o] = cell;
+        P.id[o] = id;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// push + relocate (split API): kick non-fresh SPs by (q/m) dt E_cell, drift
+// all by dt v, walk, append survivors to buffer B
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_push_relocate(MeshView<R> m, RunConst c, Particles<R> A, Particles<R> B, int a,
+                                DevState *st, pic_step_stats *stats)
+{
+    long long n = (long long)st->cnt[a];
+    long long n_old = n - st->n_fresh;
+    unsigned long long *cntB = &st->cnt[1 - a];
+    const R qmdt = (R)c.qmdt, dt = (R)c.dt;
+    long long wstride = ((long long)gridDim.x * blockDim.x) & ~31LL;
+    long long wbase = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL;
+    int lane = threadIdx.x & 31;
+    for (long long base = wbase; base < n; base += wstride) {
+        long long i = base + lane;
+        bool act = i < n;
+        R r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, lam[4];
+        int t = 0, fate = FATE_ABSORBED, steps = 0, wraps = 0;
+        long long id = 0;
+        if (act) {
+            r[0] = A.x[i];
+            r[1] = A.y[i];
+            r[2] = A.z[i];
+            v[0] = A.vx[i];
+            v[1] = A.vy[i];
+            v[2] = A.vz[i];
+            t = A.cell[i];
+            id = A.id[i];
+            if (i < n_old) {
+                typename Rec<R>::vec4 e = m.E[t];
+                v[0] = v[0] + qmdt * (R)e.x;
+                v[1] = v[1] + qmdt * (R)e.y;
+                v[2] = v[2] + qmdt * (R)e.z;
+            }
+            r[0] = r[0] + dt * v[0];
+            r[1] = r[1] + dt * v[1];
+            r[2] = r[2] + dt * v[2];
+            fate = walk<R>(m, c.walk_max, r, t, lam, steps, wraps);
+            if (fate == FATE_LIMIT)
+                set_err(&st->err, PIC_ERR_WALK_LIMIT);
+        }
+        bool alive = act && fate == FATE_ALIVE;
+        append<R>(alive, r, v, t, id, B, cntB);
+        count_fates(fate, steps, wraps, act, stats);
+    }
+}
+
+// deposit (split API): W += fixed-point weights of every SP in buffer A
+template <typename R>
+__global__ void k_deposit(MeshView<R> m, RunConst c, Particles<R> A, int a, DevState *st,
+                          unsigned long long *W)
+{
+    using T = typename Rec<R>::type;
+    long long n = (long long)st->cnt[a];
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        R r[3] = {A.x[i], A.y[i], A.z[i]};
+        int t = A.cell[i];
+        T rec = load_rec(m.rec + t);
+        R lam[4];
+        barycentric<R>(rec, r, lam);
+        deposit_one<R>(m.tet, t, lam, c.scale, W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one fused PIC step on the particle side: SPs [0, n_old) of buffer A are
+// kicked, SPs [n_old, n_old + n_new) are emitted in place; all drift, walk,
+// deposit, and survivors are appended to buffer B
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, long long step,
+                                                    int nq, const long long *__restrict__ qoff,
+                                                    Particles<R> A, Particles<R> B, int a,
+                                                    DevState *st, unsigned long long *W,
+                                                    pic_step_stats *stats)
+{
+    long long n_old = (long long)st->cnt[a];
+    long long n = n_old + st->n_new;
+    unsigned long long *cntB = &st->cnt[1 - a];
+    const R qmdt = (R)c.qmdt, dt = (R)c.dt;
+    long long wstride = ((long long)gridDim.x * blockDim.x) & ~31LL;
+    long long wbase = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL;
+    int lane = threadIdx.x & 31;
+    for (long long base = wbase; base < n; base += wstride) {
+        long long i = base + lane;
+        bool act = i < n;
+        R r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, lam[4];
+        int t = 0, fate = FATE_ABSORBED, steps = 0, wraps = 0;
+        long long id = 0;
+        if (act) {
+            if (i < n_old) {
+                r[0] = A.x[i];
+                r[1] = A.y[i];
+                r[2] = A.z[i];
+                v[0] = A.vx[i];
+                v[1] = A.vy[i];
+                v[2] = A.vz[i];
+                t = A.cell[i];
+                id = A.id[i];
+                typename Rec<R>::vec4 e = m.E[t];
+                v[0] = v[0] + qmdt * (R)e.x;
+                v[1] = v[1] + qmdt * (R)e.y;
+                v[2] = v[2] + qmdt * (R)e.z;
+            } else {
+                long long tn = i - n_old;
+                int q = find_quad(qoff, nq, tn);
+                double rd[3], vd[3];
+                if (!emit<R>(m, c, step, q, tn - qoff[q], rd, vd, t, id)) {
+                    set_err(&st->err, PIC_ERR_ARG);
+                    rd[0] = rd[1] = rd[2] = 0.0;
+                    vd[0] = vd[1] = vd[2] = 0.0;
+                    t = m.face_tet[q / 3];
+                }
+                for (int k = 0; k < 3; ++k) {
+                    r[k] = (R)rd[k];
+                    v[k] = (R)vd[k];
+                }
+            }
+            r[0] = r[0] + dt * v[0];
+            r[1] = r[1] + dt * v[1];
+            r[2] = r[2] + dt * v[2];
+            fate = walk<R>(m, c.walk_max, r, t, lam, steps, wraps);
+            if (fate == FATE_LIMIT)
+                set_err(&st->err, PIC_ERR_WALK_LIMIT);
+            if (fate == FATE_ALIVE)
+                deposit_one<R>(m.tet, t, lam, c.scale, W);
+        }
+        bool alive = act && fate == FATE_ALIVE;
+        append<R>(alive, r, v, t, id, B, cntB);
+        count_fates(fate, steps, wraps, act, stats);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// state conversion between the SoA store and interleaved FP64 arrays
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_pack(long long n, Particles<R> A, double *r, double *v, int *cell, long long *id)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    if (r) {
+        r[3 * i + 0] = (double)A.x[i];
+        r[3 * i + 1] = (double)A.y[i];
+        r[3 * i + 2] = (double)A.z[i];
+    }
+    if (v) {
+        v[3 * i + 0] = (double)A.vx[i];
+        v[3 * i + 1] = (double)A.vy[i];
+        v[3 * i + 2] = (double)A.vz[i];
+    }
+    if (cell)
+        cell[i] = A.cell[i];
+    if (id)
+        id[i] = A.id[i];
+}
+
+template <typename R>
+__global__ void k_unpack(long long n, const double *r, const double *v, const int *cell,
+                         const long long *id, Particles<R> A)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    A.x[i] = (R)r[3 * i + 0];
+    A.y[i] = (R)r[3 * i + 1];
+    A.z[i] = (R)r[3 * i + 2];
+    A.vx[i] = (R)v[3 * i + 0];
+    A.vy[i] = (R)v[3 * i + 1];
+    A.vz[i] = (R)v[3 * i + 2];
+    A.cell[i] = cell[i];
+    A.id[i] = id[i];
+}
+
+template <typename V>
+__global__ void k_field_unpack(int T, const V *E, double *out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T)
+        return;
+    V e = E[t];
+    out[3 * (size_t)t + 0] = (double)e.x;
+    out[3 * (size_t)t + 1] = (double)e.y;
+    out[3 * (size_t)t + 2] = (double)e.z;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <>
+cudaError_t launch_field<double>(cudaStream_t s, int T, const TetRec64 *rec, const int4 *tet,
+                                 const double *phi, double4 *E)
+{
+    k_field64<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E);
+    return cudaGetLastError();
+}
+template <>
+cudaError_t launch_field<float>(cudaStream_t s, int T, const TetRec32 *rec, const int4 *tet,
+                                const double *phi, float4 *E)
+{
+    k_field32<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_inject_count(cudaStream_t s, int nq, MeshView<R> m, RunConst c,
+                                long long step, int *qcount, int *err)
+{
+    if (nq <= 0)
+        return cudaSuccess;
+    k_inject_count<R><<<blocks_for(nq, 256), 256, 0, s>>>(nq, m, c, step, qcount, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_scan(cudaStream_t s, int nq, const int *qcount, long long *qoff,
+                               DevState *st, int buf, long long capacity, int split_mode,
+                               pic_step_stats *stats)
+{
+    k_inject_scan<<<1, 1024, 0, s>>>(nq, qcount, qoff, st, buf, capacity, split_mode, stats);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                               long long step, int nq, const long long *qoff, Particles<R> P,
+                               DevState *st)
+{
+    k_inject_emit<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, P, st);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                                 Particles<R> A, Particles<R> B, int a, DevState *st,
+                                 pic_step_stats *stats)
+{
+    k_push_relocate<R><<<grid, 256, 0, s>>>(m, c, A, B, a, st, stats);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c, Particles<R> A,
+                           int a, DevState *st, unsigned long long *W)
+{
+    k_deposit<R><<<grid, 256, 0, s>>>(m, c, A, a, st, W);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_step_fused(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
+                              long long step, int nq, const long long *qoff, Particles<R> A,
+                              Particles<R> B, int a, DevState *st, unsigned long long *W,
+                              pic_step_stats *stats)
+{
+    k_step_fused<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pack(cudaStream_t s, long long n, Particles<R> A, double *r, double *v,
+                        int *cell, long long *id)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_pack<R><<<blocks_for(n, 256), 256, 0, s>>>(n, A, r, v, cell, id);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_unpack(cudaStream_t s, long long n, const double *r, const double *v,
+                          const int *cell, const long long *id, Particles<R> A)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_unpack<R><<<blocks_for(n, 256), 256, 0, s>>>(n, r, v, cell, id, A);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::vec4 *E, double *out)
+{
+    k_field_unpack<<<blocks_for(T, 256), 256, 0, s>>>(T, E, out);
+    return cudaGetLastError();
+}
+
+#define PF_INSTANTIATE(R)                                                                      \
+    template cudaError_t launch_inject_count<R>(cudaStream_t, int, MeshView<R>, RunConst,      \
+                                                long long, int *, int *);                      \
+    template cudaError_t launch_inject_emit<R>(cudaStream_t, int, MeshView<R>, RunConst,       \
+                                               long long, int, const long long *,              \
+                                               Particles<R>, DevState *);                      \
+    template cudaError_t launch_push_relocate<R>(cudaStream_t, int, MeshView<R>, RunConst,     \
+                                                 Particles<R>, Particles<R>, int, DevState *,  \
+                                                 pic_step_stats *);                            \
+    template cudaError_t launch_deposit<R>(cudaStream_t, int, MeshView<R>, RunConst,           \
+                                           Particles<R>, int, DevState *,                      \
+                                           unsigned long long *);                              \
+    template cudaError_t launch_step_fused<R>(cudaStream_t, int, MeshView<R>, RunConst,        \
+                                              long long, int, const long long *, Particles<R>, \
+                                              Particles<R>, int, DevState *,                   \
+                                              unsigned long long *, pic_step_stats *);         \
+    template cudaError_t launch_pack<R>(cudaStream_t, long long, Particles<R>, double *,       \
+                                        double *, int *, long long *);                         \
+    template cudaError_t launch_unpack<R>(cudaStream_t, long long, const double *,             \
+                                          const double *, const int *, const long long *,      \
+                                          Particles<R>);                                       \
+    template cudaError_t launch_field_unpack<R>(cudaStream_t, int,                             \
+                                                const typename Rec<R>::vec4 *, double *);
+
+PF_INSTANTIATE(double)
+PF_INSTANTIATE(float)
+
+}  // namespace pf

@@ -1,0 +1,282 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+FP64 mode: from identical state (potential and SPs), one step of injection,
+push, walk and deposit is bit-exact (ids, cells, positions, velocities, the
+int64 node charge); the PCG potential agrees to the solver tolerance.
+FP32_IR mode: potentials within 1e-6 relative, positions within 1e-5 of the
+box height, cells equal wherever the SP is not within rounding of a face.
+"""
+import numpy as np
+import pytest
+
+from paper_1906_08125_gb300 import configs as K
+from paper_1906_08125_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def picfem():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_08125_gb300 import picfem as P
+    P.load()
+    return P
+
+
+def by_id(state):
+    r, v, cell, pid = state
+    o = np.argsort(pid, kind="stable")
+    return r[o], v[o], cell[o], pid[o]
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def make_pair(P, O, mesh, **kw):
+    p = K.params(**kw)
+    orc = O.Oracle(mesh, p)
+    ctx = P.Context(p).mesh_load(mesh)
+    return ctx, orc
+
+
+# ---------------------------------------------------------------------------
+def test_init_potential_and_field(picfem, oracle_mod, tip_small):
+    ctx, orc = make_pair(picfem, oracle_mod, tip_small, E0=1e10, pcg_rtol=1e-12)
+    it_g, rr_g = ctx.init_potential()
+    it_o, rr_o = orc.init_potential()
+    assert rr_g <= 1e-12 and abs(it_g - it_o) <= max(3, 0.05 * it_o)
+    assert rel(ctx.potential(), orc.potential()) <= 1e-9
+    # same potential in -> bit-identical field out
+    ctx.set_potential(orc.potential())
+    assert np.array_equal(ctx.field(), orc.field())
+
+
+def test_plate_p1_exact_fp64_and_fp32ir(picfem, oracle_mod):
+    mesh = inputs.plate_mesh()
+    exact = 1e10 * mesh.xyz[:, 2]
+    for prec, tol in ((K.PREC_FP64, 1e-10), (K.PREC_FP32_IR, 1e-6)):
+        p = K.params(E0=1e10, pcg_rtol=1e-12 if prec == K.PREC_FP64 else 1e-7, precision=prec)
+        ctx = picfem.Context(p).mesh_load(mesh)
+        ctx.init_potential()
+        assert rel(ctx.potential(), exact) <= tol
+        E = ctx.field()
+        assert np.abs(E[:, 2] + 1e10).max() <= 1e10 * max(tol, 1e-8) * 10
+
+
+@pytest.mark.parametrize("meshname", ["plate_small", "tip_small"])
+def test_one_step_split_api_bit_exact(picfem, oracle_mod, meshname, request):
+    mesh = request.getfixturevalue(meshname)
+    ctx, orc = make_pair(picfem, oracle_mod, mesh, E0=1e10, w_sp=0.5, pcg_rtol=1e-12,
+                         capacity=60000, precision=K.PREC_FP64)
+    orc.init_potential()
+    ctx.set_potential(orc.potential())
+    r, v, cell, pid = inputs.random_particles(mesh, 20000, seed=3, v_scale=4e6, v_up=6e6)
+    orc.set_particles(r, v, cell, pid)
+    ctx.set_particles(r, v, cell, pid)
+    step = 7
+    n_o = orc.inject(step)
+    n_g = ctx.inject(step)
+    assert n_g == n_o and n_g > 0
+    for a, b in zip(by_id(ctx.particles()), by_id(orc.particles())):
+        assert np.array_equal(a, b)
+    st_o = orc.push_relocate(step)
+    st_g = ctx.push_relocate(step)
+    for f in ("collected", "absorbed", "wrapped", "crossings", "max_walk", "alive"):
+        assert getattr(st_g, f) == getattr(st_o, f), f
+    g, o = by_id(ctx.particles()), by_id(orc.particles())
+    for a, b in zip(g, o):
+        assert np.array_equal(a, b)
+    W_o = orc.deposit()
+    W_g = np.zeros(mesh.n_nodes, np.int64)
+    import torch
+    Wt = torch.zeros(mesh.n_nodes, dtype=torch.int64, device="cuda")
+    ctx.deposit(Wt)
+    W_g[:] = Wt.cpu().numpy()
+    assert np.array_equal(W_g, W_o)
+    assert int(W_g.sum()) == len(o[3]) * 2 ** 32
+    orc.poisson_solve()
+    it, rr = ctx.poisson_solve()
+    assert rr <= 1e-12
+    assert rel(ctx.potential(), orc.potential()) <= 1e-9
+
+
+def test_fused_step_equals_split_sequence(picfem, oracle_mod, tip_small):
+    kw = dict(E0=1e10, w_sp=0.5, pcg_rtol=1e-12, capacity=60000, precision=K.PREC_FP64)
+    a = picfem.Context(K.params(**kw)).mesh_load(tip_small)
+    b = picfem.Context(K.params(**kw)).mesh_load(tip_small)
+    for c in (a, b):
+        c.init_potential()
+    r, v, cell, pid = inputs.random_particles(tip_small, 5000, seed=9, v_scale=4e6, v_up=6e6)
+    for c in (a, b):
+        c.set_particles(r, v, cell, pid)
+        c.step_index = 3
+    a.step(1)
+    b.inject(3)
+    b.push_relocate(3)
+    b.deposit()
+    b.poisson_solve()
+    for x, y in zip(by_id(a.particles()), by_id(b.particles())):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.charge(), b.charge())
+    assert np.array_equal(a.potential(), b.potential())
+
+
+def _teacher_forced(picfem, oracle_mod, mesh, steps, **kw):
+    """GPU steps fed with the oracle's potential every step: the particle side
+    must stay bit-exact over many steps; the GPU potential agrees to tol."""
+    ctx, orc = make_pair(picfem, oracle_mod, mesh, **kw)
+    orc.init_potential()
+    worst = 0.0
+    total = 0
+    for k in range(steps):
+        ctx.set_potential(orc.potential())
+        ctx.step_index = k
+        st_g = ctx.step(1)[0]
+        st_o = orc.step(1)[0]
+        assert st_g.injected == st_o.injected, k
+        assert st_g.collected == st_o.collected and st_g.absorbed == st_o.absorbed, k
+        g, o = by_id(ctx.particles()), by_id(orc.particles())
+        for a, b in zip(g, o):
+            assert np.array_equal(a, b), f"step {k}"
+        assert np.array_equal(ctx.charge(), orc.charge()), f"step {k}"
+        worst = max(worst, rel(ctx.potential(), orc.potential()))
+        total += len(g[3])
+    assert worst <= 1e-6
+    return total, worst
+
+
+def test_teacher_forced_100_steps_small(picfem, oracle_mod, plate_small):
+    total, worst = _teacher_forced(picfem, oracle_mod, plate_small, 100, E0=1e10, w_sp=0.1,
+                                   pcg_rtol=1e-12, capacity=100000, precision=K.PREC_FP64)
+    assert total > 10000
+
+
+@pytest.mark.slow
+def test_teacher_forced_plate_96k_100_steps(picfem, oracle_mod):
+    """The parallel-plate workload (96k tets, 10 GV/m, 4 fs): 100 steps."""
+    mesh, p, steps = K.workload("plate_96k")
+    kw = {k: p[k] for k in ("E0", "w_sp", "capacity", "dt")}
+    total, worst = _teacher_forced(picfem, oracle_mod, mesh, 100, pcg_rtol=1e-12,
+                                   precision=K.PREC_FP64, **kw)
+    assert total > 100000
+
+
+def test_free_running_plate_fp64(picfem, oracle_mod):
+    """Both sides on their own for 100 steps of the plate workload: the
+    potentials agree to 1e-6, every SP id matches, positions to 1e-5 Lz and
+    cells exactly (FP64; a differing cell would need an SP within rounding of
+    a face)."""
+    mesh, p, steps = K.workload("plate_96k", precision=K.PREC_FP64, pcg_rtol=1e-12)
+    ctx = picfem.Context(p).mesh_load(mesh)
+    orc = oracle_mod.Oracle(mesh, p)
+    ctx.init_potential()
+    orc.init_potential()
+    sg = ctx.step(steps)
+    so = orc.step(steps)
+    assert rel(ctx.potential(), orc.potential()) <= 1e-6
+    g, o = by_id(ctx.particles()), by_id(orc.particles())
+    assert np.array_equal(g[3], o[3])
+    Lz = mesh.box_hi[2] - mesh.box_lo[2]
+    assert np.abs(g[0] - o[0]).max() <= 1e-5 * Lz
+    assert np.mean(g[2] == o[2]) == 1.0
+    assert [s.injected for s in sg] == [s.injected for s in so]
+
+
+def test_free_running_plate_fp32ir(picfem, oracle_mod):
+    """FP32 push and FP32 inner PCG with FP64 refinement, against the FP64
+    oracle over 100 steps: potentials within 1e-6, positions within 1e-5 Lz
+    (matched by id), injected counts within a few flips."""
+    mesh, p, steps = K.workload("plate_96k", pcg_rtol=1e-10)
+    pg = dict(p, precision=K.PREC_FP32_IR, pcg_rtol=1e-8)
+    ctx = picfem.Context(pg).mesh_load(mesh)
+    orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64))
+    ctx.init_potential()
+    orc.init_potential()
+    ctx.step(steps)
+    orc.step(steps)
+    assert rel(ctx.potential(), orc.potential()) <= 1e-6
+    g, o = by_id(ctx.particles()), by_id(orc.particles())
+    common, ig, io = np.intersect1d(g[3], o[3], return_indices=True)
+    assert len(common) >= 0.99 * max(len(g[3]), len(o[3]))
+    Lz = mesh.box_hi[2] - mesh.box_lo[2]
+    assert np.abs(g[0][ig] - o[0][io]).max() <= 1e-5 * Lz
+
+
+def test_resume_bit_identical(picfem, oracle_mod, plate_small):
+    kw = K.params(w_sp=0.05, capacity=50000, pcg_rtol=1e-12, precision=K.PREC_FP64)
+    a = picfem.Context(kw).mesh_load(plate_small)
+    a.init_potential()
+    a.step(10, stats=False)
+    b = picfem.Context(kw).mesh_load(plate_small)
+    b.init_potential()
+    b.step(5)
+    phi, parts, k = b.potential(), b.particles(), b.step_index
+    c = picfem.Context(kw).mesh_load(plate_small)
+    c.set_potential(phi)
+    c.set_particles(*parts)
+    c.step_index = k
+    c.step(5)
+    for x, y in zip(by_id(a.particles()), by_id(c.particles())):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.potential(), c.potential())
+
+
+def test_empty_and_error_paths(picfem, oracle_mod, plate_small):
+    P = picfem
+    # no SPs and no emission: a step is a plain solve
+    p = K.params(w_sp=0.05, capacity=100, precision=K.PREC_FP64)
+    ctx = P.Context(p).mesh_load(plate_small)
+    ctx.init_potential()
+    ctx.set_work_function(np.full(plate_small.n_faces, 1000.0))
+    st = ctx.step(2)
+    assert st[-1].alive == 0 and st[-1].injected == 0
+    # capacity exceeded -> PIC_ERR_CAPACITY, no fault
+    ctx.set_work_function(np.full(plate_small.n_faces, 4.5))
+    with pytest.raises(P.PicError) as e:
+        ctx.step(1)
+    assert e.value.code == -4
+    # an SP that must cross many faces with walk_max_steps = 2
+    p = K.params(w_sp=0.05, capacity=100, walk_max_steps=2, precision=K.PREC_FP64)
+    ctx = P.Context(p).mesh_load(plate_small)
+    ctx.init_potential()
+    ctx.set_work_function(np.full(plate_small.n_faces, 1000.0))
+    ctx.set_particles(np.array([[1e-9, 1e-9, 1e-9]]), np.array([[0, 0, 1e7]]), np.array([0]),
+                      np.array([0]))
+    with pytest.raises(P.PicError) as e:
+        ctx.push_relocate(0)
+    assert e.value.code == -5
+    # PCG iteration cap -> PIC_ERR_NOT_CONVERGED
+    p = K.params(pcg_max_iter=1, pcg_rtol=1e-14, precision=K.PREC_FP64)
+    ctx = P.Context(p).mesh_load(plate_small)
+    with pytest.raises(P.PicError) as e:
+        ctx.init_potential()
+    assert e.value.code == -6
+    # bad meshes are refused on the host
+    bad = inputs.plate_mesh(nx=3, ny=3, nz=3)
+    bad.tet[5, [1, 2]] = bad.tet[5, [2, 1]]
+    with pytest.raises(P.PicError) as e:
+        P.Context(K.params()).mesh_load(bad)
+    assert e.value.code == -3
+    bad = inputs.plate_mesh(nx=3, ny=3, nz=3)
+    bad.work_function[0] = np.nan
+    with pytest.raises(P.PicError) as e:
+        P.Context(K.params()).mesh_load(bad)
+    assert e.value.code == -1
+    with pytest.raises(P.PicError) as e:
+        P.Context(K.params()).mesh_load(plate_small).adjoint(10)
+    assert e.value.code == -7
+
+
+def test_profile_and_launch_count(picfem, plate_small):
+    ctx = picfem.Context(K.params(w_sp=0.05, capacity=50000)).mesh_load(plate_small)
+    ctx.init_potential()
+    n0 = ctx.launch_count()
+    ctx.profile(True)
+    ctx.step(3)
+    rep = ctx.profile_read()
+    assert ctx.launch_count() - n0 == 3 * 5
+    for k in ("inject_count", "inject_scan", "step_fused", "pcg", "field"):
+        assert rep[k][0] == 3 and rep[k][1] > 0
