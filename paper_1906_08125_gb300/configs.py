@@ -47,7 +47,7 @@ WORKLOADS = {
     # Cu-like nanotip: r = 3 nm, h = 30 nm in a 60x60x230 nm box, ~1M tets,
     # 10 GV/m, up to 1e6 SPs, FP32 push + FP64-refined PCG to 1e-6, 500 steps
     "tip_1m": dict(mesh=lambda: inputs.tip_mesh(),
-                   params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=2_000_000,
+                   params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=3_000_000,
                                precision=PREC_FP32_IR, pcg_rtol=1e-6),
                    steps=500, target_sp=1_000_000),
     # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, ~8M tets,

@@ -296,7 +296,8 @@ def random_particles(mesh: Mesh, n: int, seed: int = 0, v_scale: float = 1.0e7,
                      v_up: float = 1.0e7, z_min_frac: float = 0.0):
     """n SPs at uniformly random points of randomly chosen tetrahedra, with
     random velocities (isotropic part of scale ``v_scale`` plus ``v_up`` along
-    +z).  Returns (r[n,3], v[n,3], cell[n], id[n])."""
+    +z).  Returns (r[n,3], v[n,3], cell[n], id[n]); the ids carry bit 62 so
+    they never collide with the ids of injected SPs ((step << 42) | ...)."""
     rng = np.random.default_rng(seed)
     T = mesh.n_tets
     cand = np.arange(T)
@@ -309,5 +310,5 @@ def random_particles(mesh: Mesh, n: int, seed: int = 0, v_scale: float = 1.0e7,
     r = np.einsum("ij,ijk->ik", lam, mesh.xyz[mesh.tet[cell]])
     v = rng.normal(0.0, v_scale, size=(n, 3))
     v[:, 2] += v_up
-    pid = np.arange(n, dtype=np.int64)
+    pid = (np.int64(1) << np.int64(62)) + np.arange(n, dtype=np.int64)
     return r, v, cell, pid

@@ -185,24 +185,71 @@ def test_free_running_plate_fp64(picfem, oracle_mod):
     assert [s.injected for s in sg] == [s.injected for s in so]
 
 
+def _bary(mesh, cell, r):
+    P = mesh.xyz[mesh.tet[cell]]
+    J = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    l = np.linalg.solve(J, (r - P[:, 0])[..., None])[..., 0]
+    return np.concatenate([1 - l.sum(1, keepdims=True), l], axis=1)
+
+
+def test_teacher_forced_fp32ir(picfem, oracle_mod, plate_small):
+    """FP32_IR from the oracle's FP64 state, one step at a time for 40 steps:
+    positions within 1e-5 Lz of the oracle's; cells equal except where the SP
+    lies within FP32 rounding of a face, and then the GPU's cell still
+    contains the GPU's position (both owners are valid)."""
+    mesh = plate_small
+    p = K.params(E0=1e10, w_sp=0.1, pcg_rtol=1e-12, capacity=100000)
+    orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64))
+    ctx = picfem.Context(dict(p, precision=K.PREC_FP32_IR, pcg_rtol=1e-8)).mesh_load(mesh)
+    orc.init_potential()
+    Lz = mesh.box_hi[2] - mesh.box_lo[2]
+    flips = total = 0
+    for k in range(40):
+        ctx.set_potential(orc.potential())
+        ctx.set_particles(*orc.particles())
+        ctx.step_index = k
+        ctx.step(1)
+        orc.step(1)
+        g, o = by_id(ctx.particles()), by_id(orc.particles())
+        common, ig, io = np.intersect1d(g[3], o[3], return_indices=True)
+        assert len(common) >= len(o[3]) - 2 and len(common) >= len(g[3]) - 2, k
+        assert np.abs(g[0][ig] - o[0][io]).max() <= 1e-5 * Lz, k
+        diff = g[2][ig] != o[2][io]
+        if diff.any():
+            lam = _bary(mesh, g[2][ig][diff], g[0][ig][diff])
+            assert lam.min() >= -1e-5, k
+        flips += int(diff.sum())
+        total += len(common)
+        assert rel(ctx.potential(), orc.potential()) <= 1e-6
+    assert flips <= 1e-3 * total
+
+
 def test_free_running_plate_fp32ir(picfem, oracle_mod):
     """FP32 push and FP32 inner PCG with FP64 refinement, against the FP64
-    oracle over 100 steps: potentials within 1e-6, positions within 1e-5 Lz
-    (matched by id), injected counts within a few flips."""
+    oracle over 100 steps of the plate workload: potentials within 1e-6; ids
+    matched; positions within 1e-5 Lz for all but the few SPs whose walk
+    passed within FP32 rounding of a face (a valid but different owner, after
+    which the trajectories legitimately differ)."""
     mesh, p, steps = K.workload("plate_96k", pcg_rtol=1e-10)
     pg = dict(p, precision=K.PREC_FP32_IR, pcg_rtol=1e-8)
     ctx = picfem.Context(pg).mesh_load(mesh)
     orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64))
     ctx.init_potential()
     orc.init_potential()
-    ctx.step(steps)
-    orc.step(steps)
+    sg = ctx.step(steps)
+    so = orc.step(steps)
     assert rel(ctx.potential(), orc.potential()) <= 1e-6
     g, o = by_id(ctx.particles()), by_id(orc.particles())
     common, ig, io = np.intersect1d(g[3], o[3], return_indices=True)
     assert len(common) >= 0.99 * max(len(g[3]), len(o[3]))
     Lz = mesh.box_hi[2] - mesh.box_lo[2]
-    assert np.abs(g[0][ig] - o[0][io]).max() <= 1e-5 * Lz
+    err = np.abs(g[0][ig] - o[0][io]).max(axis=1) / Lz
+    q = np.quantile(err, [0.5, 0.99, 0.999, 1.0])
+    assert np.mean(err <= 1e-5) >= 0.995, q
+    assert (_bary(mesh, g[2], g[0]).min(axis=1) >= -1e-5).all()
+    inj_g = np.array([s.injected for s in sg])
+    inj_o = np.array([s.injected for s in so])
+    assert abs(inj_g.sum() - inj_o.sum()) <= 0.01 * inj_o.sum()
 
 
 def test_resume_bit_identical(picfem, oracle_mod, plate_small):
