@@ -246,6 +246,39 @@ int pic_profile_read(pic_ctx ctx, pic_profile_report *out); /* synchronises */
 /* Wait for all queued work; returns the first device-side error, if any. */
 int pic_sync(pic_ctx ctx);
 
+/*
+ * pic_pcg_solve_static: Jacobi-preconditioned CG on a caller-supplied sparse
+ * symmetric positive definite system A x = b that allocates no device memory
+ * (the paper has no counterpart; this serves callers of the library, not the
+ * method).  It is for callers that cannot call cudaMalloc -- an application
+ * that runs inside a device arena it manages itself, or under an allocator
+ * that is locked or budgeted elsewhere -- and so cannot create a pic_ctx.
+ * The caller passes every input and output; the solver's work vectors live
+ * in one file-scope device array of PIC_STATIC_MAX_ROWS rows (about 10 MiB)
+ * that each GPU loading the library holds until the process exits.
+ *   n                     rows, 1 <= n <= PIC_STATIC_MAX_ROWS (else PIC_ERR_ARG,
+ *                         nothing is launched)
+ *   rowptr[n+1], col[nnz] DEVICE int32 CSR pattern (0-based; the diagonal
+ *                         must be stored)
+ *   val[nnz], b[n]        DEVICE double
+ *   x[n]                  DEVICE double: initial guess in, solution out
+ *   rtol, max_iter        stop when ||b - A x||_2 <= rtol ||b||_2 (recursive
+ *                         residual), PIC_ERR_NOT_CONVERGED at max_iter
+ *   iters, rel_res        HOST, nullable
+ *   stream                cudaStream_t (NULL = legacy default stream)
+ * The call synchronises `stream`.  The first call on a device, with that
+ * device current, looks up the device address of the scratch array and the
+ * resident grid size; make that first call before any stream capture.  All
+ * calls on a device share the scratch array (each clears the words that must
+ * start at zero): calls whose kernels overlap on the GPU race, so serialise
+ * them.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA, PIC_ERR_NOT_CONVERGED,
+ * PIC_ERR_TIMEOUT; the message is in pic_last_error(NULL).
+ */
+#define PIC_STATIC_MAX_ROWS 262144
+int pic_pcg_solve_static(int32_t n, const int32_t *rowptr, const int32_t *col,
+                         const double *val, const double *b, double *x, double rtol,
+                         int32_t max_iter, int32_t *iters, double *rel_res, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

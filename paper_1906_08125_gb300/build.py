@@ -26,6 +26,7 @@ UNITS = {
     "particles.cu": ["--fmad=false"],
     "pcg.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 

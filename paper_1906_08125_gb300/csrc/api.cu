@@ -372,6 +372,8 @@ int ensure_dstats(pic_ctx c, long long n)
 
 }  // namespace
 
+void pf::set_global_error(const char *msg) { g_err = msg; }
+
 // ===========================================================================
 // context
 // ===========================================================================

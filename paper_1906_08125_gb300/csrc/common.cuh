@@ -174,6 +174,9 @@ struct PcgArgs {
 struct PcgLaunch {
     int grid, block;
 };
+// message returned by pic_last_error(NULL)
+void set_global_error(const char *msg);
+
 cudaError_t pcg_plan(int n_slices, int num_sms, int precision, PcgLaunch *plan);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
 

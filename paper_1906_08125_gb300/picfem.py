@@ -26,7 +26,8 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_
             "pic_step", "pic_adjoint", "pic_get_step", "pic_set_step", "pic_get_potential",
             "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
             "pic_get_particles", "pic_set_particles", "pic_set_work_function",
-            "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync"]
+            "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync",
+            "pic_pcg_solve_static"]
 
 
 class Params(C.Structure):
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = True):
         "pic_profile_enable": [P, I32],
         "pic_profile_read": [P, C.POINTER(ProfileReport)],
         "pic_sync": [P],
+        "pic_pcg_solve_static": [I32, P, P, P, P, P, D, I32, C.POINTER(I32), C.POINTER(D), P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
