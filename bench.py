@@ -185,7 +185,8 @@ def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True
     prec = K.PREC_FP32_IR if precision == "fp32_ir" else K.PREC_FP64
     mesh, p, _ = K.workload(args.workload, precision=prec, seed=rank)
     if prec == K.PREC_FP64:
-        p = dict(p, pcg_rtol=1e-6)
+        # the plain FP64 form: FP64 throughout, Jacobi-PCG
+        p = dict(p, pcg_rtol=1e-6, pcg_cheb_degree=0)
     target = K.WORKLOADS[args.workload]["target_sp"]
     stream = torch.cuda.current_stream()
     ctx = picfem.Context(p, stream=stream).mesh_load(mesh)

@@ -82,10 +82,23 @@ typedef struct {
     int32_t walk_max_steps;/* face crossings per SP per step -> PIC_ERR_WALK_LIMIT */
     int32_t quant_bits;    /* S: deposit weights in units of 2^-S, 1 <= S <= 40 */
     int32_t precision;     /* PIC_PREC_*                                        */
-    int32_t reserved;
-    double ir_inner_rtol;  /* FP32_IR: inner FP32 PCG reduces its residual by
-                              this factor per refinement (e.g. 1e-3)           */
+    int32_t pcg_variant;   /* FP32_IR inner solver: PIC_PCG_STANDARD or
+                              PIC_PCG_PIPELINED                                 */
+    double ir_inner_rtol;  /* FP32_IR: the most the inner FP32 PCG is asked to
+                              reduce its residual in one refinement (e.g. 1e-4);
+                              it stops earlier once the FP64 target is met     */
+    int32_t ir_inner_max_iter; /* FP32_IR: inner iterations per refinement
+                              before the FP64 residual is recomputed (0 = no cap) */
+    int32_t pcg_cheb_degree;   /* preconditioner: <= 1 Jacobi; k >= 2 Chebyshev
+                              polynomial of degree k in D^-1 M (k - 1 extra SpMVs
+                              per CG iteration, no extra reductions)             */
+    double pcg_cheb_ratio;     /* Chebyshev interval [b / ratio, b], b the
+                              Gershgorin bound of D^-1 M (e.g. 30)               */
 } pic_params;
+
+/* inner solver of the FP32_IR Poisson solve */
+#define PIC_PCG_STANDARD 0   /* two grid reductions per iteration            */
+#define PIC_PCG_PIPELINED 1  /* one (Ghysels & Vanroose 2014), less accurate  */
 
 typedef struct {
     int64_t injected;         /* SPs injected in the step                      */

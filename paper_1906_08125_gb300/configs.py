@@ -21,19 +21,23 @@ Q_ELECTRON = -E_CHARGE
 Q_OVER_M = Q_ELECTRON / M_E     # C/kg
 
 PREC_FP64, PREC_FP32_IR = 0, 1
+PCG_STANDARD, PCG_PIPELINED = 0, 1
 FN_MURPHY_GOOD, FN_ELEMENTARY = 0, 1
 
 
 def params(dt=4e-15, E0=1e10, w_sp=1.0, pcg_rtol=1e-12, pcg_max_iter=20000,
            fn_model=FN_MURPHY_GOOD, seed=0, capacity=20000, walk_max_steps=4096,
-           quant_bits=32, precision=PREC_FP64, ir_inner_rtol=1e-3):
+           quant_bits=32, precision=PREC_FP64, ir_inner_rtol=1e-4, pcg_variant=0,
+           ir_inner_max_iter=0, pcg_cheb_degree=0, pcg_cheb_ratio=30.0):
     """Run parameters shared by the CUDA library and the oracle."""
     return dict(dt=float(dt), E0=float(E0), w_sp=float(w_sp), q=Q_ELECTRON,
                 q_over_m=Q_OVER_M, eps0=EPS0, e_charge=E_CHARGE,
                 pcg_rtol=float(pcg_rtol), pcg_max_iter=int(pcg_max_iter),
                 fn_model=int(fn_model), seed=int(seed), capacity=int(capacity),
                 walk_max_steps=int(walk_max_steps), quant_bits=int(quant_bits),
-                precision=int(precision), ir_inner_rtol=float(ir_inner_rtol))
+                precision=int(precision), ir_inner_rtol=float(ir_inner_rtol),
+                pcg_variant=int(pcg_variant), ir_inner_max_iter=int(ir_inner_max_iter),
+                pcg_cheb_degree=int(pcg_cheb_degree), pcg_cheb_ratio=float(pcg_cheb_ratio))
 
 
 # name -> (mesh factory, parameter overrides, steps, target SP count)
@@ -48,7 +52,7 @@ WORKLOADS = {
     # 10 GV/m, up to 1e6 SPs, FP32 push + FP64-refined PCG to 1e-6, 500 steps
     "tip_1m": dict(mesh=lambda: inputs.tip_mesh(),
                    params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=3_000_000,
-                               precision=PREC_FP32_IR, pcg_rtol=1e-6),
+                               precision=PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=4),
                    steps=500, target_sp=1_000_000),
     # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, ~8M tets,
     # 8 GV/m, work function 4.5 +/- 0.1 eV per face, 1e7 SPs, 200 steps

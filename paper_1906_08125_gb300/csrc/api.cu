@@ -60,6 +60,7 @@ struct pic_ctx_s {
     int *face_nodes = nullptr, *face_tet = nullptr;
     double *wf = nullptr, *fnhat = nullptr, *farea = nullptr;
     int *dof_node = nullptr, *slice_ptr = nullptr, *col = nullptr;
+    int *lcol = nullptr, *halo_ptr = nullptr, *halo_idx = nullptr;
     double *val64 = nullptr, *dinv64 = nullptr, *fN = nullptr;
     float *val32 = nullptr, *dinv32 = nullptr;
     // state
@@ -77,6 +78,9 @@ struct pic_ctx_s {
     double *f = nullptr, *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *ap = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32_0 = nullptr, *p32_1 = nullptr, *ap32 = nullptr,
           *dx32 = nullptr;
+    double *d0 = nullptr, *d1 = nullptr;
+    float *d32_0 = nullptr, *d32_1 = nullptr;
+    double cheb_b = 2.0;   // Gershgorin bound of D^-1 M
     double *partials = nullptr;
     PcgLaunch plan{};
     pic_step_stats *dstats = nullptr;  // per-step stats of pic_step
@@ -343,6 +347,21 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
     g.inner_rtol = c->p.ir_inner_rtol;
     g.max_iter = c->p.pcg_max_iter;
     g.precision = c->p.precision;
+    g.max_rows = c->plan.max_rows;
+    g.max_chunk = c->plan.max_chunk;
+    g.variant = c->p.pcg_variant;
+    g.lcol = c->lcol;
+    g.halo_ptr = c->halo_ptr;
+    g.halo_idx = c->halo_idx;
+    g.max_local = c->plan.max_local;
+    g.cheb_degree = c->p.pcg_cheb_degree;
+    g.cheb_b = c->cheb_b;
+    g.cheb_a = c->p.pcg_cheb_degree >= 2 ? c->cheb_b / c->p.pcg_cheb_ratio : 0.0;
+    g.d0 = c->d0;
+    g.d1 = c->d1;
+    g.d32_0 = c->d32_0;
+    g.d32_1 = c->d32_1;
+    g.inner_max = c->p.ir_inner_max_iter;
     CK(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->s));
     LAUNCH(K_PCG, launch_pcg(c->s, c->plan, g));
     return PIC_OK;
@@ -393,7 +412,10 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         q.capacity < 1 || q.walk_max_steps < 1 || q.quant_bits < 1 || q.quant_bits > 40 ||
         (q.precision != PIC_PREC_FP64 && q.precision != PIC_PREC_FP32_IR) ||
         (q.fn_model != PIC_FN_MURPHY_GOOD && q.fn_model != PIC_FN_ELEMENTARY) ||
-        (q.precision == PIC_PREC_FP32_IR && !(q.ir_inner_rtol > 0 && q.ir_inner_rtol < 1)))
+        (q.precision == PIC_PREC_FP32_IR && !(q.ir_inner_rtol > 0 && q.ir_inner_rtol < 1)) ||
+        (q.pcg_variant != PIC_PCG_STANDARD && q.pcg_variant != PIC_PCG_PIPELINED) ||
+        q.ir_inner_max_iter < 0 || q.pcg_cheb_degree < 0 || q.pcg_cheb_degree > 32 ||
+        (q.pcg_cheb_degree >= 2 && !(q.pcg_cheb_ratio > 1.0)))
         return fail(nullptr, PIC_ERR_ARG, "pic_create: invalid parameters");
     c = new pic_ctx_s();
     c->p = q;
@@ -787,8 +809,28 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     CK(dalloc(c, &c->p32_1, (size_t)n_pad));
     CK(dalloc(c, &c->ap32, (size_t)n_pad));
     CK(dalloc(c, &c->dx32, (size_t)n_pad));
-    CK(pcg_plan(n_slices, c->num_sms, c->p.precision, &c->plan));
+    CK(dalloc(c, &c->d0, (size_t)n_pad));
+    CK(dalloc(c, &c->d1, (size_t)n_pad));
+    CK(dalloc(c, &c->d32_0, (size_t)n_pad));
+    CK(dalloc(c, &c->d32_1, (size_t)n_pad));
+    PcgHalo halo;
+    c->lcol = c->halo_ptr = c->halo_idx = nullptr;
+    CK(pcg_plan(sptr.data(), scol.data(), n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
+                &c->plan, &halo));
     CK(dalloc(c, &c->partials, (size_t)2 * c->plan.grid * 4));
+    if (c->plan.resident) {
+        CK(dalloc(c, &c->lcol, halo.lcol.size()));
+        CK(dalloc(c, &c->halo_ptr, halo.halo_ptr.size()));
+        CK(dalloc(c, &c->halo_idx, halo.halo_idx.size() + 1));
+        CK(cudaMemcpyAsync(c->lcol, halo.lcol.data(), sizeof(int) * halo.lcol.size(),
+                           cudaMemcpyHostToDevice, c->s));
+        CK(cudaMemcpyAsync(c->halo_ptr, halo.halo_ptr.data(), sizeof(int) * halo.halo_ptr.size(),
+                           cudaMemcpyHostToDevice, c->s));
+        if (!halo.halo_idx.empty())
+            CK(cudaMemcpyAsync(c->halo_idx, halo.halo_idx.data(),
+                               sizeof(int) * halo.halo_idx.size(), cudaMemcpyHostToDevice, c->s));
+        CK(cudaStreamSynchronize(c->s));
+    }
     CK(dalloc(c, &c->sstats, 1));
 
     auto up = [&](void *dst, const void *src, size_t bytes) {
@@ -816,7 +858,9 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->s));
     for (double *v : {c->f, c->r, c->z, c->p0, c->p1, c->ap})
         CK(cudaMemsetAsync(v, 0, sizeof(double) * n_pad, c->s));
-    for (float *v : {c->r32, c->z32, c->p32_0, c->p32_1, c->ap32, c->dx32})
+    for (double *v : {c->d0, c->d1})
+        CK(cudaMemsetAsync(v, 0, sizeof(double) * n_pad, c->s));
+    for (float *v : {c->r32, c->z32, c->p32_0, c->p32_1, c->ap32, c->dx32, c->d32_0, c->d32_1})
         CK(cudaMemsetAsync(v, 0, sizeof(float) * n_pad, c->s));
 
     // temporaries of the assembly
@@ -871,6 +915,23 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     if (e != cudaSuccess)
         return fail(c, PIC_ERR_CUDA, "mesh_load: %s", cudaGetErrorString(e));
     CK(cudaStreamSynchronize(c->s));
+    {
+        // Gershgorin bound of the Jacobi-scaled matrix: max_i sum_j |M_ij| / M_ii
+        std::vector<double> hv((size_t)sell_len), hd((size_t)n_pad);
+        CK(cudaMemcpy(hv.data(), c->val64, sizeof(double) * sell_len, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(hd.data(), c->dinv64, sizeof(double) * n_pad, cudaMemcpyDeviceToHost));
+        double bmax = 0.0;
+        for (int sl = 0; sl < n_slices; ++sl) {
+            int w = (sptr[sl + 1] - sptr[sl]) / 32;
+            for (int l = 0; l < 32; ++l) {
+                double sum = 0.0;
+                for (int k = 0; k < w; ++k)
+                    sum += std::fabs(hv[(size_t)sptr[sl] + (size_t)k * 32 + l]);
+                bmax = std::max(bmax, sum * hd[(size_t)sl * 32 + l]);
+            }
+        }
+        c->cheb_b = bmax > 0.0 ? bmax : 2.0;
+    }
     c->loaded = true;
     c->a = 0;
     c->step = 0;

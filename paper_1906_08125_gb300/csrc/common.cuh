@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "picfem.h"
 
 namespace pf {
@@ -170,14 +172,38 @@ struct PcgArgs {
     double rtol, inner_rtol;
     int max_iter;
     int precision;
+    int max_rows;             // resident kernels: see PcgLaunch
+    long long max_chunk;
+    int variant;              // FP32_IR inner solver (PIC_PCG_*)
+    int inner_max;            // FP32_IR inner iterations per refinement (0 = no cap)
+    const int *lcol;          // resident kernels: block-local column of every stored entry
+    const int *halo_ptr;      // [grid+1] first halo column of each block
+    const int *halo_idx;      // global rows of the halo columns, sorted per block
+    int max_local;            // most own rows + halo columns of one block
+    int cheb_degree;          // <= 1: Jacobi; k >= 2: Chebyshev polynomial preconditioner
+    double cheb_a, cheb_b;    // Chebyshev interval of D^-1 M
+    double *d0, *d1;          // FP64 halo buffers of the Chebyshev steps [n_pad]
+    float *d32_0, *d32_1;     // FP32 halo buffers of the Chebyshev steps [n_pad]
 };
 struct PcgLaunch {
     int grid, block;
+    int resident;          // 1: rows owned in registers, own segments in shared memory
+    int rpt;               // resident: row slots per thread (1, 2, 4 or 8)
+    int smem_matrix;       // resident: the block's matrix slices live in shared memory
+    size_t smem_bytes;     // resident: dynamic shared memory per block
+    int max_rows;          // resident: 32 * most slices owned by one block
+    long long max_chunk;   // resident: most stored matrix entries owned by one block
+    int max_local;         // resident: most own rows + halo columns of one block
+};
+// Host-side tables of the resident kernels: local column indices and halos.
+struct PcgHalo {
+    std::vector<int> lcol, halo_ptr, halo_idx;
 };
 // message returned by pic_last_error(NULL)
 void set_global_error(const char *msg);
 
-cudaError_t pcg_plan(int n_slices, int num_sms, int precision, PcgLaunch *plan);
+cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slices,
+                     int num_sms, int precision, int variant, PcgLaunch *plan, PcgHalo *halo);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
 
 }  // namespace pf

@@ -22,6 +22,8 @@
 //
 // The grid barrier waits with an iteration limit: a block that waits too
 // long records PIC_ERR_TIMEOUT and the whole kernel returns.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace pf {
@@ -42,31 +44,27 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
     return *(const volatile int *)p;
 }
 
-// Grid-wide barrier over co-resident blocks (cooperative launch).  Returns
-// false when the wait ran out or another block already failed.
+// Grid-wide barrier over co-resident blocks (cooperative launch), one
+// atomic per block: block 0 adds 2^31 - (G - 1), every other block adds 1,
+// so the counter's top bit flips exactly when the last block arrives and the
+// low bits return to zero (the counter is cleared before each launch).  Each
+// block waits for the flip with an iteration limit; a block that waits too
+// long records PIC_ERR_TIMEOUT and the whole kernel returns.
 __device__ bool grid_sync(DevState *st)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned g = ld_acquire_u32(&st->bar_gen);
+        unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
         __threadfence();
-        unsigned arrived = atomicAdd(&st->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire_u32(&st->bar_gen) == g) {
-                if (++spins > SPIN_LIMIT) {
-                    atomicCAS(&st->err, 0, PIC_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 32)
-                    __nanosleep(40);
+        unsigned old = atomicAdd(&st->bar_count, inc);
+        long long spins = 0;
+        while (((old ^ ld_acquire_u32(&st->bar_count)) & 0x80000000u) == 0) {
+            if (++spins > SPIN_LIMIT) {
+                atomicCAS(&st->err, 0, PIC_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -89,11 +87,11 @@ __device__ __forceinline__ double warp_sum(double v)
 // Sum NV per-thread values over the whole grid; out[] identical in every
 // block.  `set` alternates between calls so a fast block never overwrites
 // partials a slow block has not read yet.
-template <int NV>
+template <int NV, int WARPS = PCG_WARPS>
 __device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevState *st,
                          double (&out)[NV])
 {
-    __shared__ double red[PCG_WARPS][NV];
+    __shared__ double red[WARPS][NV];
     __shared__ double res[NV];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -105,7 +103,7 @@ __device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevSt
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < PCG_WARPS; ++w)
+        for (int w = 0; w < WARPS; ++w)
             s += red[w][threadIdx.x];
         partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = s;
     }
@@ -394,8 +392,723 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
     finish(a, it, sqrt(rr64) / sqrt(ff), status, outer);
 }
 
-cudaError_t pcg_plan(int n_slices, int num_sms, int precision, PcgLaunch *plan)
+// ===========================================================================
+// Resident kernels.  Each block owns a contiguous range of slices (rows in
+// Morton order: a compact piece of the mesh) and keeps its rows' vectors in
+// registers for the whole solve.  The vectors the SpMV reads live in shared
+// memory as [own rows | halo], where the halo is the sorted list of columns
+// owned by other blocks that the block's rows reference; the block's stored
+// column indices are rewritten to these local positions on the host.  Each
+// SpMV phase first copies the halo values from global memory (independent
+// loads, all in flight together) and then reads shared memory only.  When
+// the block's matrix slices fit, they are copied into shared memory once per
+// solve as well.
+// ===========================================================================
+constexpr int RB = 512;         // threads per resident block
+constexpr int RW = RB / 32;     // warps per resident block
+
+struct Seg {
+    int s0, s1, row0, nrows;
+    int e0;                     // first stored entry of the block's slices
+    int h0, nh;                 // the block's halo in halo_idx
+};
+
+__device__ __forceinline__ Seg block_seg(const PcgArgs &a)
 {
+    long long G = gridDim.x, b = blockIdx.x;
+    Seg g;
+    g.s0 = (int)((b * a.n_slices) / G);
+    g.s1 = (int)(((b + 1) * a.n_slices) / G);
+    g.row0 = g.s0 * 32;
+    g.nrows = (g.s1 - g.s0) * 32;
+    g.e0 = a.slice_ptr[g.s0];
+    g.h0 = a.halo_ptr[b];
+    g.nh = a.halo_ptr[b + 1] - g.h0;
+    return g;
+}
+
+// copy the block's stored entries [e0, e1) into shared memory
+template <typename T>
+__device__ __forceinline__ void stage_chunk(T *dst, const T *src, int e0, int e1)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(src + e0);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    int n16 = (int)(((long long)(e1 - e0) * sizeof(T)) / 16);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x)
+        d[i] = __ldg(s + i);
+}
+
+// halo values of a vector published in global memory by the other blocks
+template <typename V>
+__device__ __forceinline__ void stage_halo(V *s, const V *glob, const PcgArgs &a, const Seg &g)
+{
+    for (int i = threadIdx.x; i < g.nh; i += blockDim.x)
+        s[g.nrows + i] = __ldcg(glob + a.halo_idx[g.h0 + i]);
+}
+
+// per-thread row slots
+template <int RPT> struct Rows {
+    int row[RPT], o[RPT], le[RPT], ge[RPT], wd[RPT];
+    bool ok[RPT];
+};
+
+template <int RPT, bool SM>
+__device__ __forceinline__ void init_rows(Rows<RPT> &t, const PcgArgs &a, const Seg &g)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        int s = g.s0 + w + k * RW;
+        t.ok[k] = s < g.s1;
+        t.row[k] = s * 32 + lane;
+        t.o[k] = t.row[k] - g.row0;
+        t.le[k] = t.ge[k] = t.wd[k] = 0;
+        if (!t.ok[k])
+            continue;
+        int b0 = a.slice_ptr[s], b1 = a.slice_ptr[s + 1];
+        t.wd[k] = (b1 - b0) >> 5;
+        t.ge[k] = b0 + lane;
+        t.le[k] = (SM ? b0 - g.e0 : b0) + lane;
+    }
+}
+
+// sum_j A_ij v_j of row slot k from shared memory; LC = local columns
+// (shared memory when SM, else global), VAL = matrix values
+template <int RPT, typename MV, typename V, typename ACC>
+__device__ __forceinline__ ACC spmv_local(const Rows<RPT> &t, int k, const int *LC, const MV *VAL,
+                                          bool val_by_global, const V *sv)
+{
+    ACC sum = 0;
+#pragma unroll 4
+    for (int c = 0; c < t.wd[k]; ++c) {
+        int lc = LC[t.le[k] + c * 32];
+        MV v = val_by_global ? __ldg(VAL + t.ge[k] + c * 32) : VAL[t.le[k] + c * 32];
+        sum += (ACC)v * (ACC)sv[lc];
+    }
+    return sum;
+}
+
+// z = M^-1 r for the preconditioner.  Jacobi: z = D^-1 r.  Chebyshev of
+// degree k: z = p_k(D^-1 M) D^-1 r, computed as k steps of the Chebyshev
+// iteration for M y = r from y = 0 on the interval [a, b] (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 12.1).  This is a fixed symmetric
+// positive definite operator as long as b bounds the spectrum of D^-1 M
+// (Gershgorin), so CG stays CG.  Each step after the first needs one SpMV of
+// the step direction: published to the block's shared segment and to a
+// double-buffered global halo copy, one plain grid barrier, no reduction.
+template <int RPT, typename T>
+__device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
+                              const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT],
+                              T (&z)[RPT], T *s_d0, T *s_d1, T *g_d0, T *g_d1)
+{
+    if (a.cheb_degree < 2) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            z[k] = dinv[k] * r[k];
+        return true;
+    }
+    const double theta = 0.5 * (a.cheb_b + a.cheb_a), delta = 0.5 * (a.cheb_b - a.cheb_a);
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    T rc[RPT], d[RPT];
+    const T inv_theta = (T)(1.0 / theta);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        rc[k] = r[k];
+        d[k] = dinv[k] * rc[k] * inv_theta;
+        z[k] = (T)0;
+    }
+    for (int j = 1;; ++j) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            z[k] = z[k] + d[k];
+        if (j >= a.cheb_degree)
+            break;
+        T *s_d = (j & 1) ? s_d1 : s_d0;
+        T *g_d = (j & 1) ? g_d1 : g_d0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            s_d[t.o[k]] = d[k];
+            g_d[t.row[k]] = d[k];
+        }
+        if (!grid_sync(a.st))
+            return false;
+        stage_halo(s_d, (const T *)g_d, a, g);
+        __syncthreads();
+        double rho_new = 1.0 / (2.0 * sigma - rho);
+        const T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / delta);
+        rho = rho_new;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            T ad = 0;
+#pragma unroll 4
+            for (int c = 0; c < t.wd[k]; ++c) {
+                int lc = LC[t.le[k] + c * 32];
+                ad += VAL[t.le[k] + c * 32] * s_d[lc];
+            }
+            rc[k] = rc[k] - ad;
+            d[k] = c1 * d[k] + c2 * (dinv[k] * rc[k]);
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Jacobi-PCG (the plain FP64 form), two grid barriers per iteration
+// ---------------------------------------------------------------------------
+template <int RPT, bool SM>
+__global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Seg g = block_seg(a);
+    double *s_val = (double *)smem;
+    int *s_lc = (int *)(smem + (SM ? a.max_chunk * 8 : 0));
+    size_t off = SM ? (size_t)a.max_chunk * 12 : 0;
+    off = (off + 15) & ~(size_t)15;
+    double *s_z = (double *)(smem + off);
+    double *s_p0 = s_z + a.max_local;
+    double *s_p1 = s_p0 + a.max_local;
+    double *s_d0 = s_p1 + a.max_local;
+    double *s_d1 = s_d0 + a.max_local;
+    if (SM) {
+        int e1 = a.slice_ptr[g.s1];
+        stage_chunk(s_val, a.val64, g.e0, e1);
+        stage_chunk(s_lc, a.lcol, g.e0, e1);
+    }
+    const int *LC = SM ? s_lc : a.lcol;
+    const double *VAL = SM ? s_val : a.val64;
+    Rows<RPT> t;
+    init_rows<RPT, SM>(t, a, g);
+    double x[RPT], r[RPT], z[RPT], p[RPT], ap[RPT], dinv[RPT], f[RPT];
+    // r = f - M x: x of the own rows into s_z, halo of x staged
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        x[k] = r[k] = z[k] = p[k] = ap[k] = dinv[k] = f[k] = 0.0;
+        if (!t.ok[k])
+            continue;
+        x[k] = a.x[t.row[k]];
+        dinv[k] = a.dinv64[t.row[k]];
+        f[k] = rhs_entry(a, t.row[k]);
+        s_z[t.o[k]] = x[k];
+    }
+    stage_halo(s_z, a.x, a, g);
+    __syncthreads();
+    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        double axv = spmv_local<RPT, double, double, double>(t, k, LC, VAL, false, s_z);
+        r[k] = f[k] - axv;
+        acc[1] += r[k] * r[k];
+        acc[2] += f[k] * f[k];
+    }
+    __syncthreads();
+    if (!apply_precond<RPT, double>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
+        return;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        acc[0] += r[k] * z[k];
+        s_z[t.o[k]] = z[k];
+        s_p0[t.o[k]] = 0.0;
+        a.z[t.row[k]] = z[k];
+        a.p0[t.row[k]] = 0.0;
+    }
+    int set = 0;
+    if (!grid_sum<3, RW>(acc, a.partials, set, a.st, tot))
+        return;
+    set ^= 1;
+    double rz = tot[0], rr = tot[1], ff = tot[2];
+    int it = 0, status = 0;
+    if (ff == 0.0) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            x[k] = 0.0;
+        rr = 0.0;
+        ff = 1.0;
+    }
+    const double tol = a.rtol * sqrt(ff);
+    double beta = 0.0;
+    int cur = 0;
+    while (sqrt(rr) > tol) {
+        if (it >= a.max_iter) {
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
+        double *sp_old = cur ? s_p1 : s_p0;
+        double *sp_new = cur ? s_p0 : s_p1;
+        const double *gp_old = cur ? a.p1 : a.p0;
+        double *gp_new = cur ? a.p0 : a.p1;
+        stage_halo(s_z, a.z, a, g);
+        stage_halo(sp_old, gp_old, a, g);
+        __syncthreads();
+        double pap[1] = {0.0}, pt[1];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            double sum = 0.0;
+#pragma unroll 4
+            for (int c = 0; c < t.wd[k]; ++c) {
+                int lc = LC[t.le[k] + c * 32];
+                sum += VAL[t.le[k] + c * 32] * (s_z[lc] + beta * sp_old[lc]);
+            }
+            p[k] = z[k] + beta * p[k];
+            ap[k] = sum;
+            sp_new[t.o[k]] = p[k];
+            gp_new[t.row[k]] = p[k];
+            pap[0] += p[k] * sum;
+        }
+        if (!grid_sum<1, RW>(pap, a.partials, set, a.st, pt))
+            return;
+        set ^= 1;
+        double alpha = rz / pt[0];
+        double acc2[2] = {0.0, 0.0}, t2[2];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            x[k] = x[k] + alpha * p[k];
+            r[k] = r[k] - alpha * ap[k];
+        }
+        if (!apply_precond<RPT, double>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
+            return;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            s_z[t.o[k]] = z[k];
+            a.z[t.row[k]] = z[k];
+            acc2[0] += r[k] * z[k];
+            acc2[1] += r[k] * r[k];
+        }
+        if (!grid_sum<2, RW>(acc2, a.partials, set, a.st, t2))
+            return;
+        set ^= 1;
+        beta = t2[0] / rz;
+        rz = t2[0];
+        rr = t2[1];
+        ++it;
+        cur ^= 1;
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        a.x[t.row[k]] = x[k];
+        if (t.row[k] < a.n)
+            a.phi[a.dof_node[t.row[k]]] = x[k];
+    }
+    finish(a, it, sqrt(rr) / sqrt(ff), status);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Jacobi-PCG inside FP64 iterative refinement.  The outer loop
+// recomputes r = f - M x in FP64 (FP64 matrix values, FP64 x) and adds the
+// FP32 correction d in FP64.  The inner solve of M d = r runs in FP32 with
+// FP64 dot products, as standard PCG (two grid barriers per iteration) or as
+// pipelined PCG (Ghysels & Vanroose, Parallel Computing 40, 2014), whose
+// recurrences let one barrier per iteration publish m = D^-1 w for the SpMV
+// n = A m and complete the reductions, at the price of a larger gap between
+// the recursive and the true residual.
+// ---------------------------------------------------------------------------
+template <int RPT> struct In32 {
+    const int *LC;
+    const float *VAL;
+    float dinv[RPT];
+};
+
+template <int RPT>
+__device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
+                               const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_z,
+                               float *s_p0, float *s_p1, float *s_d0, float *s_d1,
+                               double itol, int &set, int &it)
+{
+    float z[RPT], p[RPT], ap[RPT];
+    double acc[2] = {0.0, 0.0}, tot[2];
+    if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1, a.d32_0,
+                                   a.d32_1))
+        return false;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        p[k] = ap[k] = 0.f;
+        if (!t.ok[k])
+            continue;
+        s_z[t.o[k]] = z[k];
+        s_p0[t.o[k]] = 0.f;
+        a.z32[t.row[k]] = z[k];
+        a.p32_0[t.row[k]] = 0.f;
+        acc[0] += (double)rv[k] * (double)z[k];
+        acc[1] += (double)rv[k] * (double)rv[k];
+    }
+    if (!grid_sum<2, RW>(acc, a.partials, set, a.st, tot))
+        return false;
+    set ^= 1;
+    double rz = tot[0], rr = tot[1];
+    const double itol2 = itol * itol * rr;
+    double beta = 0.0;
+    int cur = 0;
+    for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
+                    !(a.inner_max > 0 && i >= a.inner_max);
+         ++i) {
+        float *sp_old = cur ? s_p1 : s_p0;
+        float *sp_new = cur ? s_p0 : s_p1;
+        const float *gp_old = cur ? a.p32_1 : a.p32_0;
+        float *gp_new = cur ? a.p32_0 : a.p32_1;
+        stage_halo(s_z, (const float *)a.z32, a, g);
+        stage_halo(sp_old, gp_old, a, g);
+        __syncthreads();
+        float b32 = (float)beta;
+        double pap[1] = {0.0}, pt[1];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            float sum = 0.f;
+#pragma unroll 4
+            for (int c = 0; c < t.wd[k]; ++c) {
+                int lc = m.LC[t.le[k] + c * 32];
+                sum += m.VAL[t.le[k] + c * 32] * (s_z[lc] + b32 * sp_old[lc]);
+            }
+            p[k] = z[k] + b32 * p[k];
+            ap[k] = sum;
+            sp_new[t.o[k]] = p[k];
+            gp_new[t.row[k]] = p[k];
+            pap[0] += (double)p[k] * (double)sum;
+        }
+        if (!grid_sum<1, RW>(pap, a.partials, set, a.st, pt))
+            return false;
+        set ^= 1;
+        float a32 = (float)(rz / pt[0]);
+        double acc2[2] = {0.0, 0.0}, t2[2];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            d[k] = d[k] + a32 * p[k];
+            rv[k] = rv[k] - a32 * ap[k];
+        }
+        if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1,
+                                       a.d32_0, a.d32_1))
+            return false;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            s_z[t.o[k]] = z[k];
+            a.z32[t.row[k]] = z[k];
+            acc2[0] += (double)rv[k] * (double)z[k];
+            acc2[1] += (double)rv[k] * (double)rv[k];
+        }
+        if (!grid_sum<2, RW>(acc2, a.partials, set, a.st, t2))
+            return false;
+        set ^= 1;
+        beta = t2[0] / rz;
+        rz = t2[0];
+        rr = t2[1];
+        ++it;
+        cur ^= 1;
+    }
+    return true;
+}
+
+template <int RPT>
+__device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
+                                const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_m0,
+                                float *s_m1, int &set, int &it)
+{
+    float u[RPT], wv[RPT], zz[RPT], q[RPT], sv[RPT], p[RPT], mm[RPT];
+    float *gm[2] = {a.z32, a.p32_0};
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        u[k] = m.dinv[k] * rv[k];
+        wv[k] = zz[k] = q[k] = sv[k] = p[k] = mm[k] = 0.f;
+        if (!t.ok[k])
+            continue;
+        s_m0[t.o[k]] = u[k];
+        gm[0][t.row[k]] = u[k];
+    }
+    if (!grid_sync(a.st))
+        return false;
+    stage_halo(s_m0, (const float *)gm[0], a, g);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (t.ok[k])
+            wv[k] = spmv_local<RPT, float, float, float>(t, k, m.LC, m.VAL, false, s_m0);
+    double gamma_old = 1.0, alpha_old = 1.0, rr0 = -1.0;
+    int cur = 0;
+    for (int i = 0;; ++i) {
+        cur ^= 1;
+        float *s_m = cur ? s_m1 : s_m0;
+        float *g_m = gm[cur];
+        double dots[3] = {0.0, 0.0, 0.0}, dt3[3];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            mm[k] = m.dinv[k] * wv[k];
+            s_m[t.o[k]] = mm[k];
+            g_m[t.row[k]] = mm[k];
+            dots[0] += (double)rv[k] * (double)u[k];
+            dots[1] += (double)wv[k] * (double)u[k];
+            dots[2] += (double)rv[k] * (double)rv[k];
+        }
+        if (!grid_sum<3, RW>(dots, a.partials, set, a.st, dt3))
+            return false;
+        set ^= 1;
+        double gamma = dt3[0], delta = dt3[1], rr = dt3[2];
+        if (rr0 < 0.0)
+            rr0 = rr;
+        if (rr <= a.inner_rtol * a.inner_rtol * rr0 || it >= a.max_iter || rr == 0.0 ||
+            (a.inner_max > 0 && i >= a.inner_max))
+            return true;
+        double beta = i == 0 ? 0.0 : gamma / gamma_old;
+        double alpha = i == 0 ? gamma / delta : gamma / (delta - beta * gamma / alpha_old);
+        float b32 = (float)beta, a32 = (float)alpha;
+        stage_halo(s_m, (const float *)g_m, a, g);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            float n = spmv_local<RPT, float, float, float>(t, k, m.LC, m.VAL, false, s_m);
+            zz[k] = n + b32 * zz[k];
+            q[k] = mm[k] + b32 * q[k];
+            sv[k] = wv[k] + b32 * sv[k];
+            p[k] = u[k] + b32 * p[k];
+            d[k] = d[k] + a32 * p[k];
+            rv[k] = rv[k] - a32 * sv[k];
+            u[k] = u[k] - a32 * q[k];
+            wv[k] = wv[k] - a32 * zz[k];
+        }
+        gamma_old = gamma;
+        alpha_old = alpha;
+        ++it;
+    }
+}
+
+template <int RPT, bool SM, bool PIPE>
+__global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Seg g = block_seg(a);
+    float *s_val = (float *)smem;
+    int *s_lc = (int *)(smem + (SM ? a.max_chunk * 4 : 0));
+    size_t off = SM ? (size_t)a.max_chunk * 8 : 0;
+    off = (off + 15) & ~(size_t)15;
+    double *s_x = (double *)(smem + off);
+    float *s_a = (float *)(s_x + a.max_local);
+    float *s_b = s_a + a.max_local;
+    float *s_c = s_b + a.max_local;
+    float *s_d0 = s_c + a.max_local;
+    float *s_d1 = s_d0 + a.max_local;
+    if (SM) {
+        int e1 = a.slice_ptr[g.s1];
+        stage_chunk(s_val, a.val32, g.e0, e1);
+        stage_chunk(s_lc, a.lcol, g.e0, e1);
+    }
+    In32<RPT> m;
+    m.LC = SM ? s_lc : a.lcol;
+    m.VAL = SM ? s_val : a.val32;
+    Rows<RPT> t;
+    init_rows<RPT, SM>(t, a, g);
+    double x[RPT], f[RPT], r64[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        x[k] = f[k] = r64[k] = 0.0;
+        m.dinv[k] = 0.f;
+        if (!t.ok[k])
+            continue;
+        x[k] = a.x[t.row[k]];
+        f[k] = rhs_entry(a, t.row[k]);
+        m.dinv[k] = a.dinv32[t.row[k]];
+        s_x[t.o[k]] = x[k];
+    }
+    int set = 0, it = 0, outer = 0, status = 0;
+    double ff = -1.0, rr64 = 0.0;
+    for (;;) {
+        // FP64 residual r = f - M x (own x in s_x; halo of x staged)
+        stage_halo(s_x, (const double *)a.x, a, g);
+        __syncthreads();
+        double acc[2] = {0.0, 0.0}, tot[2];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            double axv = spmv_local<RPT, double, double, double>(t, k, m.LC, a.val64, true, s_x);
+            r64[k] = f[k] - axv;
+            acc[0] += r64[k] * r64[k];
+            acc[1] += f[k] * f[k];
+        }
+        if (!grid_sum<2, RW>(acc, a.partials, set, a.st, tot))
+            return;
+        set ^= 1;
+        rr64 = tot[0];
+        if (ff < 0.0)
+            ff = tot[1];
+        if (ff == 0.0) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                x[k] = 0.0;
+            rr64 = 0.0;
+            ff = 1.0;
+            break;
+        }
+        if (sqrt(rr64) <= a.rtol * sqrt(ff))
+            break;
+        if (it >= a.max_iter) {
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
+        float rv[RPT], d[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            rv[k] = (float)r64[k];
+            d[k] = 0.f;
+        }
+        // ask the FP32 solve for what the FP64 target still needs (with a
+        // margin), but never for more than ir_inner_rtol in one refinement
+        double itol = 0.5 * a.rtol * sqrt(ff) / sqrt(rr64);
+        if (itol < a.inner_rtol)
+            itol = a.inner_rtol;
+        bool good = PIPE ? inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it)
+                         : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
+                                               itol, set, it);
+        if (!good)
+            return;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            x[k] = x[k] + (double)d[k];
+            s_x[t.o[k]] = x[k];
+            a.x[t.row[k]] = x[k];
+        }
+        if (!grid_sync(a.st))
+            return;
+        ++outer;
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        a.x[t.row[k]] = x[k];
+        if (t.row[k] < a.n)
+            a.phi[a.dof_node[t.row[k]]] = x[k];
+    }
+    finish(a, it, sqrt(rr64) / sqrt(ff), status, outer);
+}
+
+template <int RPT, bool SM> const void *res_kernel(int precision, int variant)
+{
+    if (precision == PIC_PREC_FP64)
+        return (const void *)k_pcg64_res<RPT, SM>;
+    return variant == PIC_PCG_PIPELINED ? (const void *)k_pcg32ir_res<RPT, SM, true>
+                                        : (const void *)k_pcg32ir_res<RPT, SM, false>;
+}
+
+const void *pick_resident(int precision, int variant, int rpt, bool sm)
+{
+    switch (rpt) {
+    case 1: return sm ? res_kernel<1, true>(precision, variant) : res_kernel<1, false>(precision, variant);
+    case 2: return sm ? res_kernel<2, true>(precision, variant) : res_kernel<2, false>(precision, variant);
+    case 4: return sm ? res_kernel<4, true>(precision, variant) : res_kernel<4, false>(precision, variant);
+    default: return sm ? res_kernel<8, true>(precision, variant) : res_kernel<8, false>(precision, variant);
+    }
+}
+
+constexpr size_t SMEM_LIMIT = 220 * 1024;
+
+// Row ownership, local column indices and halos of the resident kernels.
+static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G, PcgHalo *h,
+                       int *max_local, long long *max_chunk)
+{
+    h->lcol.assign((size_t)slice_ptr[n_slices], 0);
+    h->halo_ptr.assign((size_t)G + 1, 0);
+    h->halo_idx.clear();
+    *max_local = 0;
+    *max_chunk = 0;
+    std::vector<int> ext;
+    for (long long b = 0; b < G; ++b) {
+        int s0 = (int)((b * n_slices) / G), s1 = (int)(((b + 1) * n_slices) / G);
+        int row0 = 32 * s0, nrows = 32 * (s1 - s0);
+        int e0 = slice_ptr[s0], e1 = slice_ptr[s1];
+        ext.clear();
+        for (int e = e0; e < e1; ++e) {
+            int j = col[e];
+            if (j < row0 || j >= row0 + nrows)
+                ext.push_back(j);
+        }
+        std::sort(ext.begin(), ext.end());
+        ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
+        for (int e = e0; e < e1; ++e) {
+            int j = col[e];
+            h->lcol[e] = (j >= row0 && j < row0 + nrows)
+                             ? j - row0
+                             : nrows + (int)(std::lower_bound(ext.begin(), ext.end(), j) - ext.begin());
+        }
+        h->halo_idx.insert(h->halo_idx.end(), ext.begin(), ext.end());
+        h->halo_ptr[b + 1] = (int)h->halo_idx.size();
+        *max_local = std::max(*max_local, nrows + (int)ext.size());
+        *max_chunk = std::max(*max_chunk, (long long)(e1 - e0));
+    }
+}
+
+cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num_sms,
+                     int precision, int variant, PcgLaunch *plan, PcgHalo *halo)
+{
+    *plan = PcgLaunch{};
+    // resident: one block per SM (fewer for small problems), rows in registers
+    int G = (n_slices + RW - 1) / RW;
+    if (G > num_sms)
+        G = num_sms;
+    if (G < 1)
+        G = 1;
+    int max_sl = (n_slices + G - 1) / G;
+    int need = (max_sl + RW - 1) / RW;
+    int rpt = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 0;
+    if (rpt) {
+        int max_local = 0;
+        long long chunk = 0;
+        build_halo(slice_ptr, col, n_slices, G, halo, &max_local, &chunk);
+        bool fp64 = precision == PIC_PREC_FP64;
+        size_t vec = fp64 ? (size_t)max_local * 8 * 5 : (size_t)max_local * (8 + 4 * 5);
+        size_t mat = (size_t)chunk * (fp64 ? 12 : 8);
+        mat = (mat + 15) & ~(size_t)15;
+        bool sm = mat + vec <= SMEM_LIMIT;
+        size_t bytes = (sm ? mat : 0) + vec;
+        if (bytes <= SMEM_LIMIT) {
+            const void *fn = pick_resident(precision, variant, rpt, sm);
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bytes);
+            int per_sm = 0;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RB, bytes);
+            if (e != cudaSuccess)
+                return e;
+            if (per_sm >= 1) {
+                plan->grid = G;
+                plan->block = RB;
+                plan->resident = 1;
+                plan->rpt = rpt;
+                plan->smem_matrix = sm ? 1 : 0;
+                plan->smem_bytes = bytes;
+                plan->max_rows = 32 * max_sl;
+                plan->max_chunk = chunk;
+                plan->max_local = max_local;
+                return cudaSuccess;
+            }
+        }
+        *halo = PcgHalo{};
+    }
+    // general path: vectors in global memory, any size
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir,
@@ -417,6 +1130,11 @@ cudaError_t pcg_plan(int n_slices, int num_sms, int precision, PcgLaunch *plan)
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a)
 {
     void *args[] = {(void *)&a};
+    if (plan.resident) {
+        const void *fn = pick_resident(a.precision, a.variant, plan.rpt, plan.smem_matrix != 0);
+        return cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(plan.block), args,
+                                           plan.smem_bytes, s);
+    }
     const void *fn = a.precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
     return cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(plan.block), args, 0, s);
 }

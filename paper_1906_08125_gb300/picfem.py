@@ -35,8 +35,9 @@ class Params(C.Structure):
                 ("q_over_m", C.c_double), ("eps0", C.c_double), ("e_charge", C.c_double),
                 ("pcg_rtol", C.c_double), ("pcg_max_iter", C.c_int32), ("fn_model", C.c_int32),
                 ("seed", C.c_uint64), ("capacity", C.c_int64), ("walk_max_steps", C.c_int32),
-                ("quant_bits", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
-                ("ir_inner_rtol", C.c_double)]
+                ("quant_bits", C.c_int32), ("precision", C.c_int32), ("pcg_variant", C.c_int32),
+                ("ir_inner_rtol", C.c_double), ("ir_inner_max_iter", C.c_int32),
+                ("pcg_cheb_degree", C.c_int32), ("pcg_cheb_ratio", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -138,8 +139,7 @@ def _ptr(x):
 
 
 def _params(d: dict) -> Params:
-    names = [k for k, _ in Params._fields_ if k != "reserved"]
-    return Params(**{k: d[k] for k in names}, reserved=0)
+    return Params(**{k: d[k] for k, _ in Params._fields_})
 
 
 class Context:
