@@ -156,13 +156,20 @@ def bytes_step_fused(st_prev_alive, st, s, rec):
             + alive * 16 + n_new * 64)
 
 
-def bytes_pcg(st, info, fp64):
+def bytes_pcg(st, info, fp64, cheb):
+    """Algorithmic bytes of one solve: every SpMV reads the stored matrix
+    (values + column indices) and the vector it multiplies once; the vector
+    updates read and write each vector they touch once.  A CG iteration with
+    a Chebyshev preconditioner of degree k runs k SpMVs (k - 1 in the
+    preconditioner, one for the search direction)."""
     n, nnz = info["n_free"], info["nnz"]
     it, outer = int(st["pcg_iters"]), int(st["pcg_outer"])
+    k = max(1, cheb)
     if fp64:
-        return it * (12 * nnz + 96 * n) + (12 * nnz + 76 * n) + 20 * n
-    return it * (8 * nnz + 48 * n) + (outer + 1) * (12 * nnz + 24 * n) + outer * 76 * n \
-        + 28 * n + 20 * n
+        per_it = 12 * nnz + 96 * n + (k - 1) * (12 * nnz + 40 * n)
+        return it * per_it + (12 * nnz + 76 * n) + 20 * n
+    per_it = 8 * nnz + 48 * n + (k - 1) * (8 * nnz + 20 * n)
+    return it * per_it + (outer + 1) * (12 * nnz + 24 * n) + outer * 76 * n + 28 * n + 20 * n
 
 
 def bytes_field(info, s, rec):
@@ -251,7 +258,8 @@ def roofline(res, fp64):
     alg = {
         "step_fused": sum(bytes_step_fused(int(pa), row, s, rec)
                           for pa, row in zip(res["prev_alive"], st)),
-        "pcg": sum(bytes_pcg(row, info, fp64) for row in st),
+        "pcg": sum(bytes_pcg(row, info, fp64, res["params"].get("pcg_cheb_degree", 0))
+                   for row in st),
         "field": len(st) * bytes_field(info, s, rec),
         "inject_count": len(st) * bytes_inject_count(info, s),
     }

@@ -52,7 +52,7 @@ WORKLOADS = {
     # 10 GV/m, up to 1e6 SPs, FP32 push + FP64-refined PCG to 1e-6, 500 steps
     "tip_1m": dict(mesh=lambda: inputs.tip_mesh(),
                    params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=3_000_000,
-                               precision=PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=4),
+                               precision=PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
                    steps=500, target_sp=1_000_000),
     # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, ~8M tets,
     # 8 GV/m, work function 4.5 +/- 0.1 eV per face, 1e7 SPs, 200 steps

@@ -302,7 +302,7 @@ __global__ void k_zero_dirichlet(int N, const unsigned char *dir, double *phi)
 int refresh_field(pic_ctx c)
 {
     if (fp64(c))
-        LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, c->phi, (double4 *)c->E));
+        LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, c->phi, (Vec4d *)c->E));
     else
         LAUNCH(K_FIELD, launch_field<float>(c->s, c->T, c->rec32, c->tet4, c->phi, (float4 *)c->E));
     return PIC_OK;
@@ -357,6 +357,22 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
     g.cheb_degree = c->p.pcg_cheb_degree;
     g.cheb_b = c->cheb_b;
     g.cheb_a = c->p.pcg_cheb_degree >= 2 ? c->cheb_b / c->p.pcg_cheb_ratio : 0.0;
+    {
+        // Chebyshev iteration on [a, b] (Saad, Alg. 12.1): theta, delta, sigma and
+        // the recurrence rho_j = 1 / (2 sigma - rho_{j-1}), rho_0 = 1 / sigma
+        double theta = 0.5 * (g.cheb_b + g.cheb_a), delta = 0.5 * (g.cheb_b - g.cheb_a);
+        double sigma = delta > 0 ? theta / delta : 1.0, rho = 1.0 / sigma;
+        g.cheb_inv_theta = 1.0 / theta;
+        g.cheb_inv_thetaf = (float)g.cheb_inv_theta;
+        for (int j = 0; j < 32; ++j) {
+            double rho_new = 1.0 / (2.0 * sigma - rho);
+            g.cheb_c1[j] = rho_new * rho;
+            g.cheb_c2[j] = delta > 0 ? 2.0 * rho_new / delta : 0.0;
+            g.cheb_c1f[j] = (float)g.cheb_c1[j];
+            g.cheb_c2f[j] = (float)g.cheb_c2[j];
+            rho = rho_new;
+        }
+    }
     g.d0 = c->d0;
     g.d1 = c->d1;
     g.d32_0 = c->d32_0;
@@ -779,7 +795,7 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     CK(dalloc(c, &c->x, (size_t)n_pad));
     {
         void *e = nullptr;
-        CK(cudaMalloc(&e, (size_t)T * (d64 ? sizeof(double4) : sizeof(float4))));
+        CK(cudaMalloc(&e, (size_t)T * (d64 ? sizeof(Vec4d) : sizeof(float4))));
         c->allocs.push_back(e);
         c->E = e;
     }
@@ -1211,7 +1227,7 @@ extern "C" int pic_get_field(pic_ctx c, double *E)
     void *tmp = nullptr;
     CK(stage(c, 0, sizeof(double) * 3 * c->T, &tmp));
     if (fp64(c))
-        LAUNCH(K_UTIL, launch_field_unpack<double>(c->s, c->T, (const double4 *)c->E, (double *)tmp));
+        LAUNCH(K_UTIL, launch_field_unpack<double>(c->s, c->T, (const Vec4d *)c->E, (double *)tmp));
     else
         LAUNCH(K_UTIL, launch_field_unpack<float>(c->s, c->T, (const float4 *)c->E, (double *)tmp));
     CK(cudaMemcpyAsync(E, tmp, sizeof(double) * 3 * c->T, cudaMemcpyDefault, c->s));

@@ -41,8 +41,17 @@ struct __align__(64) TetRec32 {
 static_assert(sizeof(TetRec64) == 128, "one line per FP64 record");
 static_assert(sizeof(TetRec32) == 64, "half a line per FP32 record");
 
+// field of one tetrahedron, padded to one 32-byte load
+struct __align__(32) Vec4d {
+    double x, y, z, w;
+};
+__host__ __device__ inline Vec4d make_vec4d(double x, double y, double z, double w)
+{
+    return Vec4d{x, y, z, w};
+}
+
 template <typename R> struct Rec;
-template <> struct Rec<double> { using type = TetRec64; using vec4 = double4; };
+template <> struct Rec<double> { using type = TetRec64; using vec4 = Vec4d; };
 template <> struct Rec<float> { using type = TetRec32; using vec4 = float4; };
 
 // SP id layout: (step << 42) | (quadrangle << 18) | index in the quadrangle
@@ -182,6 +191,10 @@ struct PcgArgs {
     int max_local;            // most own rows + halo columns of one block
     int cheb_degree;          // <= 1: Jacobi; k >= 2: Chebyshev polynomial preconditioner
     double cheb_a, cheb_b;    // Chebyshev interval of D^-1 M
+    // coefficients of the Chebyshev steps (computed on the host):
+    // d_1 = D^-1 r / theta;  d_{j+1} = c1[j] d_j + c2[j] D^-1 r_j
+    double cheb_c1[32], cheb_c2[32], cheb_inv_theta;
+    float cheb_c1f[32], cheb_c2f[32], cheb_inv_thetaf;
     double *d0, *d1;          // FP64 halo buffers of the Chebyshev steps [n_pad]
     float *d32_0, *d32_1;     // FP32 halo buffers of the Chebyshev steps [n_pad]
 };

@@ -300,7 +300,7 @@ __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool
 // field: E_t = -sum_i Phi_{v_i} grad N_i, constant per tetrahedron
 // ---------------------------------------------------------------------------
 __global__ void k_field64(int T, const TetRec64 *__restrict__ rec, const int4 *__restrict__ tet,
-                          const double *__restrict__ phi, double4 *E)
+                          const double *__restrict__ phi, Vec4d *E)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T)
@@ -315,7 +315,7 @@ __global__ void k_field64(int T, const TetRec64 *__restrict__ rec, const int4 *_
         double s = ((p0 * g0 + p1 * r.j[0 + i]) + p2 * r.j[3 + i]) + p3 * r.j[6 + i];
         e[i] = -s;
     }
-    E[t] = make_double4(e[0], e[1], e[2], 0.0);
+    E[t] = make_vec4d(e[0], e[1], e[2], 0.0);
 }
 
 // FP32 records: the same field written with potential differences
@@ -659,7 +659,7 @@ static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b
 
 template <>
 cudaError_t launch_field<double>(cudaStream_t s, int T, const TetRec64 *rec, const int4 *tet,
-                                 const double *phi, double4 *E)
+                                 const double *phi, Vec4d *E)
 {
     k_field64<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E);
     return cudaGetLastError();

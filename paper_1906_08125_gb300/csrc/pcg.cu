@@ -84,28 +84,49 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Sum NV per-thread values over the whole grid; out[] identical in every
-// block.  `set` alternates between calls so a fast block never overwrites
-// partials a slow block has not read yet.
-template <int NV, int WARPS = PCG_WARPS>
-__device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevState *st,
-                         double (&out)[NV])
+// one static buffer per kernel for every reduction: 3 x 512 values + 4 results
+__device__ __noinline__ double *reduction_buffer()
 {
-    __shared__ double red[WARPS][NV];
-    __shared__ double res[NV];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ double buf[3 * 512 + 4];
+    return buf;
+}
+
+struct NoFinish {
+    __device__ void operator()(double *) const {}
+};
+
+// Sum NV per-thread FP64 values over the whole grid in a fixed order, so that
+// every block obtains identical totals.  In the block the values go through
+// shared memory and one warp adds them (each lane a strided run, then a
+// butterfly): far fewer FP64 operations than a butterfly in every warp, which
+// matters on a part whose FP64 rate is low.  The block partials cross the
+// grid barrier in global memory (`set` alternates between calls so a fast
+// block never overwrites partials a slow block has not read yet).  `fin` runs
+// once per block on the totals and may append derived scalars (e.g. the CG
+// step lengths) after them, so that divisions are not repeated by every
+// thread.  out[0..NV) = totals, out[NV..NO) = what fin wrote.
+template <int NV, int NO, int BLOCK, typename F>
+__device__ bool grid_sum_f(const double (&v)[NV], double *partials, int set, DevState *st,
+                           double (&out)[NO], F fin)
+{
+    static_assert(NV <= 3 && NO <= 4 && BLOCK <= 512, "reduction buffer size");
+    double *vals = reduction_buffer();
+    double *res = vals + 3 * 512;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double s = warp_sum(v[k]);
-        if (lane == 0)
-            red[wid][k] = s;
-    }
+    for (int k = 0; k < NV; ++k)
+        vals[k * BLOCK + threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x < NV) {
-        double s = 0.0;
-        for (int w = 0; w < WARPS; ++w)
-            s += red[w][threadIdx.x];
-        partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = s;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int i = lane; i < BLOCK; i += 32)
+                s += vals[k * BLOCK + i];
+            s = warp_sum(s);
+            if (lane == 0)
+                partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + k] = s;
+        }
     }
     if (!grid_sync(st))
         return false;
@@ -119,12 +140,21 @@ __device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevSt
             if (lane == 0)
                 res[k] = s;
         }
+        if (lane == 0)
+            fin(res);
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
+    for (int k = 0; k < NO; ++k)
         out[k] = res[k];
     return true;
+}
+
+template <int NV, int BLOCK = PCG_BLOCK>
+__device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevState *st,
+                         double (&out)[NV])
+{
+    return grid_sum_f<NV, NV, BLOCK>(v, partials, set, st, out, NoFinish());
 }
 
 // f_i = (q w_sp / eps0) W_i 2^-S + f_Neumann,i (eq. poisson_rhs), written
@@ -496,6 +526,10 @@ __device__ __forceinline__ ACC spmv_local(const Rows<RPT> &t, int k, const int *
 // (Gershgorin), so CG stays CG.  Each step after the first needs one SpMV of
 // the step direction: published to the block's shared segment and to a
 // double-buffered global halo copy, one plain grid barrier, no reduction.
+template <typename T> __device__ __forceinline__ T cheb_coef(double d, float f);
+template <> __device__ __forceinline__ double cheb_coef<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float cheb_coef<float>(double, float f) { return f; }
+
 template <int RPT, typename T>
 __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
                               const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT],
@@ -507,11 +541,8 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             z[k] = dinv[k] * r[k];
         return true;
     }
-    const double theta = 0.5 * (a.cheb_b + a.cheb_a), delta = 0.5 * (a.cheb_b - a.cheb_a);
-    const double sigma = theta / delta;
-    double rho = 1.0 / sigma;
     T rc[RPT], d[RPT];
-    const T inv_theta = (T)(1.0 / theta);
+    const T inv_theta = cheb_coef<T>(a.cheb_inv_theta, a.cheb_inv_thetaf);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         rc[k] = r[k];
@@ -537,9 +568,8 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             return false;
         stage_halo(s_d, (const T *)g_d, a, g);
         __syncthreads();
-        double rho_new = 1.0 / (2.0 * sigma - rho);
-        const T c1 = (T)(rho_new * rho), c2 = (T)(2.0 * rho_new / delta);
-        rho = rho_new;
+        const T c1 = cheb_coef<T>(a.cheb_c1[j - 1], a.cheb_c1f[j - 1]);
+        const T c2 = cheb_coef<T>(a.cheb_c2[j - 1], a.cheb_c2f[j - 1]);
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -621,7 +651,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         a.p0[t.row[k]] = 0.0;
     }
     int set = 0;
-    if (!grid_sum<3, RW>(acc, a.partials, set, a.st, tot))
+    if (!grid_sum<3, RB>(acc, a.partials, set, a.st, tot))
         return;
     set ^= 1;
     double rz = tot[0], rr = tot[1], ff = tot[2];
@@ -633,10 +663,10 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         rr = 0.0;
         ff = 1.0;
     }
-    const double tol = a.rtol * sqrt(ff);
+    const double tol2 = a.rtol * a.rtol * ff;
     double beta = 0.0;
     int cur = 0;
-    while (sqrt(rr) > tol) {
+    while (rr > tol2) {
         if (it >= a.max_iter) {
             status = PIC_ERR_NOT_CONVERGED;
             break;
@@ -648,7 +678,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         stage_halo(s_z, a.z, a, g);
         stage_halo(sp_old, gp_old, a, g);
         __syncthreads();
-        double pap[1] = {0.0}, pt[1];
+        double pap[1] = {0.0};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -665,11 +695,13 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
             gp_new[t.row[k]] = p[k];
             pap[0] += p[k] * sum;
         }
-        if (!grid_sum<1, RW>(pap, a.partials, set, a.st, pt))
+        double pt2[2];
+        if (!grid_sum_f<1, 2, RB>(pap, a.partials, set, a.st, pt2,
+                                  [rz](double *q) { q[1] = rz / q[0]; }))
             return;
         set ^= 1;
-        double alpha = rz / pt[0];
-        double acc2[2] = {0.0, 0.0}, t2[2];
+        double alpha = pt2[1];
+        double acc2[2] = {0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -688,12 +720,14 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
             acc2[0] += r[k] * z[k];
             acc2[1] += r[k] * r[k];
         }
-        if (!grid_sum<2, RW>(acc2, a.partials, set, a.st, t2))
+        double t3[3];
+        if (!grid_sum_f<2, 3, RB>(acc2, a.partials, set, a.st, t3,
+                                  [rz](double *q) { q[2] = q[0] / rz; }))
             return;
         set ^= 1;
-        beta = t2[0] / rz;
-        rz = t2[0];
-        rr = t2[1];
+        beta = t3[2];
+        rz = t3[0];
+        rr = t3[1];
         ++it;
         cur ^= 1;
     }
@@ -705,7 +739,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         if (t.row[k] < a.n)
             a.phi[a.dof_node[t.row[k]]] = x[k];
     }
-    finish(a, it, sqrt(rr) / sqrt(ff), status);
+    finish(a, it, sqrt(rr / ff), status);
 }
 
 // ---------------------------------------------------------------------------
@@ -747,7 +781,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         acc[0] += (double)rv[k] * (double)z[k];
         acc[1] += (double)rv[k] * (double)rv[k];
     }
-    if (!grid_sum<2, RW>(acc, a.partials, set, a.st, tot))
+    if (!grid_sum<2, RB>(acc, a.partials, set, a.st, tot))
         return false;
     set ^= 1;
     double rz = tot[0], rr = tot[1];
@@ -765,7 +799,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         stage_halo(sp_old, gp_old, a, g);
         __syncthreads();
         float b32 = (float)beta;
-        double pap[1] = {0.0}, pt[1];
+        double pap[1] = {0.0};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -782,11 +816,13 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             gp_new[t.row[k]] = p[k];
             pap[0] += (double)p[k] * (double)sum;
         }
-        if (!grid_sum<1, RW>(pap, a.partials, set, a.st, pt))
+        double pt2[2];
+        if (!grid_sum_f<1, 2, RB>(pap, a.partials, set, a.st, pt2,
+                                  [rz](double *q) { q[1] = rz / q[0]; }))
             return false;
         set ^= 1;
-        float a32 = (float)(rz / pt[0]);
-        double acc2[2] = {0.0, 0.0}, t2[2];
+        float a32 = (float)pt2[1];
+        double acc2[2] = {0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -806,12 +842,14 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             acc2[0] += (double)rv[k] * (double)z[k];
             acc2[1] += (double)rv[k] * (double)rv[k];
         }
-        if (!grid_sum<2, RW>(acc2, a.partials, set, a.st, t2))
+        double t3[3];
+        if (!grid_sum_f<2, 3, RB>(acc2, a.partials, set, a.st, t3,
+                                  [rz](double *q) { q[2] = q[0] / rz; }))
             return false;
         set ^= 1;
-        beta = t2[0] / rz;
-        rz = t2[0];
-        rr = t2[1];
+        beta = t3[2];
+        rz = t3[0];
+        rr = t3[1];
         ++it;
         cur ^= 1;
     }
@@ -860,7 +898,7 @@ __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const Pc
             dots[1] += (double)wv[k] * (double)u[k];
             dots[2] += (double)rv[k] * (double)rv[k];
         }
-        if (!grid_sum<3, RW>(dots, a.partials, set, a.st, dt3))
+        if (!grid_sum<3, RB>(dots, a.partials, set, a.st, dt3))
             return false;
         set ^= 1;
         double gamma = dt3[0], delta = dt3[1], rr = dt3[2];
@@ -947,7 +985,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
             acc[0] += r64[k] * r64[k];
             acc[1] += f[k] * f[k];
         }
-        if (!grid_sum<2, RW>(acc, a.partials, set, a.st, tot))
+        if (!grid_sum<2, RB>(acc, a.partials, set, a.st, tot))
             return;
         set ^= 1;
         rr64 = tot[0];
@@ -1024,7 +1062,7 @@ const void *pick_resident(int precision, int variant, int rpt, bool sm)
     }
 }
 
-constexpr size_t SMEM_LIMIT = 220 * 1024;
+constexpr size_t SMEM_LIMIT = 200 * 1024;   // + static reduction buffers
 
 // Row ownership, local column indices and halos of the resident kernels.
 static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G, PcgHalo *h,
