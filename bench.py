@@ -180,6 +180,21 @@ def bytes_inject_count(info, s):
     return 3 * info["n_faces"] * (4 * s + 3 * 8 + 8 + 8 + 4 + 4)
 
 
+def aggregate_replicas(total_ms, pushes, world, device):
+    """Whole-job figures of N independent replicas: the time of the slowest
+    rank (max over ranks) and the SP pushes of all ranks (sum).  One rank
+    per GPU; any torch.distributed backend (NCCL on GPUs, gloo in tests)."""
+    if world <= 1:
+        return float(total_ms), pushes
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(pushes)], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -237,14 +252,10 @@ def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read() if with_profile else {}
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     st = np.frombuffer(dstats.cpu().numpy().tobytes(), dtype=STAT_DTYPE)
     prev = np.concatenate([[n0], st["alive"][:-1]])
-    pushes = int((prev + st["injected"]).sum())
+    total_ms, pushes = aggregate_replicas(float(sum(step_ms)), int((prev + st["injected"]).sum()),
+                                          world, dev)
     res = dict(ctx=ctx, mesh=mesh, params=p, info=info, step_ms=step_ms, total_ms=total_ms,
                stats=st, prev_alive=prev, pushes=pushes, launches=launches, prof=prof,
                clocks=clk, n0=n0)
@@ -367,12 +378,7 @@ def main():
     roof, kernels = roofline(res, fp64)
     K = args.steps
     value = world * K / (res["total_ms"] * 1e-3)
-    pushes = res["pushes"]
-    if world > 1:
-        t = torch.tensor([pushes], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t)
-        pushes = float(t.item())
-    push_rate = pushes / (res["total_ms"] * 1e-3)
+    push_rate = res["pushes"] / (res["total_ms"] * 1e-3)
     e2e = run_e2e(res, args.e2e_steps)
     st = res["stats"]
     cfg = {"workload": args.workload, "tets": res["info"]["n_tets"],

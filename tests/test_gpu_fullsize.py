@@ -1,0 +1,141 @@
+"""Parity at full size: the 1M-tetrahedron tip workload in the configuration
+the benchmark times (FP32 push, FP32 Chebyshev-PCG inside FP64 refinement,
+fused pic_step), against the FP64 oracle on sampled outputs: a seeded
+population of 2e5 SPs (the oracle handles it in seconds) stepped once from
+identical state, and the potentials of the charge-free and space-charge
+solves.  Also the FP64 split path at full size, bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1906_08125_gb300 import configs as K
+from paper_1906_08125_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N_SAMPLE = 200_000
+
+
+@pytest.fixture(scope="module")
+def picfem():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_08125_gb300 import picfem as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module")
+def tip1m():
+    mesh, p, _ = K.workload("tip_1m")
+    return mesh, p
+
+
+@pytest.fixture(scope="module")
+def oracle_state(oracle_mod, tip1m):
+    """Oracle with the charge-free potential solved tightly, then the seeded
+    sample population deposited and its potential solved tightly."""
+    mesh, p = tip1m
+    orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-11,
+                                       pcg_max_iter=50000))
+    orc.init_potential()
+    phi0 = orc.potential()
+    parts = inputs.random_particles(mesh, N_SAMPLE, seed=77, v_scale=3e6, v_up=1.5e7)
+    orc.set_particles(*parts)
+    orc.deposit()
+    orc.poisson_solve()
+    return orc, phi0, parts
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def by_id(state):
+    r, v, cell, pid = state
+    o = np.argsort(pid, kind="stable")
+    return r[o], v[o], cell[o], pid[o]
+
+
+def bary(mesh, cell, r):
+    P = mesh.xyz[mesh.tet[cell]]
+    J = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    lam = np.linalg.solve(J, (r - P[:, 0])[..., None])[..., 0]
+    return np.concatenate([1 - lam.sum(1, keepdims=True), lam], axis=1)
+
+
+def test_potentials_at_bench_tolerance(picfem, tip1m, oracle_state):
+    """Both GPU forms, at the solver tolerance the benchmark uses, reach 1e-6
+    relative potential accuracy against the oracle's tight solve."""
+    mesh, p = tip1m
+    orc, phi0, parts = oracle_state
+    for form in ({}, {"precision": K.PREC_FP64, "pcg_cheb_degree": 0}):
+        ctx = picfem.Context(dict(p, **form)).mesh_load(mesh)
+        ctx.init_potential()
+        e0 = rel(ctx.potential(), phi0)
+        ctx.set_particles(*parts)
+        ctx.deposit()
+        ctx.set_potential(phi0)
+        ctx.poisson_solve()
+        e1 = rel(ctx.potential(), orc.potential())
+        ctx.close()
+        assert e0 <= 1e-6 and e1 <= 1e-6, (form, e0, e1)
+
+
+def test_one_bench_step_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
+    """One fused step in the benchmark's configuration from identical state
+    (the oracle's tight potential and the seeded sample): same SP ids up to
+    rounding flips of the injection count, positions within 1e-5 of the box
+    height, differing cells only within FP32 rounding of a face, exact charge
+    conservation, and the new potential within 1e-6."""
+    mesh, p = tip1m
+    orc, phi0, parts = oracle_state
+    phi_start = orc.potential()
+    o2 = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-11,
+                                      pcg_max_iter=50000))
+    o2.set_potential(phi_start)
+    o2.set_particles(*parts)
+    o2.step_index = 5
+    so = o2.step(1)[0]
+
+    ctx = picfem.Context(p).mesh_load(mesh)
+    ctx.set_potential(phi_start)
+    ctx.set_particles(*parts)
+    ctx.step_index = 5
+    sg = ctx.step(1)[0]
+
+    g, o = by_id(ctx.particles()), by_id(o2.particles())
+    common, ig, io = np.intersect1d(g[3], o[3], return_indices=True)
+    assert len(common) >= len(o[3]) - 10 and len(common) >= len(g[3]) - 10
+    Lz = mesh.box_hi[2] - mesh.box_lo[2]
+    assert np.abs(g[0][ig] - o[0][io]).max() <= 1e-5 * Lz
+    diff = g[2][ig] != o[2][io]
+    assert diff.mean() <= 1e-3
+    if diff.any():
+        assert bary(mesh, g[2][ig][diff], g[0][ig][diff]).min() >= -1e-5
+    assert abs(sg.injected - so.injected) <= 10
+    W = ctx.charge()
+    assert int(W.sum()) == len(g[3]) * 2 ** 32
+    assert rel(ctx.potential(), o2.potential()) <= 1e-6
+
+
+def test_fp64_split_step_bit_exact_full_size(picfem, oracle_mod, tip1m, oracle_state):
+    """FP64 form at full size: injection, push, walk and deposit of the
+    sample from identical state are bit-exact."""
+    mesh, p = tip1m
+    orc, phi0, parts = oracle_state
+    pp = dict(p, precision=K.PREC_FP64, pcg_cheb_degree=0)
+    o2 = oracle_mod.Oracle(mesh, pp)
+    o2.set_potential(orc.potential())
+    o2.set_particles(*parts)
+    ctx = picfem.Context(pp).mesh_load(mesh)
+    ctx.set_potential(orc.potential())
+    ctx.set_particles(*parts)
+    assert ctx.inject(9) == o2.inject(9)
+    sg, so = ctx.push_relocate(9), o2.push_relocate(9)
+    for f in ("collected", "absorbed", "wrapped", "crossings", "max_walk", "alive"):
+        assert getattr(sg, f) == getattr(so, f), f
+    for a, b in zip(by_id(ctx.particles()), by_id(o2.particles())):
+        assert np.array_equal(a, b)
+    ctx.deposit()
+    assert np.array_equal(ctx.charge(), o2.deposit())
