@@ -1119,6 +1119,7 @@ template <typename R> static int step_once(pic_ctx c, pic_step_stats *ds)
     const long long kstep = c->step;
     CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
     CK(cudaMemsetAsync(&c->st->cnt[1 - c->a], 0, sizeof(unsigned long long), c->s));
+    CK(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned long long), c->s));
     LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, kstep, c->qcount, &c->st->err));
     LAUNCH(K_INJECT_SCAN, launch_inject_scan(c->s, c->NQ, c->qcount, c->qoff, c->st, c->a,
                                              c->p.capacity, 0, ds));

@@ -102,6 +102,7 @@ struct DevState {
     int err;                    // first device-side error (PIC_ERR_*), 0 if none
     int pad;
     unsigned bar_count, bar_gen;  // grid barrier of the persistent PCG
+    unsigned long long work;      // next unclaimed SP of the fused step (work queue)
 };
 
 // ---------------------------------------------------------------------------

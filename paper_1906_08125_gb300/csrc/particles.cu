@@ -96,56 +96,70 @@ __device__ __forceinline__ void barycentric(const T &rec, const R r[3], R lam[4]
 // Relocation by walking neighbours (Sec. II.B.2): leave through the face
 // opposite the most negative barycentric coordinate (lowest index on ties),
 // never back through the face just entered; stop when every other coordinate
-// is >= 0.  Returns the fate; t, r (wrapped), lam (in the final tet) updated.
+// is >= 0.  walk_step does one step: it returns WALK_CONTINUE after moving to
+// the next tetrahedron (t, entered, r updated; r wrapped on Gamma_2) or the
+// fate of the SP, with lam holding the barycentrics in its final tetrahedron.
+constexpr int WALK_CONTINUE = -1;
+
+template <typename R>
+__device__ __forceinline__ int walk_step(const MeshView<R> &m, int walk_max, R r[3], int &t,
+                                         int &entered, R lam[4], int &steps, int &wraps)
+{
+    using T = typename Rec<R>::type;
+    T rec = load_rec(m.rec + t);
+    barycentric<R>(rec, r, lam);
+    int k = -1;
+    R mn = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (i == entered)
+            continue;
+        if (k < 0 || lam[i] < mn) {
+            k = i;
+            mn = lam[i];
+        }
+    }
+    if (mn >= (R)0)
+        return FATE_ALIVE;
+    if (steps >= walk_max)
+        return FATE_LIMIT;
+    ++steps;
+    int p = k == 0 ? rec.nb[0] : k == 1 ? rec.nb[1] : k == 2 ? rec.nb[2] : rec.nb[3];
+    if (p >= 0) {
+        t = p >> 2;
+        entered = p & 3;
+        return WALK_CONTINUE;
+    }
+    if (p == NB_TOP)
+        return FATE_COLLECTED;
+    if (p == NB_CATHODE)
+        return FATE_ABSORBED;
+    int v = NB_SIDE - p;
+    int sc = (v >> 2) & 3;
+    entered = v & 3;
+    t = v >> 4;
+    if (sc == 0)
+        r[0] = r[0] + (R)m.Lx;
+    else if (sc == 1)
+        r[0] = r[0] + (R)(-m.Lx);
+    else if (sc == 2)
+        r[1] = r[1] + (R)m.Ly;
+    else
+        r[1] = r[1] + (R)(-m.Ly);
+    ++wraps;
+    return WALK_CONTINUE;
+}
+
 template <typename R>
 __device__ int walk(const MeshView<R> &m, int walk_max, R r[3], int &t, R lam[4], int &steps,
                     int &wraps)
 {
-    using T = typename Rec<R>::type;
     int entered = -1;
     steps = 0;
     for (;;) {
-        T rec = load_rec(m.rec + t);
-        barycentric<R>(rec, r, lam);
-        int k = -1;
-        R mn = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (i == entered)
-                continue;
-            if (k < 0 || lam[i] < mn) {
-                k = i;
-                mn = lam[i];
-            }
-        }
-        if (mn >= (R)0)
-            return FATE_ALIVE;
-        if (steps >= walk_max)
-            return FATE_LIMIT;
-        ++steps;
-        int p = k == 0 ? rec.nb[0] : k == 1 ? rec.nb[1] : k == 2 ? rec.nb[2] : rec.nb[3];
-        if (p >= 0) {
-            t = p >> 2;
-            entered = p & 3;
-            continue;
-        }
-        if (p == NB_TOP)
-            return FATE_COLLECTED;
-        if (p == NB_CATHODE)
-            return FATE_ABSORBED;
-        int v = NB_SIDE - p;
-        int sc = (v >> 2) & 3;
-        entered = v & 3;
-        t = v >> 4;
-        if (sc == 0)
-            r[0] = r[0] + (R)m.Lx;
-        else if (sc == 1)
-            r[0] = r[0] + (R)(-m.Lx);
-        else if (sc == 2)
-            r[1] = r[1] + (R)m.Ly;
-        else
-            r[1] = r[1] + (R)(-m.Ly);
-        ++wraps;
+        int f = walk_step<R>(m, walk_max, r, t, entered, lam, steps, wraps);
+        if (f != WALK_CONTINUE)
+            return f;
     }
 }
 
@@ -532,8 +546,63 @@ __global__ void k_deposit(MeshView<R> m, RunConst c, Particles<R> A, int a, DevS
 // ---------------------------------------------------------------------------
 // one fused PIC step on the particle side: SPs [0, n_old) of buffer A are
 // kicked, SPs [n_old, n_old + n_new) are emitted in place; all drift, walk,
-// deposit, and survivors are appended to buffer B
+// deposit, and survivors are appended to buffer B.
+//
+// Walk lengths differ by orders of magnitude between SPs (tens of crossings
+// far from the tip, hundreds near the apex), so a warp that walks 32 SPs to
+// completion idles lanes behind its slowest SP.  Two forms share the same
+// per-SP arithmetic (start_sp, walk_step, deposit_one) as the split kernels:
+// coherent warps, and persistent lanes that take the next SP from the warp's
+// queue (refilled with CHUNK consecutive SPs from a global counter) as soon
+// as theirs is done.
 // ---------------------------------------------------------------------------
+constexpr int CHUNK = 128;
+
+template <typename R>
+__device__ __forceinline__ void start_sp(const MeshView<R> &m, const RunConst &c, long long step,
+                                         int nq, const long long *qoff, const Particles<R> &A,
+                                         long long n_old, long long i, DevState *st, R r[3],
+                                         R v[3], int &t, long long &id)
+{
+    const R qmdt = (R)c.qmdt, dt = (R)c.dt;
+    if (i < n_old) {
+        r[0] = A.x[i];
+        r[1] = A.y[i];
+        r[2] = A.z[i];
+        v[0] = A.vx[i];
+        v[1] = A.vy[i];
+        v[2] = A.vz[i];
+        t = A.cell[i];
+        id = A.id[i];
+        typename Rec<R>::vec4 e = m.E[t];
+        v[0] = v[0] + qmdt * (R)e.x;
+        v[1] = v[1] + qmdt * (R)e.y;
+        v[2] = v[2] + qmdt * (R)e.z;
+    } else {
+        long long tn = i - n_old;
+        int q = find_quad(qoff, nq, tn);
+        double rd[3], vd[3];
+        if (!emit<R>(m, c, step, q, tn - qoff[q], rd, vd, t, id)) {
+            set_err(&st->err, PIC_ERR_ARG);
+            rd[0] = rd[1] = rd[2] = 0.0;
+            vd[0] = vd[1] = vd[2] = 0.0;
+            t = m.face_tet[q / 3];
+        }
+        for (int k = 0; k < 3; ++k) {
+            r[k] = (R)rd[k];
+            v[k] = (R)vd[k];
+        }
+    }
+    r[0] = r[0] + dt * v[0];
+    r[1] = r[1] + dt * v[1];
+    r[2] = r[2] + dt * v[2];
+}
+
+// Coherent form: each warp takes 32 consecutive SPs and walks them to the
+// end together.  SPs that are neighbours in the buffer were injected or
+// appended together and walk through the same records, so the warp's record
+// fetches share L1 lines; on the FP32 path that locality is worth more than
+// the lanes that idle behind the warp's longest walk.
 template <typename R>
 __global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, long long step,
                                                     int nq, const long long *__restrict__ qoff,
@@ -541,10 +610,9 @@ __global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, l
                                                     DevState *st, unsigned long long *W,
                                                     pic_step_stats *stats)
 {
-    long long n_old = (long long)st->cnt[a];
-    long long n = n_old + st->n_new;
+    const long long n_old = (long long)st->cnt[a];
+    const long long n = n_old + st->n_new;
     unsigned long long *cntB = &st->cnt[1 - a];
-    const R qmdt = (R)c.qmdt, dt = (R)c.dt;
     long long wstride = ((long long)gridDim.x * blockDim.x) & ~31LL;
     long long wbase = (blockIdx.x * (long long)blockDim.x + threadIdx.x) & ~31LL;
     int lane = threadIdx.x & 31;
@@ -555,37 +623,7 @@ __global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, l
         int t = 0, fate = FATE_ABSORBED, steps = 0, wraps = 0;
         long long id = 0;
         if (act) {
-            if (i < n_old) {
-                r[0] = A.x[i];
-                r[1] = A.y[i];
-                r[2] = A.z[i];
-                v[0] = A.vx[i];
-                v[1] = A.vy[i];
-                v[2] = A.vz[i];
-                t = A.cell[i];
-                id = A.id[i];
-                typename Rec<R>::vec4 e = m.E[t];
-                v[0] = v[0] + qmdt * (R)e.x;
-                v[1] = v[1] + qmdt * (R)e.y;
-                v[2] = v[2] + qmdt * (R)e.z;
-            } else {
-                long long tn = i - n_old;
-                int q = find_quad(qoff, nq, tn);
-                double rd[3], vd[3];
-                if (!emit<R>(m, c, step, q, tn - qoff[q], rd, vd, t, id)) {
-                    set_err(&st->err, PIC_ERR_ARG);
-                    rd[0] = rd[1] = rd[2] = 0.0;
-                    vd[0] = vd[1] = vd[2] = 0.0;
-                    t = m.face_tet[q / 3];
-                }
-                for (int k = 0; k < 3; ++k) {
-                    r[k] = (R)rd[k];
-                    v[k] = (R)vd[k];
-                }
-            }
-            r[0] = r[0] + dt * v[0];
-            r[1] = r[1] + dt * v[1];
-            r[2] = r[2] + dt * v[2];
+            start_sp<R>(m, c, step, nq, qoff, A, n_old, i, st, r, v, t, id);
             fate = walk<R>(m, c.walk_max, r, t, lam, steps, wraps);
             if (fate == FATE_LIMIT)
                 set_err(&st->err, PIC_ERR_WALK_LIMIT);
@@ -595,6 +633,111 @@ __global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, l
         bool alive = act && fate == FATE_ALIVE;
         append<R>(alive, r, v, t, id, B, cntB);
         count_fates(fate, steps, wraps, act, stats);
+    }
+}
+
+// Persistent form: lanes take the next SP as soon as theirs is done (see
+// above); used where the walk is arithmetic-bound (FP64 on this part).
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_fused_persistent(
+    MeshView<R> m, RunConst c, long long step, int nq, const long long *__restrict__ qoff,
+    Particles<R> A, Particles<R> B, int a, DevState *st, unsigned long long *W,
+    pic_step_stats *stats)
+{
+    const long long n_old = (long long)st->cnt[a];
+    const long long n = n_old + st->n_new;
+    unsigned long long *cntB = &st->cnt[1 - a];
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    long long q_next = 0, q_end = 0;  // the warp's queue (warp-uniform)
+    bool exhausted = false;
+    bool active = false;
+    R r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, lam[4] = {0, 0, 0, 0};
+    int t = 0, entered = -1, steps = 0, wraps = 0;
+    long long id = 0;
+    unsigned long long n_cross = 0;
+    unsigned n_col = 0, n_abs = 0, n_wrap = 0;
+    int n_max = 0;
+    for (;;) {
+        // hand SPs to idle lanes
+        unsigned idle = __ballot_sync(FULL_MASK, !active);
+        while (idle) {
+            if (q_next >= q_end) {
+                if (exhausted)
+                    break;
+                long long b = 0;
+                if (lane == 0)
+                    b = (long long)atomicAdd(&st->work, (unsigned long long)CHUNK);
+                b = __shfl_sync(FULL_MASK, b, 0);
+                if (b >= n) {
+                    exhausted = true;
+                    break;
+                }
+                q_next = b;
+                q_end = b + CHUNK < n ? b + CHUNK : n;
+            }
+            int nidle = __popc(idle);
+            long long avail = q_end - q_next;
+            int take = avail < nidle ? (int)avail : nidle;
+            if (!active) {
+                int rank = __popc(idle & lower);
+                if (rank < take) {
+                    start_sp<R>(m, c, step, nq, qoff, A, n_old, q_next + rank, st, r, v, t, id);
+                    entered = -1;
+                    steps = 0;
+                    wraps = 0;
+                    active = true;
+                }
+            }
+            q_next += take;
+            if (take == nidle)
+                break;
+            idle = __ballot_sync(FULL_MASK, !active);
+        }
+        if (!__any_sync(FULL_MASK, active))
+            break;
+        int fate = WALK_CONTINUE;
+        if (active)
+            fate = walk_step<R>(m, c.walk_max, r, t, entered, lam, steps, wraps);
+        bool finished = active && fate != WALK_CONTINUE;
+        bool keep = finished && fate == FATE_ALIVE;
+        if (finished) {
+            if (keep)
+                deposit_one<R>(m.tet, t, lam, c.scale, W);
+            else if (fate == FATE_COLLECTED)
+                ++n_col;
+            else if (fate == FATE_ABSORBED)
+                ++n_abs;
+            else
+                set_err(&st->err, PIC_ERR_WALK_LIMIT);
+            n_cross += (unsigned long long)steps;
+            n_wrap += (unsigned)wraps;
+            n_max = steps > n_max ? steps : n_max;
+            active = false;
+        }
+        append<R>(keep, r, v, t, id, B, cntB);
+    }
+    if (stats) {
+        unsigned col = __reduce_add_sync(FULL_MASK, n_col);
+        unsigned absb = __reduce_add_sync(FULL_MASK, n_abs);
+        unsigned wr = __reduce_add_sync(FULL_MASK, n_wrap);
+        int mx = (int)__reduce_max_sync(FULL_MASK, (unsigned)n_max);
+        unsigned long long cr = n_cross;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            cr += __shfl_xor_sync(FULL_MASK, cr, o);
+        if (lane == 0) {
+            if (col)
+                atomicAdd((unsigned long long *)&stats->collected, (unsigned long long)col);
+            if (absb)
+                atomicAdd((unsigned long long *)&stats->absorbed, (unsigned long long)absb);
+            if (cr)
+                atomicAdd((unsigned long long *)&stats->crossings, cr);
+            if (wr)
+                atomicAdd((unsigned long long *)&stats->wrapped, (unsigned long long)wr);
+            if (mx)
+                atomicMax(&stats->max_walk, mx);
+        }
     }
 }
 
@@ -722,7 +865,10 @@ cudaError_t launch_step_fused(cudaStream_t s, int grid, MeshView<R> m, RunConst 
                               Particles<R> B, int a, DevState *st, unsigned long long *W,
                               pic_step_stats *stats)
 {
-    k_step_fused<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
+    if (sizeof(R) == 8)
+        k_step_fused_persistent<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
+    else
+        k_step_fused<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
     return cudaGetLastError();
 }
 
