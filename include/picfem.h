@@ -94,6 +94,10 @@ typedef struct {
                               per CG iteration, no extra reductions)             */
     double pcg_cheb_ratio;     /* Chebyshev interval [b / ratio, b], b the
                               Gershgorin bound of D^-1 M (e.g. 30)               */
+    int32_t graph;             /* 1: pic_step captures one step per buffer parity
+                              in a CUDA graph and replays it (not while
+                              profiling); 0: launches every kernel directly      */
+    int32_t reserved;
 } pic_params;
 
 /* inner solver of the FP32_IR Poisson solve */
@@ -121,7 +125,13 @@ typedef struct {
     int64_t sell_len;         /* stored entries incl. slice padding            */
     int32_t pcg_grid;         /* blocks of the persistent PCG launch           */
     int32_t particle_grid;    /* blocks of the particle kernels                */
-    double box_lo[3], box_hi[3];
+    double box_lo[3], box_hi[3];  /* over all replicas                          */
+    int32_t n_rep;            /* replicas (1 after mesh_load)                  */
+    int32_t n_rows;           /* solver rows: free DOFs + per-replica padding  */
+    int32_t pcg_resident;     /* 1: one-system resident PCG kernel             */
+    int32_t graph;            /* pic_step: 1 replays a captured CUDA graph per
+                                 step, 0 not yet captured or params.graph = 0,
+                                 -1 the capture was refused (direct launches)  */
 } pic_info;
 
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -158,6 +168,60 @@ int mesh_load(pic_ctx ctx, int32_t n_nodes, const double *xyz, int32_t n_tets,
               const int32_t *tet, const int32_t *nbr, const int32_t *periodic_nbr,
               const uint8_t *node_dirichlet, int32_t n_faces, const int32_t *face_nodes,
               const int32_t *face_tet, const double *work_function_eV);
+
+/*
+ * mesh_load_batch: n_rep independent simulations (replicas) in one context,
+ * stepped together by every call below.  The arrays are those of mesh_load
+ * for the union of the replicas' meshes, each replica a contiguous block:
+ *   rep_node_off[n_rep+1]  replica r owns nodes [rep_node_off[r], rep_node_off[r+1])
+ *   rep_tet_off[n_rep+1]   and tetrahedra [rep_tet_off[r], rep_tet_off[r+1]);
+ *                          both start at 0 and end at n_nodes / n_tets
+ *   E0_rep[n_rep]          applied field of each replica [V/m] (params.E0 is
+ *                          not used by a batch)
+ * No tetrahedron, neighbour, periodic partner or face may reach into another
+ * replica, and the emitting faces must be listed replica by replica
+ * (PIC_ERR_MESH otherwise).  Each replica's periodic box is its own bounding
+ * box in x and y.  Replica r draws its random numbers from seed + r with its
+ * own quadrangle numbering, so it reproduces a one-replica run of its mesh
+ * with seed + r; SP ids carry the batch-wide quadrangle index.  The Poisson
+ * systems are solved together, each block of the solver working on one
+ * replica, and each replica's CG stops at its own relative residual.
+ * Statistics of pic_step / push_relocate are sums over replicas; the PCG
+ * iteration count is the maximum.  All pointers are HOST arrays, copied.
+ */
+int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
+                    const int32_t *rep_tet_off, const double *E0_rep, int32_t n_nodes,
+                    const double *xyz, int32_t n_tets, const int32_t *tet, const int32_t *nbr,
+                    const int32_t *periodic_nbr, const uint8_t *node_dirichlet, int32_t n_faces,
+                    const int32_t *face_nodes, const int32_t *face_tet,
+                    const double *work_function_eV);
+
+/*
+ * Launch tuning (an autotuner's knobs; none changes what is computed except
+ * pcg_cheb_degree, which changes the preconditioner but not the stopping
+ * rule, so the potential meets the same tolerance):
+ *   particle_blocks_per_sm  blocks of 256 threads per SM of the particle
+ *                           kernels (1..64; default 8)
+ *   walk_form               fused step: 0 by precision (FP64 persistent lanes,
+ *                           FP32 coherent warps), 1 coherent warps (a warp
+ *                           walks 32 consecutive SPs to the end), 2 persistent
+ *                           lanes (a lane takes the next SP from its warp's
+ *                           queue); the SP results are identical
+ *   pcg_blocks_per_sm       batch solve (mesh_load_batch): at most this many
+ *                           blocks per SM (0 = as many as fit; 0..64); the
+ *                           one-system solver ignores it
+ *   pcg_cheb_degree         as pic_params.pcg_cheb_degree (0..32)
+ * pic_set_tuning takes effect from the next call and drops captured graphs;
+ * PIC_ERR_ARG for a value out of range.  t: HOST.
+ */
+typedef struct {
+    int32_t particle_blocks_per_sm;
+    int32_t walk_form;
+    int32_t pcg_blocks_per_sm;
+    int32_t pcg_cheb_degree;
+} pic_tuning;
+int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
+int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);
 
 /* Sizes of the loaded mesh and of the launches (info: HOST). */
 int pic_mesh_info(pic_ctx ctx, pic_info *info);

@@ -81,17 +81,33 @@ struct pic_ctx_s {
     double *d0 = nullptr, *d1 = nullptr;
     float *d32_0 = nullptr, *d32_1 = nullptr;
     double cheb_b = 2.0;   // Gershgorin bound of D^-1 M
+    // replicas of a batch (1 for a single mesh)
+    int n_rep = 1, n_rows = 0;
+    int *tet_rep = nullptr, *face_rep = nullptr, *rep_face_off = nullptr;
+    double *rep_L = nullptr, *E0_rep = nullptr;
+    int *grp = nullptr, *blk_grp = nullptr;
+    unsigned *grp_bar = nullptr;
     double *partials = nullptr;
     PcgLaunch plan{};
     pic_step_stats *dstats = nullptr;  // per-step stats of pic_step
     long long dstats_cap = 0;
     pic_step_stats *sstats = nullptr;  // scratch stats of the split calls
+    pic_step_stats *slot = nullptr;    // statistics of the step in progress
+    // CUDA graphs of one step, one per particle-buffer parity (graph_state:
+    // 1 captured, 0 not tried, -1 capture refused: direct launches)
+    cudaStream_t cap_s = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long glaunch[2] = {0, 0};
+    int graph_state = 0;
     // staging
     void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t stage_sz[4] = {0, 0, 0, 0};
     int64_t step = 0;
     long long launches = 0;
     int pgrid = 0;
+    // launch tuning (pic_set_tuning)
+    int walk_form = WALK_FORM_AUTO, pcg_bps = 0;
+    std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     // profiling
     bool prof = false;
     std::vector<ProfRec> prof_recs;
@@ -180,8 +196,20 @@ template <typename T> cudaError_t dalloc(pic_ctx c, T **p, size_t n)
     return e;
 }
 
+void free_graphs(pic_ctx c)
+{
+    for (int a = 0; a < 2; ++a) {
+        if (c->gexec[a])
+            cudaGraphExecDestroy(c->gexec[a]);
+        c->gexec[a] = nullptr;
+        c->glaunch[a] = 0;
+    }
+    c->graph_state = 0;
+}
+
 void free_mesh(pic_ctx c)
 {
+    free_graphs(c);
     for (void *q : c->allocs)
         cudaFree(q);
     c->allocs.clear();
@@ -266,8 +294,10 @@ template <typename R> MeshView<R> view(pic_ctx c)
     m.wf = c->wf;
     m.xyz = c->xyz;
     m.n_faces = c->F;
-    m.Lx = c->hi[0] - c->lo[0];
-    m.Ly = c->hi[1] - c->lo[1];
+    m.tet_rep = c->tet_rep;
+    m.face_rep = c->face_rep;
+    m.rep_face_off = c->rep_face_off;
+    m.rep_L = c->rep_L;
     return m;
 }
 
@@ -290,7 +320,7 @@ __global__ void k_phi_to_x(int n, const int *dof_node, const double *phi, double
 {
     int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d < n)
-        x[d] = phi[dof_node[d]];
+        x[d] = dof_node[d] >= 0 ? phi[dof_node[d]] : 0.0;
 }
 __global__ void k_zero_dirichlet(int N, const unsigned char *dir, double *phi)
 {
@@ -299,19 +329,24 @@ __global__ void k_zero_dirichlet(int N, const unsigned char *dir, double *phi)
         phi[i] = 0.0;
 }
 
-int refresh_field(pic_ctx c)
+// E from Phi; at the end of a pic_step step it also files the step's
+// statistics and advances the device-side step index.
+int refresh_field(pic_ctx c, bool end_of_step = false)
 {
+    DevState *st = end_of_step ? c->st : nullptr;
     if (fp64(c))
-        LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, c->phi, (Vec4d *)c->E));
+        LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, c->phi, (Vec4d *)c->E,
+                                             st, c->slot));
     else
-        LAUNCH(K_FIELD, launch_field<float>(c->s, c->T, c->rec32, c->tet4, c->phi, (float4 *)c->E));
+        LAUNCH(K_FIELD, launch_field<float>(c->s, c->T, c->rec32, c->tet4, c->phi, (float4 *)c->E,
+                                            st, c->slot));
     return PIC_OK;
 }
 
 int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
 {
     PcgArgs g{};
-    g.n = c->n_free;
+    g.n = c->n_rows;
     g.n_pad = c->n_pad;
     g.n_slices = c->n_slices;
     g.slice_ptr = c->slice_ptr;
@@ -378,7 +413,13 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
     g.d32_0 = c->d32_0;
     g.d32_1 = c->d32_1;
     g.inner_max = c->p.ir_inner_max_iter;
+    g.n_groups = c->plan.n_groups;
+    g.grp = c->grp;
+    g.blk_grp = c->blk_grp;
+    g.grp_bar = c->grp_bar;
     CK(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->s));
+    if (c->plan.n_groups > 0)
+        CK(cudaMemsetAsync(c->grp_bar, 0, sizeof(unsigned) * c->plan.n_groups, c->s));
     LAUNCH(K_PCG, launch_pcg(c->s, c->plan, g));
     return PIC_OK;
 }
@@ -471,6 +512,8 @@ extern "C" int pic_destroy(pic_ctx c)
     }
     for (auto e : c->ev_pool)
         cudaEventDestroy(e);
+    if (c->cap_s)
+        cudaStreamDestroy(c->cap_s);
     delete c;
     return PIC_OK;
 }
@@ -478,13 +521,16 @@ extern "C" int pic_destroy(pic_ctx c)
 // ===========================================================================
 // mesh
 // ===========================================================================
-extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, const int32_t *tet,
-                         const int32_t *nbr, const int32_t *pnbr, const uint8_t *dir,
-                         int32_t F, const int32_t *face_nodes, const int32_t *face_tet,
-                         const double *wf)
+// Loads R meshes (replicas) given as one set of arrays with global indices;
+// replica r owns nodes [rno[r], rno[r+1]) and tetrahedra [rto[r], rto[r+1]),
+// its faces are contiguous, E0r[r] is its applied field.  A single mesh is
+// the case R = 1.
+static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rto,
+                     const double *E0r, int32_t N, const double *xyz, int32_t T,
+                     const int32_t *tet, const int32_t *nbr, const int32_t *pnbr,
+                     const uint8_t *dir, int32_t F, const int32_t *face_nodes,
+                     const int32_t *face_tet, const double *wf)
 {
-    if (!c)
-        return fail(nullptr, PIC_ERR_ARG, "null context");
     CK(cudaSetDevice(c->dev));
     if (N < 4 || T < 1 || F < 0 || !xyz || !tet || !nbr || !dir ||
         (F > 0 && (!face_nodes || !face_tet || !wf)))
@@ -540,12 +586,62 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
         if (!(det > 0))
             return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld not positively oriented", t);
     }
-    for (int i = 0; i < 3; ++i)
-        c->lo[i] = c->hi[i] = xyz[i];
-    for (long long n = 0; n < N; ++n)
+    // ---- replicas ------------------------------------------------------------
+    if (R < 1 || !rno || !rto || !E0r || rno[0] != 0 || rto[0] != 0 || rno[R] != N || rto[R] != T)
+        return fail(c, PIC_ERR_ARG, "mesh_load: bad replica offsets");
+    for (int r = 0; r < R; ++r)
+        if (rno[r + 1] <= rno[r] || rto[r + 1] <= rto[r] || !std::isfinite(E0r[r]))
+            return fail(c, PIC_ERR_ARG, "mesh_load: replica %d empty or bad E0", r);
+    std::vector<int> tet_rep((size_t)T), face_rep((size_t)F + 1, 0), rep_face_off((size_t)R + 1, 0);
+    for (int r = 0; r < R; ++r)
+        for (long long t = rto[r]; t < rto[r + 1]; ++t)
+            tet_rep[t] = r;
+    for (long long t = 0; t < T; ++t) {
+        int r = tet_rep[t];
+        for (int k = 0; k < 4; ++k) {
+            int v = tet[4 * t + k], b = nbr[4 * t + k];
+            if (v < rno[r] || v >= rno[r + 1])
+                return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld uses a node of another replica", t);
+            if ((b >= 0 && tet_rep[b] != r) ||
+                (b == PIC_BND_SIDE && tet_rep[pnbr[4 * t + k]] != r))
+                return fail(c, PIC_ERR_MESH, "mesh_load: tet %lld neighbours another replica", t);
+        }
+    }
+    for (long long f = 0; f < F; ++f) {
+        int r = tet_rep[face_tet[f]];
+        if (f > 0 && r < face_rep[f - 1])
+            return fail(c, PIC_ERR_MESH, "mesh_load: faces are not grouped by replica");
+        face_rep[f] = r;
+        for (int k = 0; k < 3; ++k)
+            if (face_nodes[3 * f + k] < rno[r] || face_nodes[3 * f + k] >= rno[r + 1])
+                return fail(c, PIC_ERR_MESH, "mesh_load: face %lld uses a node of another replica", f);
+    }
+    for (int r = 0, f = 0; r <= R; ++r) {
+        while (f < F && face_rep[f] < r)
+            ++f;
+        rep_face_off[r] = f;
+    }
+    // bounding box of each replica (its periodic box) and of everything
+    std::vector<double> rlo(3 * (size_t)R), rhi(3 * (size_t)R), rep_L(2 * (size_t)R);
+    for (int r = 0; r < R; ++r) {
+        for (int i = 0; i < 3; ++i)
+            rlo[3 * r + i] = rhi[3 * r + i] = xyz[3LL * rno[r] + i];
+        for (long long n = rno[r]; n < rno[r + 1]; ++n)
+            for (int i = 0; i < 3; ++i) {
+                rlo[3 * r + i] = std::min(rlo[3 * r + i], xyz[3 * n + i]);
+                rhi[3 * r + i] = std::max(rhi[3 * r + i], xyz[3 * n + i]);
+            }
+        rep_L[2 * r + 0] = rhi[3 * r + 0] - rlo[3 * r + 0];
+        rep_L[2 * r + 1] = rhi[3 * r + 1] - rlo[3 * r + 1];
+    }
+    for (int i = 0; i < 3; ++i) {
+        c->lo[i] = rlo[i];
+        c->hi[i] = rhi[i];
+    }
+    for (int r = 1; r < R; ++r)
         for (int i = 0; i < 3; ++i) {
-            c->lo[i] = std::min(c->lo[i], xyz[3 * n + i]);
-            c->hi[i] = std::max(c->hi[i], xyz[3 * n + i]);
+            c->lo[i] = std::min(c->lo[i], rlo[3 * r + i]);
+            c->hi[i] = std::max(c->hi[i], rhi[3 * r + i]);
         }
 
     // ---- packed neighbour table --------------------------------------------
@@ -558,13 +654,13 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
         for (int k = 0; k < 4; ++k) {
             if (nbr[4 * t + k] != PIC_BND_SIDE)
                 continue;
-            int code = -1;
+            int code = -1, r = tet_rep[t];
             for (int ax = 0; ax < 2 && code < 0; ++ax) {
                 bool at_lo = true, at_hi = true;
                 for (int m = 0; m < 3; ++m) {
                     double q = xyz[3LL * face_vertex(t, k, m) + ax];
-                    at_lo = at_lo && q == c->lo[ax];
-                    at_hi = at_hi && q == c->hi[ax];
+                    at_lo = at_lo && q == rlo[3 * r + ax];
+                    at_hi = at_hi && q == rhi[3 * r + ax];
                 }
                 if (at_lo)
                     code = 2 * ax;      // +L
@@ -604,11 +700,19 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     }
 
     // ---- free DOFs and the stiffness pattern --------------------------------
-    std::vector<int> dof((size_t)N);
-    int nf = 0;
-    for (int n = 0; n < N; ++n)
-        dof[n] = dir[n] ? -1 : nf++;
-    if (nf == 0)
+    // each replica's rows start on a 32-row slice, so that no slice (and no
+    // solver block) mixes two replicas; rows between replicas are padding
+    std::vector<int> dof((size_t)N), rep_slice((size_t)R + 1, 0);
+    int nf = 0, nreal = 0;
+    for (int r = 0; r < R; ++r) {
+        nf = (nf + 31) & ~31;
+        rep_slice[r] = nf / 32;
+        for (long long n = rno[r]; n < rno[r + 1]; ++n)
+            dof[n] = dir[n] ? -1 : (++nreal, nf++);
+    }
+    nf = (nf + 31) & ~31;
+    rep_slice[R] = nf / 32;
+    if (nreal == 0)
         return fail(c, PIC_ERR_MESH, "mesh_load: no free nodes");
     std::vector<long long> rs((size_t)nf + 1, 0);
     for (long long t = 0; t < T; ++t)
@@ -756,7 +860,9 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     c->T = T;
     c->F = F;
     c->NQ = 3 * F;
-    c->n_free = nf;
+    c->n_free = nreal;
+    c->n_rows = nf;
+    c->n_rep = R;
     c->n_pad = n_pad;
     c->n_slices = n_slices;
     c->sell_len = sell_len;
@@ -832,8 +938,36 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     PcgHalo halo;
     c->lcol = c->halo_ptr = c->halo_idx = nullptr;
     CK(pcg_plan(sptr.data(), scol.data(), n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
-                &c->plan, &halo));
-    CK(dalloc(c, &c->partials, (size_t)2 * c->plan.grid * 4));
+                R, rep_slice.data(), c->pcg_bps, &c->plan, &halo));
+    c->rep_slice = rep_slice;
+    // a batch solve can be re-planned with more blocks (pic_set_tuning)
+    const int max_grid = c->plan.n_groups > 0
+                             ? std::max(c->plan.grid, pcg_max_group_blocks(c->p.precision, c->num_sms))
+                             : c->plan.grid;
+    CK(dalloc(c, &c->partials, (size_t)2 * max_grid * 4));
+    c->grp = c->blk_grp = nullptr;
+    c->grp_bar = nullptr;
+    if (c->plan.n_groups > 0) {
+        CK(dalloc(c, &c->grp, halo.grp.size()));
+        CK(dalloc(c, &c->blk_grp, (size_t)max_grid));
+        CK(dalloc(c, &c->grp_bar, (size_t)c->plan.n_groups));
+        CK(cudaMemcpyAsync(c->grp, halo.grp.data(), sizeof(int) * halo.grp.size(),
+                           cudaMemcpyHostToDevice, c->s));
+        CK(cudaMemcpyAsync(c->blk_grp, halo.blk_grp.data(), sizeof(int) * halo.blk_grp.size(),
+                           cudaMemcpyHostToDevice, c->s));
+    }
+    CK(dalloc(c, &c->tet_rep, (size_t)T));
+    CK(dalloc(c, &c->face_rep, (size_t)F + 1));
+    CK(dalloc(c, &c->rep_face_off, (size_t)R + 1));
+    CK(dalloc(c, &c->rep_L, 2 * (size_t)R));
+    CK(dalloc(c, &c->E0_rep, (size_t)R));
+    CK(cudaMemcpyAsync(c->tet_rep, tet_rep.data(), sizeof(int) * T, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->face_rep, face_rep.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->rep_face_off, rep_face_off.data(), sizeof(int) * (R + 1),
+                       cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->rep_L, rep_L.data(), sizeof(double) * 2 * R, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->E0_rep, E0r, sizeof(double) * R, cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
     if (c->plan.resident) {
         CK(dalloc(c, &c->lcol, halo.lcol.size()));
         CK(dalloc(c, &c->halo_ptr, halo.halo_ptr.size()));
@@ -848,6 +982,8 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
         CK(cudaStreamSynchronize(c->s));
     }
     CK(dalloc(c, &c->sstats, 1));
+    CK(dalloc(c, &c->slot, 1));
+    CK(cudaMemsetAsync(c->slot, 0, sizeof(pic_step_stats), c->s));
 
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->s);
@@ -920,7 +1056,7 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
         ++c->launches;
     }
     if (e == cudaSuccess) {
-        e = launch_neumann(c->s, nf, d_fptr, d_fcon, c->tet4, c->xyz, c->p.E0, c->fN);
+        e = launch_neumann(c->s, nf, d_fptr, d_fcon, c->tet4, c->xyz, c->tet_rep, c->E0_rep, c->fN);
         ++c->launches;
     }
     if (e == cudaSuccess) {
@@ -958,6 +1094,75 @@ extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, con
     return PIC_OK;
 }
 
+extern "C" int mesh_load(pic_ctx c, int32_t N, const double *xyz, int32_t T, const int32_t *tet,
+                         const int32_t *nbr, const int32_t *pnbr, const uint8_t *dir,
+                         int32_t F, const int32_t *face_nodes, const int32_t *face_tet,
+                         const double *wf)
+{
+    if (!c)
+        return fail(nullptr, PIC_ERR_ARG, "null context");
+    int32_t rno[2] = {0, N}, rto[2] = {0, T};
+    double e0 = c->p.E0;
+    return load_mesh(c, 1, rno, rto, &e0, N, xyz, T, tet, nbr, pnbr, dir, F, face_nodes,
+                     face_tet, wf);
+}
+
+extern "C" int mesh_load_batch(pic_ctx c, int32_t n_rep, const int32_t *rep_node_off,
+                               const int32_t *rep_tet_off, const double *E0_rep, int32_t N,
+                               const double *xyz, int32_t T, const int32_t *tet,
+                               const int32_t *nbr, const int32_t *pnbr, const uint8_t *dir,
+                               int32_t F, const int32_t *face_nodes, const int32_t *face_tet,
+                               const double *wf)
+{
+    if (!c)
+        return fail(nullptr, PIC_ERR_ARG, "null context");
+    if (n_rep < 1 || n_rep > (1 << 16))
+        return fail(c, PIC_ERR_ARG, "mesh_load_batch: bad replica count");
+    return load_mesh(c, n_rep, rep_node_off, rep_tet_off, E0_rep, N, xyz, T, tet, nbr, pnbr, dir,
+                     F, face_nodes, face_tet, wf);
+}
+
+extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
+{
+    if (!c || !t)
+        return fail(c, PIC_ERR_ARG, "null argument");
+    t->particle_blocks_per_sm = c->pgrid / c->num_sms;
+    t->walk_form = c->walk_form;
+    t->pcg_blocks_per_sm = c->pcg_bps;
+    t->pcg_cheb_degree = c->p.pcg_cheb_degree;
+    return PIC_OK;
+}
+
+extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
+{
+    if (!c || !t)
+        return fail(c, PIC_ERR_ARG, "null argument");
+    if (t->particle_blocks_per_sm < 1 || t->particle_blocks_per_sm > 64 || t->walk_form < 0 ||
+        t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
+        t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 ||
+        (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
+        return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->loaded && c->plan.n_groups > 0 && t->pcg_blocks_per_sm != c->pcg_bps) {
+        PcgLaunch plan;
+        PcgHalo halo;
+        CK(pcg_plan(nullptr, nullptr, c->n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
+                    c->n_rep, c->rep_slice.data(), t->pcg_blocks_per_sm, &plan, &halo));
+        CK(cudaMemcpy(c->grp, halo.grp.data(), sizeof(int) * halo.grp.size(),
+                      cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->blk_grp, halo.blk_grp.data(), sizeof(int) * halo.blk_grp.size(),
+                      cudaMemcpyHostToDevice));
+        c->plan = plan;
+    }
+    free_graphs(c);
+    c->pgrid = t->particle_blocks_per_sm * c->num_sms;
+    c->walk_form = t->walk_form;
+    c->pcg_bps = t->pcg_blocks_per_sm;
+    c->p.pcg_cheb_degree = t->pcg_cheb_degree;
+    return PIC_OK;
+}
+
 extern "C" int pic_mesh_info(pic_ctx c, pic_info *info)
 {
     REQUIRE_MESH();
@@ -975,6 +1180,10 @@ extern "C" int pic_mesh_info(pic_ctx c, pic_info *info)
         info->box_lo[i] = c->lo[i];
         info->box_hi[i] = c->hi[i];
     }
+    info->n_rep = c->n_rep;
+    info->n_rows = c->n_rows;
+    info->pcg_resident = c->plan.resident ? 1 : 0;
+    info->graph = c->graph_state;
     return PIC_OK;
 }
 
@@ -1009,10 +1218,13 @@ template <typename R> static int do_inject(pic_ctx c, int64_t step)
 {
     RunConst k = run_const(c);
     MeshView<R> m = view<R>(c);
-    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, step, c->qcount, &c->st->err));
+    const long long step_h = step;   // pageable source: staged before the call returns
+    CK(cudaMemcpyAsync(&c->st->hdr.step, &step_h, sizeof step_h, cudaMemcpyHostToDevice, c->s));
+    const long long *stepp = &c->st->hdr.step;
+    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, stepp, c->qcount, &c->st->err));
     LAUNCH(K_INJECT_SCAN, launch_inject_scan(c->s, c->NQ, c->qcount, c->qoff, c->st, c->a,
                                              c->p.capacity, 1, c->sstats));
-    LAUNCH(K_INJECT_EMIT, launch_inject_emit<R>(c->s, c->pgrid, m, k, step, c->NQ, c->qoff,
+    LAUNCH(K_INJECT_EMIT, launch_inject_emit<R>(c->s, c->pgrid, m, k, stepp, c->NQ, c->qoff,
                                                 parts<R>(c, c->a), c->st));
     return PIC_OK;
 }
@@ -1112,29 +1324,109 @@ extern "C" int poisson_solve(pic_ctx c, double *phi, int32_t *iters, double *rel
     return PIC_OK;
 }
 
-template <typename R> static int step_once(pic_ctx c, pic_step_stats *ds)
+// One PIC cycle, all on the device: the step index comes from st->hdr and
+// the statistics go to c->slot, so the same launches can be captured once in
+// a CUDA graph and replayed every step of the same buffer parity.
+template <typename R> static int step_once(pic_ctx c)
 {
     RunConst k = run_const(c);
     MeshView<R> m = view<R>(c);
-    const long long kstep = c->step;
+    const long long *stepp = &c->st->hdr.step;
+    pic_step_stats *ds = c->slot;
     CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
     CK(cudaMemsetAsync(&c->st->cnt[1 - c->a], 0, sizeof(unsigned long long), c->s));
     CK(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned long long), c->s));
-    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, kstep, c->qcount, &c->st->err));
+    LAUNCH(K_INJECT_COUNT, launch_inject_count<R>(c->s, c->NQ, m, k, stepp, c->qcount, &c->st->err));
     LAUNCH(K_INJECT_SCAN, launch_inject_scan(c->s, c->NQ, c->qcount, c->qoff, c->st, c->a,
                                              c->p.capacity, 0, ds));
-    LAUNCH(K_STEP_FUSED, launch_step_fused<R>(c->s, c->pgrid, m, k, kstep, c->NQ, c->qoff,
+    LAUNCH(K_STEP_FUSED, launch_step_fused<R>(c->s, c->pgrid, c->walk_form, m, k, stepp, c->NQ,
+                                              c->qoff,
                                               parts<R>(c, c->a), parts<R>(c, 1 - c->a), c->a,
                                               c->st, c->W, ds));
     c->a = 1 - c->a;
     int rc = run_pcg(c, ds, &c->st->cnt[c->a]);
     if (rc)
         return rc;
-    rc = refresh_field(c);
+    rc = refresh_field(c, true);
     if (rc)
         return rc;
-    c->step = kstep + 1;
+    c->step = c->step + 1;
     return PIC_OK;
+}
+
+static int step_direct(pic_ctx c)
+{
+    return fp64(c) ? step_once<double>(c) : step_once<float>(c);
+}
+
+// Capture the step of the current parity into a graph.  Capture runs on a
+// stream of the context's own (the caller's stream may be the legacy default
+// stream, which cannot be captured); the graph is replayed on the caller's
+// stream.  Capturing launches nothing, so the host-side step state is put
+// back afterwards.  If the driver refuses any part of the capture the
+// context keeps launching the kernels directly (graph_state = -1).
+static void capture_step(pic_ctx c)
+{
+    const int a = c->a;
+    const int64_t step = c->step;
+    const long long launches = c->launches;
+    cudaStream_t user = c->s;
+    if (!c->cap_s && cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_s = nullptr;
+        c->graph_state = -1;
+        return;
+    }
+    if (cudaStreamSynchronize(user) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_state = -1;
+        return;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->cap_s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_state = -1;
+        return;
+    }
+    c->s = c->cap_s;
+    const std::string err = c->err;
+    int rc = step_direct(c);
+    cudaError_t e = cudaStreamEndCapture(c->cap_s, &g);
+    c->s = user;
+    const long long per_step = c->launches - launches;
+    c->launches = launches;
+    c->a = a;
+    c->step = step;
+    cudaGraphExec_t x = nullptr;
+    if (rc == PIC_OK && e == cudaSuccess && g &&
+        cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+        c->gexec[a] = x;
+        c->glaunch[a] = per_step;
+        c->graph_state = 1;
+    } else {
+        cudaGetLastError();
+        c->err = err;
+        c->graph_state = -1;
+    }
+    if (g)
+        cudaGraphDestroy(g);
+}
+
+static int run_step(pic_ctx c)
+{
+    if (c->p.graph && !c->prof && c->graph_state >= 0) {
+        const int a = c->a;
+        if (!c->gexec[a])
+            capture_step(c);
+        if (c->gexec[a]) {
+            CK(cudaGraphLaunch(c->gexec[a], c->s));
+            c->launches += c->glaunch[a];
+            c->a = 1 - a;
+            c->step = c->step + 1;
+            return PIC_OK;
+        }
+    }
+    return step_direct(c);
 }
 
 extern "C" int pic_step(pic_ctx c, int64_t n, pic_step_stats *stats)
@@ -1148,8 +1440,11 @@ extern "C" int pic_step(pic_ctx c, int64_t n, pic_step_stats *stats)
     if (rc)
         return rc;
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(pic_step_stats) * (size_t)n, c->s));
+    const StepHdr hdr{c->step, c->step, c->dstats, c->dstats_cap};   // staged before return
+    CK(cudaMemcpyAsync(&c->st->hdr, &hdr, sizeof hdr, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemsetAsync(c->slot, 0, sizeof(pic_step_stats), c->s));
     for (int64_t s = 0; s < n; ++s) {
-        rc = fp64(c) ? step_once<double>(c, c->dstats + s) : step_once<float>(c, c->dstats + s);
+        rc = run_step(c);
         if (rc)
             return rc;
     }
@@ -1210,7 +1505,7 @@ extern "C" int pic_set_potential(pic_ctx c, const double *phi)
     CK(cudaMemcpyAsync(c->phi, phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
     k_zero_dirichlet<<<(c->N + 255) / 256, 256, 0, c->s>>>(c->N, c->dir, c->phi);
     ++c->launches;
-    k_phi_to_x<<<(c->n_free + 255) / 256, 256, 0, c->s>>>(c->n_free, c->dof_node, c->phi, c->x);
+    k_phi_to_x<<<(c->n_rows + 255) / 256, 256, 0, c->s>>>(c->n_rows, c->dof_node, c->phi, c->x);
     ++c->launches;
     CK(cudaGetLastError());
     int rc = refresh_field(c);

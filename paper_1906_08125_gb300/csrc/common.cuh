@@ -79,7 +79,11 @@ template <typename R> struct MeshView {
     const double *wf;                   // [F]
     const double *xyz;                  // [N*3]
     int n_faces;
-    double Lx, Ly;                      // periodic shifts
+    // replicas (a batch; one replica for a single mesh)
+    const int *tet_rep;                 // [T] replica of each tetrahedron
+    const int *face_rep;                // [F] replica of each emitting face
+    const int *rep_face_off;            // [R+1] first face of each replica
+    const double *rep_L;                // [2R] periodic box length in x and y
 };
 
 // Run constants of the particle kernels.
@@ -94,6 +98,18 @@ struct RunConst {
 };
 
 // Device-side bookkeeping of one context.
+// Step bookkeeping kept on the device, so that a whole step can be captured
+// in a CUDA graph and replayed: the index of the step being run (key of the
+// random numbers and part of the SP ids) and the per-step statistics array of
+// the current pic_step call.  The last kernel of a step copies the step's
+// statistics into ring[step - step0] and advances step.
+struct StepHdr {
+    long long step;
+    long long step0;
+    pic_step_stats *ring;
+    long long ring_cap;
+};
+
 struct DevState {
     unsigned long long cnt[2];  // SPs in particle buffer 0 / 1
     long long n_new;            // SPs injected in this step (after the scan)
@@ -103,6 +119,7 @@ struct DevState {
     int pad;
     unsigned bar_count, bar_gen;  // grid barrier of the persistent PCG
     unsigned long long work;      // next unclaimed SP of the fused step (work queue)
+    StepHdr hdr;
 };
 
 // ---------------------------------------------------------------------------
@@ -116,25 +133,27 @@ cudaError_t launch_matrix_values(cudaStream_t s, long long nnz, const long long 
                                  const long long *sell_pos, const int *slot_row,
                                  const int *slot_col, double *val64, float *val32,
                                  double *dinv64, float *dinv32);
-cudaError_t launch_neumann(cudaStream_t s, int n_free, const int *fptr, const int *fcontrib,
-                           const int4 *tet, const double *xyz, double E0, double *fN);
+cudaError_t launch_neumann(cudaStream_t s, int n_rows, const int *fptr, const int *fcontrib,
+                           const int4 *tet, const double *xyz, const int *tet_rep,
+                           const double *E0_rep, double *fN);
 cudaError_t launch_face_geometry(cudaStream_t s, int F, const int *face_nodes,
                                  const double *xyz, double *nhat, double *area);
 
 // particles
 template <typename R>
 cudaError_t launch_field(cudaStream_t s, int T, const typename Rec<R>::type *rec,
-                         const int4 *tet, const double *phi, typename Rec<R>::vec4 *E);
+                         const int4 *tet, const double *phi, typename Rec<R>::vec4 *E,
+                         DevState *end_step, pic_step_stats *slot);
 template <typename R>
 cudaError_t launch_inject_count(cudaStream_t s, int nq, MeshView<R> m, RunConst c,
-                                long long step, int *qcount, int *err);
+                                const long long *step, int *qcount, int *err);
 cudaError_t launch_inject_scan(cudaStream_t s, int nq, const int *qcount, long long *qoff,
                                DevState *st, int buf, long long capacity, int split_mode,
                                pic_step_stats *stats);
 template <typename R>
 cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
-                               long long step, int nq, const long long *qoff, Particles<R> P,
-                               DevState *st);
+                               const long long *step, int nq, const long long *qoff,
+                               Particles<R> P, DevState *st);
 template <typename R>
 cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                                  Particles<R> A, Particles<R> B, int a, DevState *st,
@@ -142,9 +161,12 @@ cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunCon
 template <typename R>
 cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                            Particles<R> A, int a, DevState *st, unsigned long long *W);
+// walk_form: WALK_FORM_AUTO (persistent lanes for FP64, coherent warps for
+// FP32), WALK_FORM_COHERENT or WALK_FORM_PERSISTENT
+enum { WALK_FORM_AUTO = 0, WALK_FORM_COHERENT = 1, WALK_FORM_PERSISTENT = 2 };
 template <typename R>
-cudaError_t launch_step_fused(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
-                              long long step, int nq, const long long *qoff, Particles<R> A,
+cudaError_t launch_step_fused(cudaStream_t s, int grid, int walk_form, MeshView<R> m, RunConst c,
+                              const long long *step, int nq, const long long *qoff, Particles<R> A,
                               Particles<R> B, int a, DevState *st, unsigned long long *W,
                               pic_step_stats *stats);
 template <typename R>
@@ -198,6 +220,13 @@ struct PcgArgs {
     float cheb_c1f[32], cheb_c2f[32], cheb_inv_thetaf;
     double *d0, *d1;          // FP64 halo buffers of the Chebyshev steps [n_pad]
     float *d32_0, *d32_1;     // FP32 halo buffers of the Chebyshev steps [n_pad]
+    // independent systems solved side by side (a batch of replicas): group g
+    // owns slices [grp[4g], grp[4g+1]) and blocks [grp[4g+2], +grp[4g+3]);
+    // n_groups == 0 means one system over the whole grid
+    int n_groups;
+    const int *grp;           // [4 * n_groups]
+    const int *blk_grp;       // [grid] group of each block
+    unsigned *grp_bar;        // [n_groups] barrier counters, zero at launch
 };
 struct PcgLaunch {
     int grid, block;
@@ -208,16 +237,25 @@ struct PcgLaunch {
     int max_rows;          // resident: 32 * most slices owned by one block
     long long max_chunk;   // resident: most stored matrix entries owned by one block
     int max_local;         // resident: most own rows + halo columns of one block
+    int n_groups;          // general: independent systems (0: one system, whole grid)
 };
-// Host-side tables of the resident kernels: local column indices and halos.
+// Host-side tables: local column indices and halos of the resident kernels;
+// group tables of the general kernels when several systems are solved side
+// by side.
 struct PcgHalo {
     std::vector<int> lcol, halo_ptr, halo_idx;
+    std::vector<int> grp, blk_grp;
 };
 // message returned by pic_last_error(NULL)
 void set_global_error(const char *msg);
 
+// grp_slices[g] .. grp_slices[g+1]: slices of system g (n_sys >= 1)
+// blocks_per_sm > 0 caps the blocks of a batch solve at blocks_per_sm per SM
 cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slices,
-                     int num_sms, int precision, int variant, PcgLaunch *plan, PcgHalo *halo);
+                     int num_sms, int precision, int variant, int n_sys, const int *grp_slices,
+                     int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo);
+// the most blocks a batch solve can use (its partial-sum buffer is sized for it)
+int pcg_max_group_blocks(int precision, int num_sms);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
 
 }  // namespace pf

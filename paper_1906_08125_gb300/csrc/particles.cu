@@ -136,16 +136,17 @@ __device__ __forceinline__ int walk_step(const MeshView<R> &m, int walk_max, R r
         return FATE_ABSORBED;
     int v = NB_SIDE - p;
     int sc = (v >> 2) & 3;
+    const double *L = m.rep_L + 2 * m.tet_rep[t];   // the replica's periodic box
     entered = v & 3;
     t = v >> 4;
     if (sc == 0)
-        r[0] = r[0] + (R)m.Lx;
+        r[0] = r[0] + (R)L[0];
     else if (sc == 1)
-        r[0] = r[0] + (R)(-m.Lx);
+        r[0] = r[0] + (R)(-L[0]);
     else if (sc == 2)
-        r[1] = r[1] + (R)m.Ly;
+        r[1] = r[1] + (R)L[1];
     else
-        r[1] = r[1] + (R)(-m.Ly);
+        r[1] = r[1] + (R)(-L[1]);
     ++wraps;
     return WALK_CONTINUE;
 }
@@ -209,6 +210,9 @@ __device__ bool emit(const MeshView<R> &m, const RunConst &c, long long step, in
                      double r[3], double v[3], int &cell, long long &id)
 {
     int f = q / 3, vtx = q - 3 * f;
+    const int rep = m.face_rep[f];
+    const uint64_t seed = c.seed + (uint64_t)rep;                    // replica's stream
+    const uint64_t ql = (uint64_t)(q - 3 * m.rep_face_off[rep]);     // quadrangle in it
     const int *fn = m.face_nodes + 3 * f;
     int ia = fn[vtx], ib = fn[vtx == 2 ? 0 : vtx + 1], ic = fn[vtx == 0 ? 2 : vtx - 1];
     const double *V = m.xyz + 3 * (size_t)ia, *Vn = m.xyz + 3 * (size_t)ib;
@@ -216,15 +220,15 @@ __device__ bool emit(const MeshView<R> &m, const RunConst &c, long long step, in
     double R1 = 0.0, R2 = 0.0;
     bool ok = false;
     for (int a = 0; a < MAX_ATTEMPTS && !ok; ++a) {
-        R1 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, (uint64_t)(1 + 2 * a));
-        R2 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, (uint64_t)(2 + 2 * a));
+        R1 = uniform01(seed, (uint64_t)step, ql, (uint64_t)j, (uint64_t)(1 + 2 * a));
+        R2 = uniform01(seed, (uint64_t)step, ql, (uint64_t)j, (uint64_t)(2 + 2 * a));
         double l_next = R1 * 0.5, l_prev = R2 * 0.5;
         double l_v = (1.0 - l_next) - l_prev;
         ok = l_v >= l_next && l_v >= l_prev;
     }
     if (!ok)
         return false;
-    double R3 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, 255);
+    double R3 = uniform01(seed, (uint64_t)step, ql, (uint64_t)j, 255);
     int ft = m.face_tet[f];
     double E[3];
     e3(m.E[ft], E);
@@ -313,10 +317,25 @@ __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool
 // ---------------------------------------------------------------------------
 // field: E_t = -sum_i Phi_{v_i} grad N_i, constant per tetrahedron
 // ---------------------------------------------------------------------------
+// End of a step (see StepHdr): file the step's statistics and advance the
+// step index.  Run by one thread of the step's last kernel.
+__device__ __forceinline__ void end_step(DevState *st, pic_step_stats *slot)
+{
+    StepHdr &h = st->hdr;
+    long long i = h.step - h.step0;
+    if (i >= 0 && i < h.ring_cap)
+        h.ring[i] = *slot;
+    *slot = pic_step_stats{};
+    h.step = h.step + 1;
+}
+
 __global__ void k_field64(int T, const TetRec64 *__restrict__ rec, const int4 *__restrict__ tet,
-                          const double *__restrict__ phi, Vec4d *E)
+                          const double *__restrict__ phi, Vec4d *E, DevState *st,
+                          pic_step_stats *slot)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (st && t == 0)
+        end_step(st, slot);
     if (t >= T)
         return;
     TetRec64 r = load_rec(rec + t);
@@ -337,9 +356,12 @@ __global__ void k_field64(int T, const TetRec64 *__restrict__ rec, const int4 *_
 // -sum grad N_k), so that the FP32 gradients never multiply the large
 // absolute potential.
 __global__ void k_field32(int T, const TetRec32 *__restrict__ rec, const int4 *__restrict__ tet,
-                          const double *__restrict__ phi, float4 *E)
+                          const double *__restrict__ phi, float4 *E, DevState *st,
+                          pic_step_stats *slot)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (st && t == 0)
+        end_step(st, slot);
     if (t >= T)
         return;
     TetRec32 r = load_rec(rec + t);
@@ -357,12 +379,13 @@ __global__ void k_field32(int T, const TetRec32 *__restrict__ rec, const int4 *_
 // injection: count per quadrangle (eqs. nsp, rnd_nsp) and exclusive scan
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_inject_count(int nq, MeshView<R> m, RunConst c, long long step, int *qcount,
-                               int *err)
+__global__ void k_inject_count(int nq, MeshView<R> m, RunConst c, const long long *stepp,
+                               int *qcount, int *err)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq)
         return;
+    const long long step = *stepp;
     int f = q / 3;
     double E[3];
     e3(m.E[m.face_tet[f]], E);
@@ -373,7 +396,9 @@ __global__ void k_inject_count(int nq, MeshView<R> m, RunConst c, long long step
     double J = fn_current(F, m.wf[f], c.fn_model);
     double Aq = m.face_area[f] / 3.0;
     double nsp = ((J * Aq) * c.dt) / (c.e_charge * c.w_sp);
-    double R0 = uniform01(c.seed, (uint64_t)step, (uint64_t)q, 0, 0);
+    const int rep = m.face_rep[f];
+    double R0 = uniform01(c.seed + (uint64_t)rep, (uint64_t)step,
+                          (uint64_t)(q - 3 * m.rep_face_off[rep]), 0, 0);
     double fl = floor(nsp);
     double frac = nsp - fl;
     long long cnt = (long long)fl + (R0 >= frac ? 0 : 1);
@@ -446,9 +471,10 @@ __global__ void __launch_bounds__(1024) k_inject_scan(int nq, const int *__restr
 
 // split API: write the fresh SPs at the end of buffer A
 template <typename R>
-__global__ void k_inject_emit(MeshView<R> m, RunConst c, long long step, int nq,
+__global__ void k_inject_emit(MeshView<R> m, RunConst c, const long long *stepp, int nq,
                               const long long *__restrict__ qoff, Particles<R> P, DevState *st)
 {
+    const long long step = *stepp;
     long long n_new = st->n_new, base = st->base;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long tn = blockIdx.x * (long long)blockDim.x + threadIdx.x; tn < n_new; tn += stride) {
@@ -604,12 +630,14 @@ __device__ __forceinline__ void start_sp(const MeshView<R> &m, const RunConst &c
 // fetches share L1 lines; on the FP32 path that locality is worth more than
 // the lanes that idle behind the warp's longest walk.
 template <typename R>
-__global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, long long step,
-                                                    int nq, const long long *__restrict__ qoff,
+__global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c,
+                                                    const long long *stepp, int nq,
+                                                    const long long *__restrict__ qoff,
                                                     Particles<R> A, Particles<R> B, int a,
                                                     DevState *st, unsigned long long *W,
                                                     pic_step_stats *stats)
 {
+    const long long step = *stepp;
     const long long n_old = (long long)st->cnt[a];
     const long long n = n_old + st->n_new;
     unsigned long long *cntB = &st->cnt[1 - a];
@@ -640,10 +668,11 @@ __global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c, l
 // above); used where the walk is arithmetic-bound (FP64 on this part).
 template <typename R>
 __global__ void __launch_bounds__(256) k_step_fused_persistent(
-    MeshView<R> m, RunConst c, long long step, int nq, const long long *__restrict__ qoff,
+    MeshView<R> m, RunConst c, const long long *stepp, int nq, const long long *__restrict__ qoff,
     Particles<R> A, Particles<R> B, int a, DevState *st, unsigned long long *W,
     pic_step_stats *stats)
 {
+    const long long step = *stepp;
     const long long n_old = (long long)st->cnt[a];
     const long long n = n_old + st->n_new;
     unsigned long long *cntB = &st->cnt[1 - a];
@@ -802,22 +831,22 @@ static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b
 
 template <>
 cudaError_t launch_field<double>(cudaStream_t s, int T, const TetRec64 *rec, const int4 *tet,
-                                 const double *phi, Vec4d *E)
+                                 const double *phi, Vec4d *E, DevState *st, pic_step_stats *slot)
 {
-    k_field64<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E);
+    k_field64<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E, st, slot);
     return cudaGetLastError();
 }
 template <>
 cudaError_t launch_field<float>(cudaStream_t s, int T, const TetRec32 *rec, const int4 *tet,
-                                const double *phi, float4 *E)
+                                const double *phi, float4 *E, DevState *st, pic_step_stats *slot)
 {
-    k_field32<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E);
+    k_field32<<<blocks_for(T, 256), 256, 0, s>>>(T, rec, tet, phi, E, st, slot);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_inject_count(cudaStream_t s, int nq, MeshView<R> m, RunConst c,
-                                long long step, int *qcount, int *err)
+                                const long long *step, int *qcount, int *err)
 {
     if (nq <= 0)
         return cudaSuccess;
@@ -835,8 +864,8 @@ cudaError_t launch_inject_scan(cudaStream_t s, int nq, const int *qcount, long l
 
 template <typename R>
 cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
-                               long long step, int nq, const long long *qoff, Particles<R> P,
-                               DevState *st)
+                               const long long *step, int nq, const long long *qoff,
+                               Particles<R> P, DevState *st)
 {
     k_inject_emit<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, P, st);
     return cudaGetLastError();
@@ -860,12 +889,14 @@ cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c, 
 }
 
 template <typename R>
-cudaError_t launch_step_fused(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
-                              long long step, int nq, const long long *qoff, Particles<R> A,
+cudaError_t launch_step_fused(cudaStream_t s, int grid, int walk_form, MeshView<R> m, RunConst c,
+                              const long long *step, int nq, const long long *qoff, Particles<R> A,
                               Particles<R> B, int a, DevState *st, unsigned long long *W,
                               pic_step_stats *stats)
 {
-    if (sizeof(R) == 8)
+    const bool persistent = walk_form == WALK_FORM_AUTO ? sizeof(R) == 8
+                                                         : walk_form == WALK_FORM_PERSISTENT;
+    if (persistent)
         k_step_fused_persistent<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
     else
         k_step_fused<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
@@ -901,9 +932,9 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
 
 #define PF_INSTANTIATE(R)                                                                      \
     template cudaError_t launch_inject_count<R>(cudaStream_t, int, MeshView<R>, RunConst,      \
-                                                long long, int *, int *);                      \
+                                                const long long *, int *, int *);              \
     template cudaError_t launch_inject_emit<R>(cudaStream_t, int, MeshView<R>, RunConst,       \
-                                               long long, int, const long long *,              \
+                                               const long long *, int, const long long *,      \
                                                Particles<R>, DevState *);                      \
     template cudaError_t launch_push_relocate<R>(cudaStream_t, int, MeshView<R>, RunConst,     \
                                                  Particles<R>, Particles<R>, int, DevState *,  \
@@ -911,8 +942,9 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
     template cudaError_t launch_deposit<R>(cudaStream_t, int, MeshView<R>, RunConst,           \
                                            Particles<R>, int, DevState *,                      \
                                            unsigned long long *);                              \
-    template cudaError_t launch_step_fused<R>(cudaStream_t, int, MeshView<R>, RunConst,        \
-                                              long long, int, const long long *, Particles<R>, \
+    template cudaError_t launch_step_fused<R>(cudaStream_t, int, int, MeshView<R>, RunConst,   \
+                                              const long long *, int, const long long *,       \
+                                              Particles<R>,                                    \
                                               Particles<R>, int, DevState *,                   \
                                               unsigned long long *, pic_step_stats *);         \
     template cudaError_t launch_pack<R>(cudaStream_t, long long, Particles<R>, double *,       \

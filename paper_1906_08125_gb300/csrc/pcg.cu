@@ -44,31 +44,50 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
     return *(const volatile int *)p;
 }
 
-// Grid-wide barrier over co-resident blocks (cooperative launch), one
-// atomic per block: block 0 adds 2^31 - (G - 1), every other block adds 1,
-// so the counter's top bit flips exactly when the last block arrives and the
-// low bits return to zero (the counter is cleared before each launch).  Each
-// block waits for the flip with an iteration limit; a block that waits too
-// long records PIC_ERR_TIMEOUT and the whole kernel returns.
-__device__ bool grid_sync(DevState *st)
+// The blocks that solve one system: the whole grid, or (for a batch of
+// independent systems) the group of blocks assigned to one of them.
+struct Grp {
+    unsigned *ctr;   // barrier counter of the group
+    int nb, rank;    // blocks in the group, this block's rank in it
+    int b0;          // first block of the group
+};
+
+__device__ __forceinline__ Grp grp_of(const PcgArgs &a)
+{
+    if (a.n_groups <= 0)
+        return Grp{&a.st->bar_count, (int)gridDim.x, (int)blockIdx.x, 0};
+    int g = a.blk_grp[blockIdx.x];
+    int b0 = a.grp[4 * g + 2];
+    return Grp{a.grp_bar + g, a.grp[4 * g + 3], (int)blockIdx.x - b0, b0};
+}
+
+// Barrier over the blocks of one group (all blocks are co-resident: the
+// launch is cooperative), one atomic per block: the group's first block adds
+// 2^31 - (nb - 1), every other block adds 1, so the counter's top bit flips
+// exactly when the last block arrives and the low bits return to zero (the
+// counter is cleared before each launch).  Each block waits for the flip
+// with an iteration limit; a block that waits too long records
+// PIC_ERR_TIMEOUT and the whole kernel returns.
+__device__ bool grid_sync(const PcgArgs &a)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const Grp g = grp_of(a);
         int ok = 1;
-        unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+        unsigned inc = g.rank == 0 ? 0x80000000u - (unsigned)(g.nb - 1) : 1u;
         __threadfence();
-        unsigned old = atomicAdd(&st->bar_count, inc);
+        unsigned old = atomicAdd(g.ctr, inc);
         long long spins = 0;
-        while (((old ^ ld_acquire_u32(&st->bar_count)) & 0x80000000u) == 0) {
+        while (((old ^ ld_acquire_u32(g.ctr)) & 0x80000000u) == 0) {
             if (++spins > SPIN_LIMIT) {
-                atomicCAS(&st->err, 0, PIC_ERR_TIMEOUT);
+                atomicCAS(&a.st->err, 0, PIC_ERR_TIMEOUT);
                 ok = 0;
                 break;
             }
         }
         __threadfence();
-        if (ld_volatile_i32(&st->err) == PIC_ERR_TIMEOUT)
+        if (ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)
             ok = 0;
         ok_s = ok;
     }
@@ -106,8 +125,8 @@ struct NoFinish {
 // step lengths) after them, so that divisions are not repeated by every
 // thread.  out[0..NV) = totals, out[NV..NO) = what fin wrote.
 template <int NV, int NO, int BLOCK, typename F>
-__device__ bool grid_sum_f(const double (&v)[NV], double *partials, int set, DevState *st,
-                           double (&out)[NO], F fin)
+__device__ bool grid_sum_f(const double (&v)[NV], int set, const PcgArgs &a, double (&out)[NO],
+                           F fin)
 {
     static_assert(NV <= 3 && NO <= 4 && BLOCK <= 512, "reduction buffer size");
     double *vals = reduction_buffer();
@@ -125,17 +144,18 @@ __device__ bool grid_sum_f(const double (&v)[NV], double *partials, int set, Dev
                 s += vals[k * BLOCK + i];
             s = warp_sum(s);
             if (lane == 0)
-                partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + k] = s;
+                a.partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + k] = s;
         }
     }
-    if (!grid_sync(st))
+    if (!grid_sync(a))
         return false;
     if (wid == 0) {
+        const Grp g = grp_of(a);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double s = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32)
-                s += __ldcg(partials + ((size_t)set * gridDim.x + b) * 4 + k);
+            for (int b = lane; b < g.nb; b += 32)
+                s += __ldcg(a.partials + ((size_t)set * gridDim.x + g.b0 + b) * 4 + k);
             s = warp_sum(s);
             if (lane == 0)
                 res[k] = s;
@@ -151,60 +171,88 @@ __device__ bool grid_sum_f(const double (&v)[NV], double *partials, int set, Dev
 }
 
 template <int NV, int BLOCK = PCG_BLOCK>
-__device__ bool grid_sum(const double (&v)[NV], double *partials, int set, DevState *st,
-                         double (&out)[NV])
+__device__ bool grid_sum(const double (&v)[NV], int set, const PcgArgs &a, double (&out)[NV])
 {
-    return grid_sum_f<NV, NV, BLOCK>(v, partials, set, st, out, NoFinish());
+    return grid_sum_f<NV, NV, BLOCK>(v, set, a, out, NoFinish());
 }
 
 // f_i = (q w_sp / eps0) W_i 2^-S + f_Neumann,i (eq. poisson_rhs), written
-// without contraction so it equals the plain evaluation bit for bit
+// without contraction so it equals the plain evaluation bit for bit; 0 on
+// padding rows (no node)
 __device__ __forceinline__ double rhs_entry(const PcgArgs &a, int row)
 {
-    if (row >= a.n)
+    int node = a.dof_node[row];
+    if (node < 0)
         return 0.0;
-    double w = (double)(long long)a.W[a.dof_node[row]];
+    double w = (double)(long long)a.W[node];
     return __dadd_rn(__dmul_rn(a.coef, __dmul_rn(w, a.wscale)), a.fN[row]);
 }
 
+// Statistics of the solve: the first block of each group reports; with
+// several groups (a batch) the step reports the largest iteration count and
+// residual among them.
 __device__ __forceinline__ void finish(const PcgArgs &a, int it, double relres, int status,
                                        int outer = 0)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0 && grp_of(a).rank == 0) {
         if (status)
             atomicCAS(&a.st->err, 0, status);
         if (a.stats) {
-            a.stats->pcg_iters = it;
-            a.stats->pcg_relres = relres;
-            a.stats->pcg_outer = outer;
+            atomicMax(&a.stats->pcg_iters, it);
+            atomicMax((unsigned long long *)&a.stats->pcg_relres,
+                      (unsigned long long)__double_as_longlong(relres));
+            atomicMax(&a.stats->pcg_outer, outer);
             if (a.alive)
                 a.stats->alive = (int64_t)*a.alive;
         }
     }
 }
 
-__device__ __forceinline__ void scatter_phi(const PcgArgs &a, int gw, int NW, int lane)
+// The slices a warp works on in the general kernels: the group's slice range
+// strided by the group's warps (the whole matrix when there are no groups).
+struct Span {
+    int s0, s1, gw, nw;
+};
+
+__device__ __forceinline__ Span row_span(const PcgArgs &a)
 {
-    for (int s = gw; s < a.n_slices; s += NW) {
+    const int w = threadIdx.x >> 5;
+    if (a.n_groups <= 0)
+        return Span{0, a.n_slices, (int)blockIdx.x * PCG_WARPS + w, (int)gridDim.x * PCG_WARPS};
+    int g = a.blk_grp[blockIdx.x];
+    const int *d = a.grp + 4 * g;
+    return Span{d[0], d[1], ((int)blockIdx.x - d[2]) * PCG_WARPS + w, d[3] * PCG_WARPS};
+}
+#define FOR_SLICES(sp, s) for (int s = (sp).s0 + (sp).gw; s < (sp).s1; s += (sp).nw)
+
+__device__ __forceinline__ void scatter_phi(const PcgArgs &a, const Span &sp, int lane)
+{
+    FOR_SLICES(sp, s)
+    {
         int row = s * 32 + lane;
-        if (row < a.n)
-            a.phi[a.dof_node[row]] = a.x[row];
+        int node = a.dof_node[row];
+        if (node >= 0)
+            a.phi[node] = a.x[row];
     }
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Jacobi-PCG
+// General kernels: any problem size, vectors in global memory, warps strided
+// over their group's slices; used for a batch of replicas (one group each)
+// and for systems too large for the resident kernels.
 // ---------------------------------------------------------------------------
+
+// FP64 Jacobi-PCG (the plain FP64 form)
 __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * PCG_WARPS + (threadIdx.x >> 5);
-    const int NW = gridDim.x * PCG_WARPS;
+    const Span sp = row_span(a);
     int set = 0;
 
     // r = f - M x, z = D^-1 r, p_old = 0
     double acc[3] = {0.0, 0.0, 0.0}, tot[3];
-    for (int s = gw; s < a.n_slices; s += NW) {
+    FOR_SLICES(sp, s)
+    {
         int row = s * 32 + lane;
         int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
         double ax = 0.0;
@@ -222,30 +270,30 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
         acc[1] += r * r;
         acc[2] += f * f;
     }
-    if (!grid_sum<3>(acc, a.partials, set, a.st, tot))
+    if (!grid_sum<3>(acc, set, a, tot))
         return;
     set ^= 1;
     double rz = tot[0], rr = tot[1], ff = tot[2];
     if (ff == 0.0) {
-        for (int s = gw; s < a.n_slices; s += NW)
-            a.x[s * 32 + lane] = 0.0;
-        scatter_phi(a, gw, NW, lane);
+        FOR_SLICES(sp, s) a.x[s * 32 + lane] = 0.0;
+        scatter_phi(a, sp, lane);
         finish(a, 0, 0.0, 0);
         return;
     }
-    const double tol = a.rtol * sqrt(ff);
+    const double tol2 = a.rtol * a.rtol * ff;
     int it = 0;
     double beta = 0.0;
     double *pold = a.p0, *pnew = a.p1;
     int status = 0;
-    while (sqrt(rr) > tol) {
+    while (rr > tol2) {
         if (it >= a.max_iter) {
             status = PIC_ERR_NOT_CONVERGED;
             break;
         }
         // phase A: p = z + beta p_old (on the fly), Ap = M p, p.Ap
-        double pap[1] = {0.0}, pt[1];
-        for (int s = gw; s < a.n_slices; s += NW) {
+        double pap[1] = {0.0}, pt2[2];
+        FOR_SLICES(sp, s)
+        {
             int row = s * 32 + lane;
             int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
             double ap = 0.0;
@@ -259,13 +307,14 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
             a.ap[row] = ap;
             pap[0] += p * ap;
         }
-        if (!grid_sum<1>(pap, a.partials, set, a.st, pt))
+        if (!grid_sum_f<1, 2, PCG_BLOCK>(pap, set, a, pt2, [rz](double *q) { q[1] = rz / q[0]; }))
             return;
         set ^= 1;
-        double alpha = rz / pt[0];
+        double alpha = pt2[1];
         // phase B: x += alpha p, r -= alpha Ap, z = D^-1 r
-        double acc2[2] = {0.0, 0.0}, t2[2];
-        for (int s = gw; s < a.n_slices; s += NW) {
+        double acc2[2] = {0.0, 0.0}, t3[3];
+        FOR_SLICES(sp, s)
+        {
             int row = s * 32 + lane;
             double p = pnew[row];
             a.x[row] = a.x[row] + alpha * p;
@@ -276,43 +325,91 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
             acc2[0] += r * z;
             acc2[1] += r * r;
         }
-        if (!grid_sum<2>(acc2, a.partials, set, a.st, t2))
+        if (!grid_sum_f<2, 3, PCG_BLOCK>(acc2, set, a, t3, [rz](double *q) { q[2] = q[0] / rz; }))
             return;
         set ^= 1;
-        beta = t2[0] / rz;
-        rz = t2[0];
-        rr = t2[1];
+        beta = t3[2];
+        rz = t3[0];
+        rr = t3[1];
         ++it;
         double *tmp = pold;
         pold = pnew;
         pnew = tmp;
     }
-    scatter_phi(a, gw, NW, lane);
-    finish(a, it, sqrt(rr) / sqrt(ff), status);
+    scatter_phi(a, sp, lane);
+    finish(a, it, sqrt(rr / ff), status);
 }
 
-// ---------------------------------------------------------------------------
-// FP32 PCG inside FP64 iterative refinement
-// ---------------------------------------------------------------------------
+// z = M^-1 r on the rows of this warp, FP32, vectors in global memory:
+// Jacobi, or the Chebyshev polynomial of degree k in D^-1 M (see
+// apply_precond below); rc lives in ap32 and the step direction d in the
+// double-buffered d32_0 / d32_1, which also serve as the halo copies.
+__device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
+{
+    if (a.cheb_degree < 2) {
+        FOR_SLICES(sp, s)
+        {
+            int row = s * 32 + lane;
+            a.z32[row] = a.dinv32[row] * a.r32[row];
+        }
+        return true;
+    }
+    const int kdeg = a.cheb_degree;
+    FOR_SLICES(sp, s)
+    {
+        int row = s * 32 + lane;
+        float rc = a.r32[row];
+        float d = a.dinv32[row] * rc * a.cheb_inv_thetaf;
+        a.z32[row] = d;
+        a.ap32[row] = rc;
+        a.d32_1[row] = d;
+    }
+    for (int j = 1; j < kdeg; ++j) {
+        const float *cur = (j & 1) ? a.d32_1 : a.d32_0;
+        float *nxt = (j & 1) ? a.d32_0 : a.d32_1;
+        const float c1 = a.cheb_c1f[j - 1], c2 = a.cheb_c2f[j - 1];
+        if (!grid_sync(a))
+            return false;
+        FOR_SLICES(sp, s)
+        {
+            int row = s * 32 + lane;
+            int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
+            float ad = 0.f;
+            for (int c = 0; c < width; ++c) {
+                int k = b + c * 32 + lane;
+                ad += a.val32[k] * __ldcg(cur + a.col[k]);
+            }
+            float rc = a.ap32[row] - ad;
+            float d = c1 * cur[row] + c2 * (a.dinv32[row] * rc);
+            a.z32[row] = a.z32[row] + d;
+            a.ap32[row] = rc;
+            if (j + 1 < kdeg)
+                nxt[row] = d;
+        }
+    }
+    return true;
+}
+
+// FP32 PCG inside FP64 iterative refinement (see the resident form below)
 __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * PCG_WARPS + (threadIdx.x >> 5);
-    const int NW = gridDim.x * PCG_WARPS;
+    const Span sp = row_span(a);
     int set = 0;
 
-    for (int s = gw; s < a.n_slices; s += NW) {
+    FOR_SLICES(sp, s)
+    {
         int row = s * 32 + lane;
         a.f[row] = rhs_entry(a, row);
     }
-    // own rows only: no barrier needed before the first residual
     int it = 0, status = 0, outer = 0;
     double ff = -1.0, rr64 = 0.0;
     for (;;) {
-        // FP64 residual r = f - M x (x of neighbours complete after the
+        // FP64 residual r = f - M x (x of the other blocks complete after the
         // barrier that ended the previous refinement)
         double acc[2] = {0.0, 0.0}, tot[2];
-        for (int s = gw; s < a.n_slices; s += NW) {
+        FOR_SLICES(sp, s)
+        {
             int row = s * 32 + lane;
             int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
             double ax = 0.0;
@@ -326,49 +423,59 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
             acc[0] += r * r;
             acc[1] += f * f;
         }
-        if (!grid_sum<2>(acc, a.partials, set, a.st, tot))
+        if (!grid_sum<2>(acc, set, a, tot))
             return;
         set ^= 1;
         rr64 = tot[0];
         if (ff < 0.0)
             ff = tot[1];
         if (ff == 0.0) {
-            for (int s = gw; s < a.n_slices; s += NW)
-                a.x[s * 32 + lane] = 0.0;
-            scatter_phi(a, gw, NW, lane);
-            finish(a, 0, 0.0, 0);
-            return;
+            FOR_SLICES(sp, s) a.x[s * 32 + lane] = 0.0;
+            rr64 = 0.0;
+            ff = 1.0;
+            break;
         }
-        if (sqrt(rr64) <= a.rtol * sqrt(ff))
+        if (rr64 <= a.rtol * a.rtol * ff)
             break;
         if (it >= a.max_iter) {
             status = PIC_ERR_NOT_CONVERGED;
             break;
         }
+        double itol = 0.5 * a.rtol * sqrt(ff / rr64);
+        if (itol < a.inner_rtol)
+            itol = a.inner_rtol;
         // inner FP32 PCG on M d = r, d = 0
-        double acc2[2] = {0.0, 0.0}, t2[2];
-        for (int s = gw; s < a.n_slices; s += NW) {
+        FOR_SLICES(sp, s)
+        {
             int row = s * 32 + lane;
-            float r = (float)a.r[row];
-            float z = a.dinv32[row] * r;
-            a.r32[row] = r;
-            a.z32[row] = z;
-            a.p32_0[row] = 0.f;
+            a.r32[row] = (float)a.r[row];
             a.dx32[row] = 0.f;
+            a.p32_0[row] = 0.f;
+        }
+        if (!precond_global(a, sp, lane))
+            return;
+        double acc2[2] = {0.0, 0.0}, t2[2];
+        FOR_SLICES(sp, s)
+        {
+            int row = s * 32 + lane;
+            float r = a.r32[row], z = a.z32[row];
             acc2[0] += (double)r * (double)z;
             acc2[1] += (double)r * (double)r;
         }
-        if (!grid_sum<2>(acc2, a.partials, set, a.st, t2))
+        if (!grid_sum<2>(acc2, set, a, t2))
             return;
         set ^= 1;
         double rz = t2[0], rr = t2[1];
-        const double itol2 = a.inner_rtol * a.inner_rtol * rr;
+        const double itol2 = itol * itol * rr;
         double beta = 0.0;
         float *pold = a.p32_0, *pnew = a.p32_1;
-        while (rr > itol2 && it < a.max_iter) {
+        for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
+                        !(a.inner_max > 0 && i >= a.inner_max);
+             ++i) {
             float b32 = (float)beta;
-            double pap[1] = {0.0}, pt[1];
-            for (int s = gw; s < a.n_slices; s += NW) {
+            double pap[1] = {0.0}, pt2[2];
+            FOR_SLICES(sp, s)
+            {
                 int row = s * 32 + lane;
                 int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
                 float ap = 0.f;
@@ -382,26 +489,32 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
                 a.ap32[row] = ap;
                 pap[0] += (double)p * (double)ap;
             }
-            if (!grid_sum<1>(pap, a.partials, set, a.st, pt))
+            if (!grid_sum_f<1, 2, PCG_BLOCK>(pap, set, a, pt2,
+                                             [rz](double *q) { q[1] = rz / q[0]; }))
                 return;
             set ^= 1;
-            float alpha = (float)(rz / pt[0]);
-            double acc3[2] = {0.0, 0.0}, t3[2];
-            for (int s = gw; s < a.n_slices; s += NW) {
+            float alpha = (float)pt2[1];
+            FOR_SLICES(sp, s)
+            {
                 int row = s * 32 + lane;
-                float p = pnew[row];
-                a.dx32[row] = a.dx32[row] + alpha * p;
-                float r = a.r32[row] - alpha * a.ap32[row];
-                float z = a.dinv32[row] * r;
-                a.r32[row] = r;
-                a.z32[row] = z;
+                a.dx32[row] = a.dx32[row] + alpha * pnew[row];
+                a.r32[row] = a.r32[row] - alpha * a.ap32[row];
+            }
+            if (!precond_global(a, sp, lane))
+                return;
+            double acc3[2] = {0.0, 0.0}, t3[3];
+            FOR_SLICES(sp, s)
+            {
+                int row = s * 32 + lane;
+                float r = a.r32[row], z = a.z32[row];
                 acc3[0] += (double)r * (double)z;
                 acc3[1] += (double)r * (double)r;
             }
-            if (!grid_sum<2>(acc3, a.partials, set, a.st, t3))
+            if (!grid_sum_f<2, 3, PCG_BLOCK>(acc3, set, a, t3,
+                                             [rz](double *q) { q[2] = q[0] / rz; }))
                 return;
             set ^= 1;
-            beta = t3[0] / rz;
+            beta = t3[2];
             rz = t3[0];
             rr = t3[1];
             ++it;
@@ -410,16 +523,17 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
             pnew = tmp;
         }
         // refinement update in FP64
-        for (int s = gw; s < a.n_slices; s += NW) {
+        FOR_SLICES(sp, s)
+        {
             int row = s * 32 + lane;
             a.x[row] = a.x[row] + (double)a.dx32[row];
         }
-        if (!grid_sync(a.st))
+        if (!grid_sync(a))
             return;
         ++outer;
     }
-    scatter_phi(a, gw, NW, lane);
-    finish(a, it, sqrt(rr64) / sqrt(ff), status, outer);
+    scatter_phi(a, sp, lane);
+    finish(a, it, sqrt(rr64 / ff), status, outer);
 }
 
 // ===========================================================================
@@ -564,7 +678,7 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             s_d[t.o[k]] = d[k];
             g_d[t.row[k]] = d[k];
         }
-        if (!grid_sync(a.st))
+        if (!grid_sync(a))
             return false;
         stage_halo(s_d, (const T *)g_d, a, g);
         __syncthreads();
@@ -651,7 +765,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         a.p0[t.row[k]] = 0.0;
     }
     int set = 0;
-    if (!grid_sum<3, RB>(acc, a.partials, set, a.st, tot))
+    if (!grid_sum<3, RB>(acc, set, a, tot))
         return;
     set ^= 1;
     double rz = tot[0], rr = tot[1], ff = tot[2];
@@ -696,7 +810,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
             pap[0] += p[k] * sum;
         }
         double pt2[2];
-        if (!grid_sum_f<1, 2, RB>(pap, a.partials, set, a.st, pt2,
+        if (!grid_sum_f<1, 2, RB>(pap, set, a, pt2,
                                   [rz](double *q) { q[1] = rz / q[0]; }))
             return;
         set ^= 1;
@@ -721,7 +835,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
             acc2[1] += r[k] * r[k];
         }
         double t3[3];
-        if (!grid_sum_f<2, 3, RB>(acc2, a.partials, set, a.st, t3,
+        if (!grid_sum_f<2, 3, RB>(acc2, set, a, t3,
                                   [rz](double *q) { q[2] = q[0] / rz; }))
             return;
         set ^= 1;
@@ -736,8 +850,9 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         if (!t.ok[k])
             continue;
         a.x[t.row[k]] = x[k];
-        if (t.row[k] < a.n)
-            a.phi[a.dof_node[t.row[k]]] = x[k];
+        int node = a.dof_node[t.row[k]];
+        if (node >= 0)
+            a.phi[node] = x[k];
     }
     finish(a, it, sqrt(rr / ff), status);
 }
@@ -781,7 +896,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         acc[0] += (double)rv[k] * (double)z[k];
         acc[1] += (double)rv[k] * (double)rv[k];
     }
-    if (!grid_sum<2, RB>(acc, a.partials, set, a.st, tot))
+    if (!grid_sum<2, RB>(acc, set, a, tot))
         return false;
     set ^= 1;
     double rz = tot[0], rr = tot[1];
@@ -817,7 +932,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             pap[0] += (double)p[k] * (double)sum;
         }
         double pt2[2];
-        if (!grid_sum_f<1, 2, RB>(pap, a.partials, set, a.st, pt2,
+        if (!grid_sum_f<1, 2, RB>(pap, set, a, pt2,
                                   [rz](double *q) { q[1] = rz / q[0]; }))
             return false;
         set ^= 1;
@@ -843,7 +958,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             acc2[1] += (double)rv[k] * (double)rv[k];
         }
         double t3[3];
-        if (!grid_sum_f<2, 3, RB>(acc2, a.partials, set, a.st, t3,
+        if (!grid_sum_f<2, 3, RB>(acc2, set, a, t3,
                                   [rz](double *q) { q[2] = q[0] / rz; }))
             return false;
         set ^= 1;
@@ -872,7 +987,7 @@ __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const Pc
         s_m0[t.o[k]] = u[k];
         gm[0][t.row[k]] = u[k];
     }
-    if (!grid_sync(a.st))
+    if (!grid_sync(a))
         return false;
     stage_halo(s_m0, (const float *)gm[0], a, g);
     __syncthreads();
@@ -898,7 +1013,7 @@ __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const Pc
             dots[1] += (double)wv[k] * (double)u[k];
             dots[2] += (double)rv[k] * (double)rv[k];
         }
-        if (!grid_sum<3, RB>(dots, a.partials, set, a.st, dt3))
+        if (!grid_sum<3, RB>(dots, set, a, dt3))
             return false;
         set ^= 1;
         double gamma = dt3[0], delta = dt3[1], rr = dt3[2];
@@ -985,7 +1100,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
             acc[0] += r64[k] * r64[k];
             acc[1] += f[k] * f[k];
         }
-        if (!grid_sum<2, RB>(acc, a.partials, set, a.st, tot))
+        if (!grid_sum<2, RB>(acc, set, a, tot))
             return;
         set ^= 1;
         rr64 = tot[0];
@@ -1029,7 +1144,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
             s_x[t.o[k]] = x[k];
             a.x[t.row[k]] = x[k];
         }
-        if (!grid_sync(a.st))
+        if (!grid_sync(a))
             return;
         ++outer;
     }
@@ -1038,8 +1153,9 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
         if (!t.ok[k])
             continue;
         a.x[t.row[k]] = x[k];
-        if (t.row[k] < a.n)
-            a.phi[a.dof_node[t.row[k]]] = x[k];
+        int node = a.dof_node[t.row[k]];
+        if (node >= 0)
+            a.phi[node] = x[k];
     }
     finish(a, it, sqrt(rr64) / sqrt(ff), status, outer);
 }
@@ -1099,10 +1215,67 @@ static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G
     }
 }
 
+int pcg_max_group_blocks(int precision, int num_sms)
+{
+    const void *fn = precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_BLOCK, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * num_sms;
+}
+
 cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num_sms,
-                     int precision, int variant, PcgLaunch *plan, PcgHalo *halo)
+                     int precision, int variant, int n_sys, const int *grp_slices,
+                     int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo)
 {
     *plan = PcgLaunch{};
+    if (n_sys > 1) {
+        // a batch: the general kernels, each system on its own group of
+        // blocks, blocks in proportion to the system's slices
+        const void *fn = precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_BLOCK, 0);
+        if (e != cudaSuccess)
+            return e;
+        if (blocks_per_sm > 0 && blocks_per_sm < per_sm)
+            per_sm = blocks_per_sm;
+        int max_blocks = per_sm * num_sms;
+        if (per_sm < 1 || n_sys > max_blocks)
+            return cudaErrorInvalidConfiguration;
+        std::vector<int> nb((size_t)n_sys, 1);
+        int spare = max_blocks - n_sys;
+        long long tot = 0;
+        for (int g = 0; g < n_sys; ++g)
+            tot += grp_slices[g + 1] - grp_slices[g];
+        int used = 0;
+        for (int g = 0; g < n_sys; ++g) {
+            long long sl = grp_slices[g + 1] - grp_slices[g];
+            int want = (int)((double)spare * (double)sl / (double)(tot > 0 ? tot : 1));
+            int cap = (int)((sl + PCG_WARPS - 1) / PCG_WARPS);  // at most a slice per warp
+            want = std::min(want, std::max(0, cap - 1));
+            nb[g] += want;
+            used += want;
+        }
+        (void)used;
+        halo->grp.assign(4 * (size_t)n_sys, 0);
+        halo->blk_grp.clear();
+        int b = 0;
+        for (int g = 0; g < n_sys; ++g) {
+            halo->grp[4 * g + 0] = grp_slices[g];
+            halo->grp[4 * g + 1] = grp_slices[g + 1];
+            halo->grp[4 * g + 2] = b;
+            halo->grp[4 * g + 3] = nb[g];
+            for (int k = 0; k < nb[g]; ++k)
+                halo->blk_grp.push_back(g);
+            b += nb[g];
+        }
+        plan->grid = b;
+        plan->block = PCG_BLOCK;
+        plan->n_groups = n_sys;
+        return cudaSuccess;
+    }
     // resident: one block per SM (fewer for small problems), rows in registers
     int G = (n_slices + RW - 1) / RW;
     if (G > num_sms)
@@ -1165,16 +1338,31 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
     return cudaSuccess;
 }
 
+// Cooperative launch (all blocks co-resident, which the grid barrier needs)
+// through the extensible launch API, which stream capture records as a
+// cooperative kernel node.
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a)
 {
     void *args[] = {(void *)&a};
+    const void *fn;
+    size_t smem = 0;
     if (plan.resident) {
-        const void *fn = pick_resident(a.precision, a.variant, plan.rpt, plan.smem_matrix != 0);
-        return cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(plan.block), args,
-                                           plan.smem_bytes, s);
+        fn = pick_resident(a.precision, a.variant, plan.rpt, plan.smem_matrix != 0);
+        smem = plan.smem_bytes;
+    } else {
+        fn = a.precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
     }
-    const void *fn = a.precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
-    return cudaLaunchCooperativeKernel(fn, dim3(plan.grid), dim3(plan.block), args, 0, s);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.grid);
+    cfg.blockDim = dim3(plan.block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace pf

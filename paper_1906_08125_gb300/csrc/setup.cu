@@ -107,12 +107,13 @@ __global__ void k_matrix_values(long long nnz, const long long *__restrict__ cpt
 // Neumann load int_{Gamma_1} N_i E0 dGamma = E0 A / 3 for each vertex i of a
 // top triangle (eq. poisson_rhs, second term), summed over the triangles of
 // free DOF i in increasing (tetrahedron, face) order.
-__global__ void k_neumann(int n_free, const int *__restrict__ fptr, const int *__restrict__ fcontrib,
-                          const int4 *__restrict__ tet, const double *__restrict__ xyz, double E0,
+__global__ void k_neumann(int n_rows, const int *__restrict__ fptr, const int *__restrict__ fcontrib,
+                          const int4 *__restrict__ tet, const double *__restrict__ xyz,
+                          const int *__restrict__ tet_rep, const double *__restrict__ E0_rep,
                           double *fN)
 {
     int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= n_free)
+    if (d >= n_rows)
         return;
     double sum = 0.0;
     for (int k = fptr[d]; k < fptr[d + 1]; ++k) {
@@ -131,7 +132,7 @@ __global__ void k_neumann(int n_free, const int *__restrict__ fptr, const int *_
         double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2],
                        u[0] * w[1] - u[1] * w[0]};
         double area = 0.5 * sqrt((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
-        sum += (E0 * area) / 3.0;
+        sum += (E0_rep[tet_rep[t]] * area) / 3.0;
     }
     fN[d] = sum;
 }
@@ -181,12 +182,14 @@ cudaError_t launch_matrix_values(cudaStream_t s, long long nnz, const long long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_neumann(cudaStream_t s, int n_free, const int *fptr, const int *fcontrib,
-                           const int4 *tet, const double *xyz, double E0, double *fN)
+cudaError_t launch_neumann(cudaStream_t s, int n_rows, const int *fptr, const int *fcontrib,
+                           const int4 *tet, const double *xyz, const int *tet_rep,
+                           const double *E0_rep, double *fN)
 {
-    if (n_free <= 0)
+    if (n_rows <= 0)
         return cudaSuccess;
-    k_neumann<<<blocks_for(n_free, 256), 256, 0, s>>>(n_free, fptr, fcontrib, tet, xyz, E0, fN);
+    k_neumann<<<blocks_for(n_rows, 256), 256, 0, s>>>(n_rows, fptr, fcontrib, tet, xyz, tet_rep,
+                                                      E0_rep, fN);
     return cudaGetLastError();
 }
 

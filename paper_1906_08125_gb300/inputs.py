@@ -312,3 +312,89 @@ def random_particles(mesh: Mesh, n: int, seed: int = 0, v_scale: float = 1.0e7,
     v[:, 2] += v_up
     pid = (np.int64(1) << np.int64(62)) + np.arange(n, dtype=np.int64)
     return r, v, cell, pid
+
+
+# ---------------------------------------------------------------------------
+# ensembles: several independent meshes in one batch
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class Batch:
+    """Replica meshes concatenated into one: replica r owns nodes
+    [node_off[r], node_off[r+1]), tetrahedra [tet_off[r], tet_off[r+1]) and
+    emitting faces [face_off[r], face_off[r+1]); it keeps its own coordinates
+    (replicas overlap in space but share no tetrahedron).  E0[r] is its
+    applied field and members[r] its own mesh."""
+    mesh: Mesh
+    node_off: np.ndarray
+    tet_off: np.ndarray
+    face_off: np.ndarray
+    E0: np.ndarray
+    members: list
+
+    @property
+    def n_rep(self) -> int:
+        return len(self.members)
+
+
+def batch_meshes(meshes, E0, name="batch") -> Batch:
+    """Concatenate ``meshes`` with node/tetrahedron/face index offsets."""
+    node_off = np.concatenate([[0], np.cumsum([m.n_nodes for m in meshes])]).astype(np.int64)
+    tet_off = np.concatenate([[0], np.cumsum([m.n_tets for m in meshes])]).astype(np.int64)
+    face_off = np.concatenate([[0], np.cumsum([m.n_faces for m in meshes])]).astype(np.int64)
+    if node_off[-1] >= 2 ** 31 or tet_off[-1] >= 2 ** 31:
+        raise ValueError("batch too large for 32-bit indices")
+
+    def shifted(a, off):
+        a = a.astype(np.int64)
+        return np.where(a >= 0, a + off, a)
+
+    lo = np.min([m.box_lo for m in meshes], axis=0)
+    hi = np.max([m.box_hi for m in meshes], axis=0)
+    mesh = Mesh(
+        xyz=np.concatenate([m.xyz for m in meshes]),
+        tet=np.concatenate([m.tet.astype(np.int64) + node_off[r]
+                            for r, m in enumerate(meshes)]).astype(np.int32),
+        nbr=np.concatenate([shifted(m.nbr, tet_off[r])
+                            for r, m in enumerate(meshes)]).astype(np.int32),
+        periodic_nbr=np.concatenate([shifted(m.periodic_nbr, tet_off[r])
+                                     for r, m in enumerate(meshes)]).astype(np.int32),
+        dirichlet=np.concatenate([m.dirichlet for m in meshes]),
+        face_nodes=np.concatenate([m.face_nodes.astype(np.int64) + node_off[r]
+                                   for r, m in enumerate(meshes)]).astype(np.int32),
+        face_tet=np.concatenate([m.face_tet.astype(np.int64) + tet_off[r]
+                                 for r, m in enumerate(meshes)]).astype(np.int32),
+        work_function=np.concatenate([m.work_function for m in meshes]),
+        box_lo=lo, box_hi=hi, name=name)
+    return Batch(mesh=mesh, node_off=node_off, tet_off=tet_off, face_off=face_off,
+                 E0=np.asarray(E0, dtype=np.float64), members=list(meshes))
+
+
+# tip resolutions of the ensemble: mesh spacings scaled by these factors give
+# about 1.0M, 485k, 260k, 137k and 64k tetrahedra at radius 3 nm (60 nm box)
+# and 947k, 470k, 244k and 112k at radius 6 nm (80 nm box)
+ENSEMBLE_SCALES = {3: (1.0, 1.4, 2.0, 2.8, 4.0), 6: (1.4, 2.0, 2.8, 4.0)}
+
+
+def ensemble_tip(radius_nm: int, scale: float) -> Mesh:
+    """Tip of the ensemble: radius 3 or 6 nm, all spacings times ``scale``."""
+    width = 60 * NM if radius_nm == 3 else 80 * NM
+    return tip_mesh(radius=radius_nm * NM, width=width, h_fine=0.4 * NM * scale,
+                    h_shank=1.5 * NM * scale, h_lat_max=3 * NM * scale,
+                    h_top_max=6 * NM * scale, name=f"tip_r{radius_nm}_s{scale}")
+
+
+def ensemble(n_rep=64, seed=0, E0_range=(8e9, 12e9), scales=None) -> Batch:
+    """Seeded ensemble of field-emitter replicas: radius 3 or 6 nm (equal
+    odds), a mesh resolution drawn from ``scales`` (default
+    ``ENSEMBLE_SCALES``), E0 ~ U(E0_range).  Identical meshes are built once."""
+    rng = np.random.default_rng(seed)
+    scales = scales or ENSEMBLE_SCALES
+    cache, meshes, E0 = {}, [], []
+    for _ in range(n_rep):
+        rad = int(rng.choice(sorted(scales)))
+        sc = float(rng.choice(scales[rad]))
+        if (rad, sc) not in cache:
+            cache[(rad, sc)] = ensemble_tip(rad, sc)
+        meshes.append(cache[(rad, sc)])
+        E0.append(rng.uniform(*E0_range))
+    return batch_meshes(meshes, E0, name=f"ensemble{n_rep}")

@@ -21,6 +21,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_MESH", -4: "PIC_ER
 PREC_FP64, PREC_FP32_IR = 0, 1
 
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_load",
+            "mesh_load_batch", "pic_get_tuning", "pic_set_tuning",
             "pic_mesh_info",
             "pic_init_potential", "inject", "push_relocate", "deposit", "poisson_solve",
             "pic_step", "pic_adjoint", "pic_get_step", "pic_set_step", "pic_get_potential",
@@ -37,7 +38,13 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("capacity", C.c_int64), ("walk_max_steps", C.c_int32),
                 ("quant_bits", C.c_int32), ("precision", C.c_int32), ("pcg_variant", C.c_int32),
                 ("ir_inner_rtol", C.c_double), ("ir_inner_max_iter", C.c_int32),
-                ("pcg_cheb_degree", C.c_int32), ("pcg_cheb_ratio", C.c_double)]
+                ("pcg_cheb_degree", C.c_int32), ("pcg_cheb_ratio", C.c_double),
+                ("graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("particle_blocks_per_sm", C.c_int32), ("walk_form", C.c_int32),
+                ("pcg_blocks_per_sm", C.c_int32), ("pcg_cheb_degree", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -55,7 +62,9 @@ class MeshInfo(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_tets", C.c_int32), ("n_faces", C.c_int32),
                 ("n_free", C.c_int32), ("nnz", C.c_int64), ("sell_len", C.c_int64),
                 ("pcg_grid", C.c_int32), ("particle_grid", C.c_int32),
-                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
+                ("n_rep", C.c_int32), ("n_rows", C.c_int32), ("pcg_resident", C.c_int32),
+                ("graph", C.c_int32)]
 
 
 PROF_MAX = 16
@@ -97,7 +106,10 @@ def load(build_if_missing: bool = True):
         "pic_last_error": [P],
         "pic_version": [],
         "mesh_load": [P, I32, P, I32, P, P, P, P, I32, P, P, P],
+        "mesh_load_batch": [P, I32, P, P, P, I32, P, I32, P, P, P, P, I32, P, P, P],
         "pic_mesh_info": [P, C.POINTER(MeshInfo)],
+        "pic_get_tuning": [P, C.POINTER(Tuning)],
+        "pic_set_tuning": [P, C.POINTER(Tuning)],
         "pic_init_potential": [P, C.POINTER(I32), C.POINTER(D)],
         "inject": [P, I64, C.POINTER(I64)],
         "push_relocate": [P, I64, C.POINTER(StepStats)],
@@ -139,7 +151,7 @@ def _ptr(x):
 
 
 def _params(d: dict) -> Params:
-    return Params(**{k: d[k] for k, _ in Params._fields_})
+    return Params(**{k: d[k] for k, _ in Params._fields_ if k != "reserved"})
 
 
 class Context:
@@ -186,6 +198,36 @@ class Context:
                                      _ptr(nbr), _ptr(pnbr), _ptr(dirichlet), mesh.n_faces,
                                      _ptr(fnodes), _ptr(ftet), _ptr(wf)))
         self.mesh = mesh
+        return self
+
+    def mesh_load_batch(self, batch):
+        """Load a ``inputs.Batch`` (replica meshes concatenated, with offsets)."""
+        mesh = batch.mesh
+        xyz, tet, nbr, pnbr, dirichlet, fnodes, ftet, wf = mesh.arrays()
+        rno = np.ascontiguousarray(batch.node_off, dtype=np.int32)
+        rto = np.ascontiguousarray(batch.tet_off, dtype=np.int32)
+        e0 = np.ascontiguousarray(batch.E0, dtype=np.float64)
+        self._check(self.L.mesh_load_batch(self.h, len(e0), _ptr(rno), _ptr(rto), _ptr(e0),
+                                           mesh.n_nodes, _ptr(xyz), mesh.n_tets, _ptr(tet),
+                                           _ptr(nbr), _ptr(pnbr), _ptr(dirichlet), mesh.n_faces,
+                                           _ptr(fnodes), _ptr(ftet), _ptr(wf)))
+        self.mesh = mesh
+        return self
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.L.pic_get_tuning(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def set_tuning(self, **kw):
+        """Change launch knobs (see pic_set_tuning); unnamed ones are kept."""
+        cur = self.tuning()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise KeyError(f"unknown tuning knobs {sorted(unknown)}")
+        cur.update(kw)
+        t = Tuning(**{k: int(v) for k, v in cur.items()})
+        self._check(self.L.pic_set_tuning(self.h, C.byref(t)))
         return self
 
     def info(self) -> dict:
