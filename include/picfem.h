@@ -211,6 +211,10 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           blocks per SM (0 = as many as fit; 0..64); the
  *                           one-system solver ignores it
  *   pcg_cheb_degree         as pic_params.pcg_cheb_degree (0..32)
+ *   pcg_balance             batch solve: 1 (default) shares the blocks out in
+ *                           proportion to each replica's slices x the CG
+ *                           iterations of its last solve, re-planned at the
+ *                           start of every pic_step call; 0 by slices only
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -219,6 +223,7 @@ typedef struct {
     int32_t walk_form;
     int32_t pcg_blocks_per_sm;
     int32_t pcg_cheb_degree;
+    int32_t pcg_balance;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);

@@ -27,6 +27,7 @@ SPACE = {
     "walk_form": (1, 2),
     "pcg_blocks_per_sm": (0, 1, 2, 4),
     "pcg_cheb_degree": (0, 4, 6, 8),
+    "pcg_balance": (0, 1),
 }
 
 
@@ -76,7 +77,8 @@ def tune(ctx, steps=4, warmup=2, space=None, cache_path=None, use_cache=True, lo
     restored to the snapshot afterwards."""
     space = dict(space or SPACE)
     if ctx.info()["n_rep"] <= 1:
-        space.pop("pcg_blocks_per_sm", None)       # the one-system solver ignores it
+        space.pop("pcg_blocks_per_sm", None)       # the one-system solver ignores them
+        space.pop("pcg_balance", None)
     if ctx.params["pcg_cheb_degree"] < 2 and "pcg_cheb_degree" in space:
         # a plain Jacobi form stays Jacobi: the degree is part of what it is
         space.pop("pcg_cheb_degree")

@@ -106,8 +106,10 @@ struct pic_ctx_s {
     long long launches = 0;
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
-    int walk_form = WALK_FORM_AUTO, pcg_bps = 0;
+    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1;
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
+    int *grp_iters = nullptr;     // iterations of each replica's last solve
+    std::vector<int> grp_h, blk_grp_h;   // the batch plan's tables (host copies)
     // profiling
     bool prof = false;
     std::vector<ProfRec> prof_recs;
@@ -417,6 +419,7 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
     g.grp = c->grp;
     g.blk_grp = c->blk_grp;
     g.grp_bar = c->grp_bar;
+    g.grp_iters = c->grp_iters;
     CK(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->s));
     if (c->plan.n_groups > 0)
         CK(cudaMemsetAsync(c->grp_bar, 0, sizeof(unsigned) * c->plan.n_groups, c->s));
@@ -938,7 +941,7 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     PcgHalo halo;
     c->lcol = c->halo_ptr = c->halo_idx = nullptr;
     CK(pcg_plan(sptr.data(), scol.data(), n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
-                R, rep_slice.data(), c->pcg_bps, &c->plan, &halo));
+                R, rep_slice.data(), nullptr, c->pcg_bps, &c->plan, &halo));
     c->rep_slice = rep_slice;
     // a batch solve can be re-planned with more blocks (pic_set_tuning)
     const int max_grid = c->plan.n_groups > 0
@@ -951,6 +954,10 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
         CK(dalloc(c, &c->grp, halo.grp.size()));
         CK(dalloc(c, &c->blk_grp, (size_t)max_grid));
         CK(dalloc(c, &c->grp_bar, (size_t)c->plan.n_groups));
+        CK(dalloc(c, &c->grp_iters, (size_t)c->plan.n_groups));
+        CK(cudaMemsetAsync(c->grp_iters, 0, sizeof(int) * c->plan.n_groups, c->s));
+        c->grp_h = halo.grp;
+        c->blk_grp_h = halo.blk_grp;
         CK(cudaMemcpyAsync(c->grp, halo.grp.data(), sizeof(int) * halo.grp.size(),
                            cudaMemcpyHostToDevice, c->s));
         CK(cudaMemcpyAsync(c->blk_grp, halo.blk_grp.data(), sizeof(int) * halo.blk_grp.size(),
@@ -1122,6 +1129,48 @@ extern "C" int mesh_load_batch(pic_ctx c, int32_t n_rep, const int32_t *rep_node
                      F, face_nodes, face_tet, wf);
 }
 
+// Re-plan the batch solve's block groups (same kernels, new group tables);
+// work = per-replica weights or null (slices).  The tables live in device
+// memory, so captured graphs stay valid unless the grid size changes.
+static int replan_batch(pic_ctx c, const double *work)
+{
+    PcgLaunch plan;
+    PcgHalo halo;
+    CK(pcg_plan(nullptr, nullptr, c->n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
+                c->n_rep, c->rep_slice.data(), work, c->pcg_bps, &plan, &halo));
+    if (halo.grp == c->grp_h && halo.blk_grp == c->blk_grp_h)
+        return PIC_OK;
+    c->grp_h = halo.grp;
+    c->blk_grp_h = halo.blk_grp;
+    CK(cudaMemcpyAsync(c->grp, c->grp_h.data(), sizeof(int) * c->grp_h.size(),
+                       cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->blk_grp, c->blk_grp_h.data(), sizeof(int) * c->blk_grp_h.size(),
+                       cudaMemcpyHostToDevice, c->s));
+    if (plan.grid != c->plan.grid)
+        free_graphs(c);
+    c->plan = plan;
+    return PIC_OK;
+}
+
+// Balance the batch solve on the iteration counts of the last solve of each
+// replica (stable from step to step: every solve is warm-started).
+static int balance_batch(pic_ctx c)
+{
+    if (c->plan.n_groups <= 0 || !c->pcg_balance)
+        return PIC_OK;
+    const int G = c->plan.n_groups;
+    std::vector<int> it((size_t)G);
+    CK(cudaMemcpyAsync(it.data(), c->grp_iters, sizeof(int) * G, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    std::vector<double> w((size_t)G);
+    bool any = false;
+    for (int g = 0; g < G; ++g) {
+        any = any || it[g] > 0;
+        w[g] = (double)(c->rep_slice[g + 1] - c->rep_slice[g]) * (double)std::max(it[g], 1);
+    }
+    return any ? replan_batch(c, w.data()) : PIC_OK;
+}
+
 extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
 {
     if (!c || !t)
@@ -1130,6 +1179,7 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->walk_form = c->walk_form;
     t->pcg_blocks_per_sm = c->pcg_bps;
     t->pcg_cheb_degree = c->p.pcg_cheb_degree;
+    t->pcg_balance = c->pcg_balance;
     return PIC_OK;
 }
 
@@ -1139,27 +1189,22 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         return fail(c, PIC_ERR_ARG, "null argument");
     if (t->particle_blocks_per_sm < 1 || t->particle_blocks_per_sm > 64 || t->walk_form < 0 ||
         t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
-        t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 ||
+        t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
+        t->pcg_balance > 1 ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
     CK(cudaStreamSynchronize(c->s));
-    if (c->loaded && c->plan.n_groups > 0 && t->pcg_blocks_per_sm != c->pcg_bps) {
-        PcgLaunch plan;
-        PcgHalo halo;
-        CK(pcg_plan(nullptr, nullptr, c->n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
-                    c->n_rep, c->rep_slice.data(), t->pcg_blocks_per_sm, &plan, &halo));
-        CK(cudaMemcpy(c->grp, halo.grp.data(), sizeof(int) * halo.grp.size(),
-                      cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->blk_grp, halo.blk_grp.data(), sizeof(int) * halo.blk_grp.size(),
-                      cudaMemcpyHostToDevice));
-        c->plan = plan;
-    }
     free_graphs(c);
     c->pgrid = t->particle_blocks_per_sm * c->num_sms;
     c->walk_form = t->walk_form;
     c->pcg_bps = t->pcg_blocks_per_sm;
+    c->pcg_balance = t->pcg_balance;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
+    if (c->loaded && c->plan.n_groups > 0) {
+        CK(cudaMemsetAsync(c->grp_iters, 0, sizeof(int) * c->plan.n_groups, c->s));
+        return replan_batch(c, nullptr);
+    }
     return PIC_OK;
 }
 
@@ -1437,6 +1482,9 @@ extern "C" int pic_step(pic_ctx c, int64_t n, pic_step_stats *stats)
     if (n == 0)
         return PIC_OK;
     int rc = ensure_dstats(c, n);
+    if (rc)
+        return rc;
+    rc = balance_batch(c);
     if (rc)
         return rc;
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(pic_step_stats) * (size_t)n, c->s));

@@ -227,6 +227,7 @@ struct PcgArgs {
     const int *grp;           // [4 * n_groups]
     const int *blk_grp;       // [grid] group of each block
     unsigned *grp_bar;        // [n_groups] barrier counters, zero at launch
+    int *grp_iters;           // [n_groups] iterations of each system's last solve (or null)
 };
 struct PcgLaunch {
     int grid, block;
@@ -250,10 +251,12 @@ struct PcgHalo {
 void set_global_error(const char *msg);
 
 // grp_slices[g] .. grp_slices[g+1]: slices of system g (n_sys >= 1)
-// blocks_per_sm > 0 caps the blocks of a batch solve at blocks_per_sm per SM
+// blocks_per_sm > 0 caps the blocks of a batch solve at blocks_per_sm per SM;
+// a batch's blocks are shared out in proportion to grp_work (null: to the
+// systems' slices)
 cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slices,
                      int num_sms, int precision, int variant, int n_sys, const int *grp_slices,
-                     int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo);
+                     const double *grp_work, int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo);
 // the most blocks a batch solve can use (its partial-sum buffer is sized for it)
 int pcg_max_group_blocks(int precision, int num_sms);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);

@@ -197,6 +197,8 @@ __device__ __forceinline__ void finish(const PcgArgs &a, int it, double relres, 
     if (threadIdx.x == 0 && grp_of(a).rank == 0) {
         if (status)
             atomicCAS(&a.st->err, 0, status);
+        if (a.grp_iters && a.n_groups > 0)
+            a.grp_iters[a.blk_grp[blockIdx.x]] = it;
         if (a.stats) {
             atomicMax(&a.stats->pcg_iters, it);
             atomicMax((unsigned long long *)&a.stats->pcg_relres,
@@ -1228,12 +1230,15 @@ int pcg_max_group_blocks(int precision, int num_sms)
 
 cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num_sms,
                      int precision, int variant, int n_sys, const int *grp_slices,
-                     int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo)
+                     const double *grp_work, int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo)
 {
     *plan = PcgLaunch{};
     if (n_sys > 1) {
         // a batch: the general kernels, each system on its own group of
-        // blocks, blocks in proportion to the system's slices
+        // blocks.  A group's time is its iterations x its slices / its
+        // blocks, so blocks in proportion to slices x iterations (grp_work,
+        // from the previous solve) make the groups finish together; without
+        // that information, in proportion to the slices.
         const void *fn = precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir;
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PCG_BLOCK, 0);
@@ -1246,13 +1251,17 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
             return cudaErrorInvalidConfiguration;
         std::vector<int> nb((size_t)n_sys, 1);
         int spare = max_blocks - n_sys;
-        long long tot = 0;
+        auto work = [&](int g) {
+            double sl = (double)(grp_slices[g + 1] - grp_slices[g]);
+            return grp_work ? grp_work[g] : sl;
+        };
+        double tot = 0.0;
         for (int g = 0; g < n_sys; ++g)
-            tot += grp_slices[g + 1] - grp_slices[g];
+            tot += work(g);
         int used = 0;
         for (int g = 0; g < n_sys; ++g) {
             long long sl = grp_slices[g + 1] - grp_slices[g];
-            int want = (int)((double)spare * (double)sl / (double)(tot > 0 ? tot : 1));
+            int want = (int)((double)spare * work(g) / (tot > 0.0 ? tot : 1.0));
             int cap = (int)((sl + PCG_WARPS - 1) / PCG_WARPS);  // at most a slice per warp
             want = std::min(want, std::max(0, cap - 1));
             nb[g] += want;
