@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--ensemble", type=int, default=64, help="replicas of the batched ensemble")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -295,6 +297,132 @@ def roofline(res, fp64):
     return roof, out_k
 
 
+# ---------------------------------------------------------------------------
+# the batched ensemble: 64 field-emitter replicas in one context
+# ---------------------------------------------------------------------------
+ENSEMBLE_WSP = 0.015
+
+
+def ensemble_inputs(n_rep):
+    """The seeded ensemble (radius 3 or 6 nm, E0 ~ U(8, 12) GV/m, 64k-1M tets
+    per replica) and a starting population of 10 % of each replica's
+    tetrahedron count, clipped to 1e4-5e5 SPs, in batch numbering."""
+    from paper_1906_08125_gb300 import inputs
+    b = inputs.ensemble(n_rep=n_rep, seed=0)
+    pops = []
+    for r, m in enumerate(b.members):
+        n = int(np.clip(0.1 * m.n_tets, 1e4, 5e5))
+        x, v, cell, pid = inputs.random_particles(m, n, seed=100 + r, v_scale=3e6, v_up=1.5e7)
+        pops.append((x, v, cell + b.tet_off[r], pid + (np.int64(r) << np.int64(32))))
+    cat = tuple(np.concatenate([p[k] for p in pops]) for k in range(4))
+    return b, (cat[0], cat[1], cat[2].astype(np.int32), cat[3])
+
+
+def bytes_batch_pcg(ri, fp64, cheb, outer):
+    """bytes_pcg summed over the replicas of a batch, each with its own
+    iteration count (the last solve's), stored entries and free DOFs."""
+    total = 0
+    for it, nnz, n in zip(ri["pcg_iters"], ri["stored"], ri["free_dofs"]):
+        total += bytes_pcg({"pcg_iters": int(it), "pcg_outer": outer},
+                           {"n_free": int(n), "nnz": int(nnz)}, fp64, cheb)
+    return total
+
+
+def run_ensemble(n_rep, steps, warmup):
+    import torch
+    from paper_1906_08125_gb300 import autotune
+    from paper_1906_08125_gb300 import configs as K
+    from paper_1906_08125_gb300 import picfem as P
+    P.load()
+    b, cat = ensemble_inputs(n_rep)
+    peak, kind = peaks()
+    forms = {"fp32_ir": dict(precision=K.PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
+             "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0)}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"replicas": n_rep, "tets": int(b.mesh.n_tets), "nodes": int(b.mesh.n_nodes),
+           "emitting_faces": int(b.mesh.n_faces), "sp_start": int(len(cat[3])),
+           "w_sp": ENSEMBLE_WSP, "pcg_rtol": 1e-6,
+           "l2": "not flushed: the batch's matrix and SPs (> 1 GB) exceed L2",
+           "batched": {}, "sequential": {}}
+    state = None
+    for name, form in forms.items():
+        p = K.params(w_sp=ENSEMBLE_WSP, capacity=12_000_000, **form)
+        c = P.Context(p).mesh_load_batch(b)
+        c.init_potential()
+        c.set_particles(*cat)
+        c.deposit()
+        c.poisson_solve()
+        c.step(warmup, stats=False)
+        entry = {}
+        if name == "fp32_ir":
+            state = (c.potential(), c.particles(), c.step_index)
+            knobs, _, trials = autotune.tune(
+                c, steps=3, warmup=1, use_cache=False,
+                space={"particle_blocks_per_sm": (8, 16), "pcg_cheb_degree": (4, 6)})
+            entry["tuning"] = knobs
+            entry["tuning_trials"] = len(trials)
+            c.step(2, stats=False)                  # balance on the tuned solves
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        st = c.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ri = c.replica_info()
+        c.profile(True)
+        c.step(2, stats=False)
+        prof = c.profile_read()
+        c.profile(False)
+        pcg_ms = prof["pcg"][1] / prof["pcg"][0]
+        cheb = c.tuning()["pcg_cheb_degree"]
+        alg = bytes_batch_pcg(ri, form["precision"] == K.PREC_FP64, cheb,
+                              int(np.median([s.pcg_outer for s in st])))
+        gbs = alg / (pcg_ms * 1e-3) / 1e9
+        entry.update({"ms_per_step": round(ms, 3),
+                      "replica_cycles_per_s": round(n_rep * 1e3 / ms, 1),
+                      "sp_in_flight": int(st[-1].alive),
+                      "pcg_ms_per_step": round(pcg_ms, 3),
+                      "pcg_share": round(pcg_ms * prof["pcg"][0]
+                                         / sum(v[1] for v in prof.values()), 3),
+                      "pcg_iters_replicas": [int(ri["pcg_iters"].min()),
+                                             int(np.median(ri["pcg_iters"])),
+                                             int(ri["pcg_iters"].max())],
+                      "roofline_pcg": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                                       "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                       "peak_source": kind}})
+        out["batched"][name] = entry
+        c.close()
+    # the same replicas one context at a time, from the FP32 batch's state
+    phi, parts, k = state
+    rid = np.searchsorted(b.tet_off, parts[2], side="right") - 1
+    for name, form in forms.items():
+        tot = 0.0
+        for r, m in enumerate(b.members):
+            p = K.params(w_sp=ENSEMBLE_WSP, capacity=2_000_000, E0=float(b.E0[r]), seed=r, **form)
+            c = P.Context(p).mesh_load(m)
+            c.set_potential(phi[b.node_off[r]:b.node_off[r + 1]])
+            sel = rid == r
+            ids = parts[3][sel].copy()
+            inj = (ids >> np.int64(62)) == 0
+            ids[inj] -= np.int64(3 * b.face_off[r]) << np.int64(18)
+            c.set_particles(parts[0][sel], parts[1][sel],
+                            (parts[2][sel] - b.tet_off[r]).astype(np.int32), ids)
+            c.step_index = k
+            c.step(2, stats=False)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            c.step(4, stats=False)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 4
+            c.close()
+        out["sequential"][name] = {"ms_per_ensemble_step": round(tot, 3),
+                                   "replica_cycles_per_s": round(n_rep * 1e3 / tot, 1)}
+    return out
+
+
 def run_e2e(res, steps):
     """The same metric through the C ABI with host buffers: per step the
     per-face work function goes host->device, one cycle runs, and the step
@@ -406,6 +534,9 @@ def main():
                     "pcg_iters_mean": round(float(r64["stats"]["pcg_iters"].mean()), 1)}
         r64["ctx"].close()
         del r64
+    ens = None
+    if rank == 0 and world == 1 and not args.no_ensemble:
+        ens = run_ensemble(args.ensemble, steps=10, warmup=10)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle(args.workload, args.cpu_steps)
@@ -416,7 +547,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp, **extra}
+                "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp,
+                "ensemble": ens, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -228,6 +228,13 @@ typedef struct {
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);
 
+/* Per replica (HOST arrays [n_rep], each nullable): CG iterations of its
+ * last solve in a batch (inner iterations in the FP32_IR form; 0 when the
+ * context holds one mesh), stored matrix entries (sliced ELLPACK, padding
+ * included), solver rows (a multiple of 32) and free DOFs. */
+int pic_replica_info(pic_ctx ctx, int32_t *pcg_iters, int64_t *stored, int32_t *rows,
+                     int32_t *free_dofs);
+
 /* Sizes of the loaded mesh and of the launches (info: HOST). */
 int pic_mesh_info(pic_ctx ctx, pic_info *info);
 
@@ -282,12 +289,44 @@ int poisson_solve(pic_ctx ctx, double *phi, int32_t *iters, double *rel_res);
 int pic_step(pic_ctx ctx, int64_t n_steps, pic_step_stats *stats);
 
 /*
- * pic_adjoint: d(collected charge)/d(E0) and d/d(work function per face)
- * over n_steps with checkpoints every ckpt_every steps.  Not built yet:
- * returns PIC_ERR_NOT_IMPLEMENTED.
+ * pic_adjoint: the charge Q collected through Gamma_1 over n_steps steps from
+ * the current state, and its derivatives with respect to the applied field
+ * of each replica and the work function of each emitting face, by reverse
+ * mode over the steps of Sec. II.B.
+ *
+ * The run starts with a deposit and a Poisson solve of the SPs present (so
+ * Phi_0 follows E0 too) and then takes n_steps ordinary steps; the context is
+ * left in the state after them.  Q is piecewise constant in the parameters
+ * (stochastic rounding of the SP counts, eq. rnd_nsp; discrete cell crossings
+ * and exits), so the derivative is that of the smooth model obtained by
+ * freezing the discrete decisions of this run: every SP injected from
+ * quadrangle q carries the weight n_sp,q(theta) / n_sp,q(theta0) (eq. nsp,
+ * n_sp proportional to J_FN(F_q, phi_f)); counts, random numbers, cells at
+ * the start of each step, fates, final cells and periodic shifts are those of
+ * the run; the deposit is taken without the integer rounding; the potential
+ * is the solution of M Phi = f.  Q = q w_sp sum over collected SPs of the
+ * weight.
+ *
+ * Memory: the state is kept every ckpt_every steps (SPs and Phi); the reverse
+ * pass recomputes one segment at a time and keeps its per-step SP arrays, so
+ * device memory grows with ckpt_every, not with n_steps.  The adjoint Poisson
+ * solves (M is symmetric: adjoint CG is CG on the same matrix) use the
+ * context's solver with relative residual 1e-10 (FP64 in the FP32_IR form
+ * through its FP64 refinement).
+ *
+ *   Q        HOST double [1]: collected charge [C] (nullable)
+ *   dQ_dE0   HOST double [n_rep]: dQ/dE0 of each replica [C m/V] (nullable)
+ *   dQ_dphi  HOST double [n_faces]: dQ/dphi_f [C/eV] (nullable)
+ * PIC_ERR_ARG for n_steps < 1 or ckpt_every < 1; device errors of the steps
+ * as in pic_step.
  */
-int pic_adjoint(pic_ctx ctx, int64_t n_steps, int32_t ckpt_every, double *dQ_dE0,
+int pic_adjoint(pic_ctx ctx, int64_t n_steps, int32_t ckpt_every, double *Q, double *dQ_dE0,
                 double *dQ_dphi);
+
+/* Applied field of each replica (E0 of the Neumann condition on Gamma_1,
+ * eq. poisson_bc): HOST double [n_rep]; the Neumann load is rebuilt as in
+ * mesh_load, the potential is not re-solved. */
+int pic_set_applied_field(pic_ctx ctx, const double *E0);
 
 /* ---- state (checkpoint / resume, parity) ---- */
 int pic_get_step(pic_ctx ctx, int64_t *step);

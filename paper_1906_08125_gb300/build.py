@@ -27,6 +27,7 @@ UNITS = {
     "pcg.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "adjoint.cu": [],
 }
 
 

@@ -26,11 +26,17 @@ enum KernelId {
     K_STEP_FUSED,
     K_PCG,
     K_UTIL,
+    K_COMPACT,
+    K_ADJ_FIELD,
+    K_ADJ_ROWS,
+    K_ADJ_SP,
     K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"field",          "inject_count", "inject_scan",
                                          "inject_emit",    "push_relocate", "deposit",
-                                         "step_fused",     "pcg",          "util"};
+                                         "step_fused",     "pcg",          "util",
+                                         "compact",        "adj_field",    "adj_rows",
+                                         "adj_sp"};
 
 struct ProfRec {
     int kid;
@@ -42,7 +48,7 @@ struct ProfRec {
 struct pic_ctx_s {
     pic_params p{};
     cudaStream_t s = nullptr;
-    int dev = 0, num_sms = 0;
+    int dev = 0, num_sms = 0, l2_bytes = 0;
     std::string err;
     // sizes
     int N = 0, T = 0, F = 0, NQ = 0, n_free = 0, n_pad = 0, n_slices = 0;
@@ -109,6 +115,10 @@ struct pic_ctx_s {
     int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1;
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
+    int *nfptr = nullptr, *nfcon = nullptr;   // Neumann contributions per row
+    int *rep_slice_d = nullptr;   // rep_slice on the device
+    std::vector<long long> rep_sell;   // stored matrix entries of each replica
+    std::vector<int> rep_free;         // free DOFs of each replica
     std::vector<int> grp_h, blk_grp_h;   // the batch plan's tables (host copies)
     // profiling
     bool prof = false;
@@ -345,7 +355,18 @@ int refresh_field(pic_ctx c, bool end_of_step = false)
     return PIC_OK;
 }
 
-int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
+// A solve with a right-hand side of the caller's (the adjoint solves): f =
+// rhs (rows), iterate and result in x (rows, warm start), scattered to the
+// node array out; stopping at relative residual rtol.
+struct SolveOverride {
+    const double *rhs;
+    double *x;
+    double *out;
+    double rtol;
+};
+
+int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
+            const SolveOverride *ov = nullptr)
 {
     PcgArgs g{};
     g.n = c->n_rows;
@@ -420,6 +441,17 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive)
     g.blk_grp = c->blk_grp;
     g.grp_bar = c->grp_bar;
     g.grp_iters = c->grp_iters;
+    // stream the matrix past L2 when it does not fit in about half of it
+    const double mat_bytes = (double)c->sell_len * (fp64(c) ? 12.0 : 8.0);
+    g.stream_matrix = mat_bytes > 0.5 * (double)c->l2_bytes ? 1 : 0;
+    g.rhs = nullptr;
+    if (ov) {
+        g.rhs = ov->rhs;
+        g.x = ov->x;
+        g.phi = ov->out;
+        g.rtol = ov->rtol;
+        g.grp_iters = nullptr;    // the balance follows the forward solves
+    }
     CK(cudaMemsetAsync(&c->st->bar_count, 0, sizeof(unsigned), c->s));
     if (c->plan.n_groups > 0)
         CK(cudaMemsetAsync(c->grp_bar, 0, sizeof(unsigned) * c->plan.n_groups, c->s));
@@ -493,6 +525,7 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         return fail(nullptr, PIC_ERR_CUDA, "pic_create: device lacks cooperative launch");
     }
     c->pgrid = c->num_sms * 8;
+    cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->dev);
     *out = c;
     return PIC_OK;
 }
@@ -943,6 +976,16 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     CK(pcg_plan(sptr.data(), scol.data(), n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
                 R, rep_slice.data(), nullptr, c->pcg_bps, &c->plan, &halo));
     c->rep_slice = rep_slice;
+    c->rep_sell.assign((size_t)R, 0);
+    c->rep_free.assign((size_t)R, 0);
+    for (int r = 0; r < R; ++r) {
+        c->rep_sell[r] = (long long)sptr[rep_slice[r + 1]] - sptr[rep_slice[r]];
+        for (long long n = rno[r]; n < rno[r + 1]; ++n)
+            c->rep_free[r] += dir[n] ? 0 : 1;
+    }
+    CK(dalloc(c, &c->rep_slice_d, rep_slice.size()));
+    CK(cudaMemcpyAsync(c->rep_slice_d, rep_slice.data(), sizeof(int) * rep_slice.size(),
+                       cudaMemcpyHostToDevice, c->s));
     // a batch solve can be re-planned with more blocks (pic_set_tuning)
     const int max_grid = c->plan.n_groups > 0
                              ? std::max(c->plan.grid, pcg_max_group_blocks(c->p.precision, c->num_sms))
@@ -1043,8 +1086,11 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     if (e == cudaSuccess) e = tmalloc((void **)&d_spos, sizeof(long long) * nnz);
     if (e == cudaSuccess) e = tmalloc((void **)&d_srow, sizeof(int) * nnz);
     if (e == cudaSuccess) e = tmalloc((void **)&d_scl, sizeof(int) * nnz);
-    if (e == cudaSuccess) e = tmalloc((void **)&d_fptr, sizeof(int) * (nf + 1));
-    if (e == cudaSuccess) e = tmalloc((void **)&d_fcon, sizeof(int) * (fcon.size() + 1));
+    // the Neumann tables stay (pic_set_applied_field rebuilds the load)
+    if (e == cudaSuccess) e = dalloc(c, &d_fptr, (size_t)nf + 1);
+    if (e == cudaSuccess) e = dalloc(c, &d_fcon, fcon.size() + 1);
+    c->nfptr = d_fptr;
+    c->nfcon = d_fcon;
     if (e == cudaSuccess) e = up(d_nb, nb4.data(), sizeof(int4) * T);
     if (e == cudaSuccess) e = up(d_cptr, cptr.data(), sizeof(long long) * (nnz + 1));
     if (e == cudaSuccess) e = up(d_contrib, contrib.data(), sizeof(int) * contrib.size());
@@ -1168,7 +1214,33 @@ static int balance_batch(pic_ctx c)
         any = any || it[g] > 0;
         w[g] = (double)(c->rep_slice[g + 1] - c->rep_slice[g]) * (double)std::max(it[g], 1);
     }
-    return any ? replan_batch(c, w.data()) : PIC_OK;
+    return replan_batch(c, any ? w.data() : nullptr);
+}
+
+extern "C" int pic_replica_info(pic_ctx c, int32_t *pcg_iters, int64_t *stored, int32_t *rows,
+                                int32_t *free_dofs)
+{
+    REQUIRE_MESH();
+    const int R = c->n_rep;
+    if (pcg_iters) {
+        if (c->plan.n_groups > 0) {
+            CK(cudaMemcpyAsync(pcg_iters, c->grp_iters, sizeof(int) * R, cudaMemcpyDeviceToHost,
+                               c->s));
+            CK(cudaStreamSynchronize(c->s));
+        } else {
+            for (int r = 0; r < R; ++r)
+                pcg_iters[r] = 0;
+        }
+    }
+    for (int r = 0; r < R; ++r) {
+        if (stored)
+            stored[r] = c->rep_sell[r];
+        if (rows)
+            rows[r] = 32 * (c->rep_slice[r + 1] - c->rep_slice[r]);
+        if (free_dofs)
+            free_dofs[r] = c->rep_free[r];
+    }
+    return PIC_OK;
 }
 
 extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
@@ -1201,10 +1273,9 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->pcg_bps = t->pcg_blocks_per_sm;
     c->pcg_balance = t->pcg_balance;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
-    if (c->loaded && c->plan.n_groups > 0) {
-        CK(cudaMemsetAsync(c->grp_iters, 0, sizeof(int) * c->plan.n_groups, c->s));
-        return replan_batch(c, nullptr);
-    }
+    // the iteration counts of the last solves stay valid weights
+    if (c->loaded && c->plan.n_groups > 0)
+        return c->pcg_balance ? balance_batch(c) : replan_batch(c, nullptr);
     return PIC_OK;
 }
 
@@ -1512,9 +1583,354 @@ extern "C" int pic_step(pic_ctx c, int64_t n, pic_step_stats *stats)
     return PIC_OK;
 }
 
-extern "C" int pic_adjoint(pic_ctx c, int64_t, int32_t, double *, double *)
+// ===========================================================================
+// adjoint: reverse mode over the steps (see pic_adjoint in picfem.h)
+// ===========================================================================
+namespace {
+
+// device memory owned by one pic_adjoint call, freed on every exit
+struct Scratch {
+    std::vector<void *> mem;
+    ~Scratch()
+    {
+        for (void *p : mem)
+            cudaFree(p);
+    }
+    template <typename T> cudaError_t get(T **p, size_t n)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            mem.push_back(q);
+            *p = (T *)q;
+        }
+        return e;
+    }
+};
+
+template <typename R> cudaError_t alloc_parts(Scratch &m, Particles<R> &P, long long n)
 {
-    return fail(c, PIC_ERR_NOT_IMPLEMENTED, "pic_adjoint is not built");
+    cudaError_t e = cudaSuccess;
+    R **f[6] = {&P.x, &P.y, &P.z, &P.vx, &P.vy, &P.vz};
+    for (R **q : f)
+        if (e == cudaSuccess)
+            e = m.get(q, (size_t)n);
+    if (e == cudaSuccess)
+        e = m.get(&P.cell, (size_t)n);
+    if (e == cudaSuccess)
+        e = m.get(&P.id, (size_t)n);
+    return e;
+}
+
+template <typename R>
+cudaError_t copy_parts(cudaStream_t s, Particles<R> dst, Particles<R> src, long long n)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const size_t b = sizeof(R) * (size_t)n;
+    R *d[6] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz};
+    R *o[6] = {src.x, src.y, src.z, src.vx, src.vy, src.vz};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(d[k], o[k], b, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst.cell, src.cell, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst.id, src.id, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToDevice,
+                            s);
+    return e;
+}
+
+template <typename R> struct Ckpt {      // the state at the start of a step
+    Particles<R> sp{};
+    long long n = 0;
+    double *phi = nullptr;
+    int64_t step = 0;
+};
+
+template <typename R> struct TapeStep {  // what the reverse pass needs of one step
+    Particles<R> pre{};                  // SPs before the push (old, then injected)
+    long long n = 0, n_old = 0;
+    int *dest = nullptr;                 // slot after the push, or DEST_*
+    double *phi = nullptr;               // Phi_k
+};
+
+struct AdjBuffers {
+    AdjSP a[2];
+    double *Ebar[2];
+    double *phibar, *rhs, *x, *fbar, *gE0, *gwf;
+    Vec4d *E64;
+    int *dest, *scan;
+};
+
+}  // namespace
+
+template <typename R> static int save_ckpt(pic_ctx c, Scratch &m, Ckpt<R> &k)
+{
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    k.n = (long long)h.cnt[c->a];
+    CK(alloc_parts(m, k.sp, k.n));
+    CK(copy_parts(c->s, k.sp, parts<R>(c, c->a), k.n));
+    CK(m.get(&k.phi, (size_t)c->N));
+    CK(cudaMemcpyAsync(k.phi, c->phi, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->s));
+    k.step = c->step;
+    return PIC_OK;
+}
+
+template <typename R> static int restore_ckpt(pic_ctx c, const Ckpt<R> &k)
+{
+    CK(copy_parts(c->s, parts<R>(c, c->a), k.sp, k.n));
+    const unsigned long long n = (unsigned long long)k.n;   // staged before return
+    const long long zero = 0;
+    CK(cudaMemcpyAsync(&c->st->cnt[c->a], &n, sizeof n, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(&c->st->n_fresh, &zero, sizeof zero, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->phi, k.phi, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->s));
+    k_phi_to_x<<<(c->n_rows + 255) / 256, 256, 0, c->s>>>(c->n_rows, c->dof_node, c->phi, c->x);
+    ++c->launches;
+    CK(cudaGetLastError());
+    c->step = k.step;
+    return refresh_field(c);
+}
+
+// One step with the same arithmetic as pic_step, but with survivors kept in
+// index order (ordered push + stable compaction back into the same buffer),
+// so that a recomputed segment reproduces the forward run SP for SP.  With a
+// tape, the step's SPs before the push, their destinations and Phi_k are kept.
+template <typename R>
+static int ordered_step(pic_ctx c, Scratch &m, const AdjBuffers &B, TapeStep<R> *tp,
+                        long long *collected)
+{
+    const int64_t step = c->step;
+    RunConst k = run_const(c);
+    if (tp) {
+        CK(m.get(&tp->phi, (size_t)c->N));
+        CK(cudaMemcpyAsync(tp->phi, c->phi, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->s));
+    }
+    int rc = do_inject<R>(c, step);
+    if (rc)
+        return rc;
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (h.err)
+        return check_device_error(c);
+    const long long n = (long long)h.cnt[c->a];
+    int *dest = B.dest;
+    if (tp) {
+        tp->n = n;
+        tp->n_old = n - h.n_fresh;
+        CK(alloc_parts(m, tp->pre, n));
+        CK(copy_parts(c->s, tp->pre, parts<R>(c, c->a), n));
+        CK(m.get(&tp->dest, (size_t)n));
+        dest = tp->dest;
+    }
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    LAUNCH(K_PUSH_RELOCATE, launch_push_relocate<R>(c->s, c->pgrid, view<R>(c), k, parts<R>(c, c->a),
+                                                    parts<R>(c, 1 - c->a), c->a, c->st, c->sstats,
+                                                    dest));
+    LAUNCH(K_COMPACT, launch_compact<R>(c->s, n, dest, parts<R>(c, 1 - c->a), parts<R>(c, c->a),
+                                        c->st, c->a, B.scan));
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
+    LAUNCH(K_DEPOSIT, launch_deposit<R>(c->s, c->pgrid, view<R>(c), k, parts<R>(c, c->a), c->a,
+                                        c->st, c->W));
+    rc = run_pcg(c, c->sstats, nullptr);
+    if (rc)
+        return rc;
+    rc = refresh_field(c);
+    if (rc)
+        return rc;
+    pic_step_stats st;
+    CK(cudaMemcpyAsync(&st, c->sstats, sizeof st, cudaMemcpyDeviceToHost, c->s));
+    rc = check_device_error(c);
+    if (rc)
+        return rc;
+    *collected += st.collected;
+    c->step = step + 1;
+    return PIC_OK;
+}
+
+// Reverse of recorded step k.  On entry B.a[in] is the adjoint of the state
+// after the step (by slot of `post`) and Ebar_next that of E_{k+1}; on exit
+// B.a[1 - in] holds the adjoint of the old SPs before the step and
+// Ebar_cur that of E_k.
+template <typename R>
+static int adjoint_step(pic_ctx c, const AdjBuffers &B, const TapeStep<R> &tp, Particles<R> post,
+                        int in, const double *Ebar_next, double *Ebar_cur)
+{
+    // E_{k+1} = field(Phi_{k+1}), M Phi_{k+1} = f(W_{k+1}, E0): adjoint solve
+    CK(cudaMemsetAsync(B.phibar, 0, sizeof(double) * c->N, c->s));
+    LAUNCH(K_ADJ_FIELD, launch_field_adjoint(c->s, c->T, c->rec64, c->tet4, Ebar_next, B.phibar));
+    LAUNCH(K_ADJ_ROWS, launch_gather_rows(c->s, c->n_rows, c->dof_node, B.phibar, B.rhs));
+    CK(cudaMemsetAsync(B.fbar, 0, sizeof(double) * c->N, c->s));
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    const SolveOverride ov{B.rhs, B.x, B.fbar, 1e-10};
+    int rc = run_pcg(c, c->sstats, nullptr, &ov);
+    if (rc)
+        return rc;
+    LAUNCH(K_ADJ_ROWS, launch_dE0(c->s, c->n_rows, B.x, c->fN, c->rep_slice_d, c->n_rep, c->E0_rep,
+                                  B.gE0));
+    if (!Ebar_cur)
+        return PIC_OK;
+    // E_k in FP64 from the recorded Phi_k
+    LAUNCH(K_FIELD, launch_field<double>(c->s, c->T, c->rec64, c->tet4, tp.phi, B.E64, nullptr,
+                                         nullptr));
+    CK(cudaMemsetAsync(Ebar_cur, 0, sizeof(double) * 3 * (size_t)c->T, c->s));
+    AdjStep<R> g;
+    g.n = tp.n;
+    g.n_old = tp.n_old;
+    g.pre = tp.pre;
+    g.post = post;
+    g.dest = tp.dest;
+    g.in = B.a[in];
+    g.out = B.a[1 - in];
+    g.rec64 = c->rec64;
+    g.tet = c->tet4;
+    g.E = B.E64;
+    g.fbar = B.fbar;
+    g.coef = (c->p.q * c->p.w_sp) / c->p.eps0;
+    g.Ebar = Ebar_cur;
+    g.gwf = B.gwf;
+    g.face_tet = c->face_tet;
+    g.face_rep = c->face_rep;
+    g.rep_face_off = c->rep_face_off;
+    g.fnhat = c->fnhat;
+    g.wf = c->wf;
+    g.seed = c->p.seed;
+    g.fn_model = c->p.fn_model;
+    g.qmdt = c->p.q_over_m * c->p.dt;
+    g.dt = c->p.dt;
+    g.qw = c->p.q * c->p.w_sp;
+    LAUNCH(K_ADJ_SP, launch_adjoint_sp<R>(c->s, g));
+    return PIC_OK;
+}
+
+template <typename R>
+static int run_adjoint(pic_ctx c, int64_t n_steps, int32_t ckpt_every, double *Q, double *dE0,
+                       double *dwf)
+{
+    Scratch m;
+    AdjBuffers B{};
+    const size_t cap = (size_t)c->p.capacity;
+    for (int s = 0; s < 2; ++s) {
+        double **f[7] = {&B.a[s].rx, &B.a[s].ry, &B.a[s].rz, &B.a[s].vx,
+                         &B.a[s].vy, &B.a[s].vz, &B.a[s].w};
+        for (double **q : f)
+            CK(m.get(q, cap));
+        CK(m.get(&B.Ebar[s], 3 * (size_t)c->T));
+    }
+    CK(m.get(&B.phibar, (size_t)c->N));
+    CK(m.get(&B.fbar, (size_t)c->N));
+    CK(m.get(&B.rhs, (size_t)c->n_pad));
+    CK(m.get(&B.x, (size_t)c->n_pad));
+    CK(m.get(&B.gE0, (size_t)c->n_rep));
+    CK(m.get(&B.gwf, (size_t)c->F));
+    CK(m.get(&B.E64, (size_t)c->T));
+    CK(m.get(&B.dest, cap));
+    CK(m.get(&B.scan, 2 * ((cap + 1023) / 1024) + 2));
+    CK(cudaMemsetAsync(B.x, 0, sizeof(double) * c->n_pad, c->s));
+    CK(cudaMemsetAsync(B.gE0, 0, sizeof(double) * c->n_rep, c->s));
+    CK(cudaMemsetAsync(B.gwf, 0, sizeof(double) * (c->F ? c->F : 1), c->s));
+
+    // forward: Phi_0 of the SPs present, then the steps, with checkpoints
+    CK(cudaMemsetAsync(c->W, 0, sizeof(unsigned long long) * c->N, c->s));
+    RunConst k = run_const(c);
+    LAUNCH(K_DEPOSIT, launch_deposit<R>(c->s, c->pgrid, view<R>(c), k, parts<R>(c, c->a), c->a,
+                                        c->st, c->W));
+    CK(cudaMemsetAsync(c->sstats, 0, sizeof(pic_step_stats), c->s));
+    int rc = run_pcg(c, c->sstats, nullptr);
+    if (!rc)
+        rc = refresh_field(c);
+    if (!rc)
+        rc = check_device_error(c);
+    if (rc)
+        return rc;
+    const int64_t n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+    std::vector<Ckpt<R>> ck((size_t)n_seg + 1);
+    long long collected = 0;
+    for (int64_t s = 0; s < n_seg; ++s) {
+        if ((rc = save_ckpt(c, m, ck[s])))
+            return rc;
+        const int64_t len = std::min<int64_t>(ckpt_every, n_steps - s * ckpt_every);
+        for (int64_t j = 0; j < len; ++j)
+            if ((rc = ordered_step<R>(c, m, B, nullptr, &collected)))
+                return rc;
+    }
+    if ((rc = save_ckpt(c, m, ck[n_seg])))
+        return rc;
+
+    // reverse, one recomputed segment at a time
+    CK(cudaMemsetAsync(B.Ebar[0], 0, sizeof(double) * 3 * (size_t)c->T, c->s));
+    int in = 0, eb = 0;   // B.a[in]: adjoint of the current state; B.Ebar[eb]: of its E
+    CK(cudaMemsetAsync(B.a[0].rx, 0, sizeof(double) * cap, c->s));
+    {
+        double *z[7] = {B.a[0].rx, B.a[0].ry, B.a[0].rz, B.a[0].vx, B.a[0].vy, B.a[0].vz, B.a[0].w};
+        for (double *q : z)
+            CK(cudaMemsetAsync(q, 0, sizeof(double) * cap, c->s));
+    }
+    for (int64_t s = n_seg - 1; s >= 0; --s) {
+        Scratch seg;
+        if ((rc = restore_ckpt(c, ck[s])))
+            return rc;
+        const int64_t len = std::min<int64_t>(ckpt_every, n_steps - s * ckpt_every);
+        std::vector<TapeStep<R>> tape((size_t)len);
+        long long dummy = 0;
+        for (int64_t j = 0; j < len; ++j)
+            if ((rc = ordered_step<R>(c, seg, B, &tape[j], &dummy)))
+                return rc;
+        for (int64_t j = len - 1; j >= 0; --j) {
+            Particles<R> post = j + 1 < len ? tape[j + 1].pre : ck[s + 1].sp;
+            if ((rc = adjoint_step<R>(c, B, tape[j], post, in, B.Ebar[eb], B.Ebar[1 - eb])))
+                return rc;
+            in = 1 - in;
+            eb = 1 - eb;
+        }
+        CK(cudaStreamSynchronize(c->s));   // before the segment's tape is freed
+    }
+    // Phi_0 = M^-1 f(W_0, E0)
+    TapeStep<R> none;
+    if ((rc = adjoint_step<R>(c, B, none, Particles<R>{}, in, B.Ebar[eb], nullptr)))
+        return rc;
+    if ((rc = restore_ckpt(c, ck[n_seg])))
+        return rc;
+    if (dE0)
+        CK(cudaMemcpyAsync(dE0, B.gE0, sizeof(double) * c->n_rep, cudaMemcpyDeviceToHost, c->s));
+    if (dwf && c->F)
+        CK(cudaMemcpyAsync(dwf, B.gwf, sizeof(double) * c->F, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (Q)
+        *Q = (c->p.q * c->p.w_sp) * (double)collected;
+    return check_device_error(c);
+}
+
+extern "C" int pic_adjoint(pic_ctx c, int64_t n_steps, int32_t ckpt_every, double *Q,
+                           double *dQ_dE0, double *dQ_dphi)
+{
+    REQUIRE_MESH();
+    if (n_steps < 1 || ckpt_every < 1 || c->step + n_steps >= (1LL << 21))
+        return fail(c, PIC_ERR_ARG, "pic_adjoint: bad step counts");
+    free_graphs(c);
+    return fp64(c) ? run_adjoint<double>(c, n_steps, ckpt_every, Q, dQ_dE0, dQ_dphi)
+                   : run_adjoint<float>(c, n_steps, ckpt_every, Q, dQ_dE0, dQ_dphi);
+}
+
+extern "C" int pic_set_applied_field(pic_ctx c, const double *E0)
+{
+    REQUIRE_MESH();
+    if (!E0)
+        return fail(c, PIC_ERR_ARG, "null E0");
+    for (int r = 0; r < c->n_rep; ++r)
+        if (!std::isfinite(E0[r]))
+            return fail(c, PIC_ERR_ARG, "pic_set_applied_field: non-finite E0");
+    CK(cudaMemcpyAsync(c->E0_rep, E0, sizeof(double) * c->n_rep, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemsetAsync(c->fN, 0, sizeof(double) * c->n_pad, c->s));
+    LAUNCH(K_UTIL, launch_neumann(c->s, c->n_rows, c->nfptr, c->nfcon, c->tet4, c->xyz, c->tet_rep,
+                                  c->E0_rep, c->fN));
+    CK(cudaStreamSynchronize(c->s));
+    if (c->n_rep == 1)
+        c->p.E0 = E0[0];
+    return PIC_OK;
 }
 
 // ===========================================================================

@@ -157,7 +157,7 @@ cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst
 template <typename R>
 cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                                  Particles<R> A, Particles<R> B, int a, DevState *st,
-                                 pic_step_stats *stats);
+                                 pic_step_stats *stats, int *dest = nullptr);
 template <typename R>
 cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                            Particles<R> A, int a, DevState *st, unsigned long long *W);
@@ -228,6 +228,8 @@ struct PcgArgs {
     const int *blk_grp;       // [grid] group of each block
     unsigned *grp_bar;        // [n_groups] barrier counters, zero at launch
     int *grp_iters;           // [n_groups] iterations of each system's last solve (or null)
+    int stream_matrix;        // general kernels: 1 stream the matrix past L2 (it does not fit)
+    const double *rhs;        // null: f from W and the Neumann load; else f[row] = rhs[row]
 };
 struct PcgLaunch {
     int grid, block;
@@ -260,5 +262,56 @@ cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slice
 // the most blocks a batch solve can use (its partial-sum buffer is sized for it)
 int pcg_max_group_blocks(int precision, int num_sms);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
+
+// ---------------------------------------------------------------------------
+// adjoint (pic_adjoint)
+// ---------------------------------------------------------------------------
+// where the push put SP i: its slot in the other buffer, or one of these
+enum { DEST_COLLECTED = -1, DEST_ABSORBED = -2 };
+
+// adjoint of the SP state (position, velocity, weight), FP64, structure of arrays
+struct AdjSP {
+    double *rx, *ry, *rz, *vx, *vy, *vz, *w;
+};
+
+// One step of the reverse pass over the SPs of a recorded step: `pre` holds
+// the step's SPs before the push (the n_old old ones, then the injected
+// ones), `dest` where the push sent each, `post` the buffer it wrote.
+template <typename R> struct AdjStep {
+    long long n, n_old;
+    Particles<R> pre, post;
+    const int *dest;
+    AdjSP in;                  // adjoint of the post-push state, by slot
+    AdjSP out;                 // adjoint of the pre-step state of the old SPs
+    const TetRec64 *rec64;
+    const int4 *tet;
+    const Vec4d *E;            // E_k in FP64
+    const double *fbar;        // node adjoint of the RHS of the solve after the step
+    double coef;               // q w_sp / eps0
+    double *Ebar;              // [3T] adjoint of E_k (accumulated)
+    double *gwf;               // [F] dQ/dphi_f (accumulated)
+    const int *face_tet, *face_rep, *rep_face_off;
+    const double *fnhat, *wf;
+    uint64_t seed;
+    int fn_model;
+    double qmdt, dt, qw;       // q/m dt, dt, q w_sp
+};
+template <typename R> cudaError_t launch_adjoint_sp(cudaStream_t s, const AdjStep<R> &g);
+// Phi_bar += E^T Ebar (E = -grad Phi per tetrahedron)
+cudaError_t launch_field_adjoint(cudaStream_t s, int T, const TetRec64 *rec, const int4 *tet,
+                                 const double *Ebar, double *phibar);
+// Stable compaction after an ordered push (dest[i] = 1 for a survivor held at
+// B[i], else DEST_*): survivors move to A[0..n_alive) in index order, dest[i]
+// becomes the survivor's slot, st->cnt[a] = n_alive, st->n_fresh = 0.
+// scratch: 2 * ceil(n / 1024) + 2 ints.
+template <typename R>
+cudaError_t launch_compact(cudaStream_t s, long long n, int *dest, Particles<R> B, Particles<R> A,
+                           DevState *st, int a, int *scratch);
+// rows of a node vector (0 on padding rows)
+cudaError_t launch_gather_rows(cudaStream_t s, int n_rows, const int *dof_node,
+                               const double *node_v, double *rows);
+// gE0[r] += sum over the rows of replica r of x_row fN_row / E0_r
+cudaError_t launch_dE0(cudaStream_t s, int n_rows, const double *x, const double *fN,
+                       const int *rep_slice, int n_rep, const double *E0_rep, double *gE0);
 
 }  // namespace pf

@@ -266,12 +266,12 @@ __device__ __forceinline__ int find_quad(const long long *qoff, int nq, long lon
 // counters with one atomic per warp
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void append(bool alive, const R r[3], const R v[3], int cell,
-                                       long long id, Particles<R> B, unsigned long long *cntB)
+__device__ __forceinline__ long long append(bool alive, const R r[3], const R v[3], int cell,
+                                            long long id, Particles<R> B, unsigned long long *cntB)
 {
     unsigned mask = __ballot_sync(FULL_MASK, alive);
     if (!mask)
-        return;
+        return -1;
     int lane = threadIdx.x & 31;
     unsigned long long base = 0;
     if (lane == 0)
@@ -287,7 +287,9 @@ __device__ __forceinline__ void append(bool alive, const R r[3], const R v[3], i
         B.vz[o] = v[2];
         B.cell[o] = cell;
         B.id[o] = id;
+        return o;
     }
+    return -1;
 }
 
 __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool act,
@@ -508,7 +510,7 @@ __global__ void k_inject_emit(MeshView<R> m, RunConst c, const long long *stepp,
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_push_relocate(MeshView<R> m, RunConst c, Particles<R> A, Particles<R> B, int a,
-                                DevState *st, pic_step_stats *stats)
+                                DevState *st, pic_step_stats *stats, int *dest)
 {
     long long n = (long long)st->cnt[a];
     long long n_old = n - st->n_fresh;
@@ -546,7 +548,24 @@ __global__ void k_push_relocate(MeshView<R> m, RunConst c, Particles<R> A, Parti
                 set_err(&st->err, PIC_ERR_WALK_LIMIT);
         }
         bool alive = act && fate == FATE_ALIVE;
-        append<R>(alive, r, v, t, id, B, cntB);
+        if (dest) {
+            // ordered form: a survivor keeps its index in B (the buffer is
+            // compacted afterwards, in index order); dest flags the fate
+            if (alive) {
+                B.x[i] = r[0];
+                B.y[i] = r[1];
+                B.z[i] = r[2];
+                B.vx[i] = v[0];
+                B.vy[i] = v[1];
+                B.vz[i] = v[2];
+                B.cell[i] = t;
+                B.id[i] = id;
+            }
+            if (act)
+                dest[i] = alive ? 1 : fate == FATE_COLLECTED ? DEST_COLLECTED : DEST_ABSORBED;
+        } else {
+            append<R>(alive, r, v, t, id, B, cntB);
+        }
         count_fates(fate, steps, wraps, act, stats);
     }
 }
@@ -874,9 +893,9 @@ cudaError_t launch_inject_emit(cudaStream_t s, int grid, MeshView<R> m, RunConst
 template <typename R>
 cudaError_t launch_push_relocate(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                                  Particles<R> A, Particles<R> B, int a, DevState *st,
-                                 pic_step_stats *stats)
+                                 pic_step_stats *stats, int *dest)
 {
-    k_push_relocate<R><<<grid, 256, 0, s>>>(m, c, A, B, a, st, stats);
+    k_push_relocate<R><<<grid, 256, 0, s>>>(m, c, A, B, a, st, stats, dest);
     return cudaGetLastError();
 }
 
@@ -930,6 +949,128 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// adjoint of one step for each SP (pic_adjoint)
+// ---------------------------------------------------------------------------
+// (d ln J/dF, d ln J/dphi) of fn_current: ln J = ln a + 2 ln Fn - ln phi
+// - 2 ln t(f) - v(f) b phi^1.5 / Fn, Fn = F 1e-9, f = c_S^2 Fn / phi^2; where
+// f is clamped to 1, v and t do not move with F or phi.
+__device__ void fn_dlog(double F, double phi, int model, double &dF, double &dphi)
+{
+    const double b = 6.830890, cS2 = 1.439964;
+    const double Fn = F * 1e-9;
+    double v = 1.0, t = 1.0, vp = 0.0, tp = 0.0, fF = 0.0, fphi = 0.0;
+    if (model == PIC_FN_MURPHY_GOOD) {
+        const double fr = (cS2 * Fn) / (phi * phi);
+        const double f = fr > 1.0 ? 1.0 : fr;
+        const double lf = log(f);
+        v = (1.0 - f) + (f / 6.0) * lf;
+        t = (1.0 + f / 9.0) - (f / 18.0) * lf;
+        if (fr <= 1.0) {
+            vp = lf / 6.0 - 5.0 / 6.0;      // dv/df
+            tp = 1.0 / 18.0 - lf / 18.0;    // dt/df
+            fF = cS2 / (phi * phi);         // df/dFn
+            fphi = -2.0 * fr / phi;         // df/dphi
+        }
+    }
+    const double s15 = phi * sqrt(phi);
+    const double dFn = 2.0 / Fn - 2.0 * (tp / t) * fF - b * s15 * (vp * fF / Fn - v / (Fn * Fn));
+    dphi = -1.0 / phi - 2.0 * (tp / t) * fphi - b * (vp * fphi * s15 + 1.5 * v * sqrt(phi)) / Fn;
+    dF = dFn * 1e-9;
+}
+
+// Reverse of one step for SP i of the step: collection (d Q / d omega =
+// q w_sp), deposit (f = coef W 2^-S: omega_bar += coef sum_j fbar_j N_j,
+// r_bar += coef sum_j fbar_j grad N_j in the final cell), drift r' = r + dt v'
+// (the walk's cells and shifts are frozen), then the kick v' = v + (q/m) dt E
+// of an old SP, or for a new one the emission v0 = (q/m) dt (1/2 + R3) E(t_f),
+// r0 = point + v0 dt R3 and its weight J(F, phi_f) / J(theta0) with
+// F = -E(t_f).n_f (eqs. sp_velocity, sp_displacement, nsp).
+template <typename R>
+__global__ void k_adjoint_sp(AdjStep<R> g)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.n)
+        return;
+    double rb[3] = {0.0, 0.0, 0.0}, vb[3] = {0.0, 0.0, 0.0}, wb = 0.0;
+    const int d = g.dest[i];
+    if (d >= 0) {
+        rb[0] = g.in.rx[d];
+        rb[1] = g.in.ry[d];
+        rb[2] = g.in.rz[d];
+        vb[0] = g.in.vx[d];
+        vb[1] = g.in.vy[d];
+        vb[2] = g.in.vz[d];
+        wb = g.in.w[d];
+        const int t = g.post.cell[d];
+        const double r[3] = {(double)g.post.x[d], (double)g.post.y[d], (double)g.post.z[d]};
+        const TetRec64 rec = load_rec(g.rec64 + t);
+        double lam[4];
+        barycentric<double>(rec, r, lam);
+        const int4 nd = __ldg(g.tet + t);
+        const double fb[4] = {g.fbar[nd.x], g.fbar[nd.y], g.fbar[nd.z], g.fbar[nd.w]};
+        wb += g.coef * (((fb[0] * lam[0] + fb[1] * lam[1]) + fb[2] * lam[2]) + fb[3] * lam[3]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double g0 = -((rec.j[c] + rec.j[3 + c]) + rec.j[6 + c]);
+            rb[c] += g.coef * (((fb[0] * g0 + fb[1] * rec.j[c]) + fb[2] * rec.j[3 + c]) +
+                               fb[3] * rec.j[6 + c]);
+        }
+    } else if (d == DEST_COLLECTED) {
+        wb = g.qw;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        vb[c] += g.dt * rb[c];
+    if (i < g.n_old) {
+        const size_t t = (size_t)g.pre.cell[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            atomicAdd(g.Ebar + 3 * t + c, g.qmdt * vb[c]);
+        g.out.rx[i] = rb[0];
+        g.out.ry[i] = rb[1];
+        g.out.rz[i] = rb[2];
+        g.out.vx[i] = vb[0];
+        g.out.vy[i] = vb[1];
+        g.out.vz[i] = vb[2];
+        g.out.w[i] = wb;
+        return;
+    }
+    const long long id = g.pre.id[i];
+    const long long step = id >> 42;
+    const int q = (int)((id >> 18) & ((1LL << 24) - 1));
+    const long long j = id & ((1LL << 18) - 1);
+    const int f = q / 3;
+    const int rep = g.face_rep[f];
+    const double R3 = uniform01(g.seed + (uint64_t)rep, (uint64_t)step,
+                                (uint64_t)(q - 3 * g.rep_face_off[rep]), (uint64_t)j, 255);
+    const size_t ft = (size_t)g.face_tet[f];
+    const double s = g.qmdt * (0.5 + R3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        atomicAdd(g.Ebar + 3 * ft + c, s * (vb[c] + (g.dt * R3) * rb[c]));
+    const Vec4d e = g.E[ft];
+    const double *n = g.fnhat + 3 * (size_t)f;
+    const double F = -((e.x * n[0] + e.y * n[1]) + e.z * n[2]);
+    if (!(F > 0.0) || wb == 0.0)
+        return;
+    double dF, dphi;
+    fn_dlog(F, g.wf[f], g.fn_model, dF, dphi);
+    atomicAdd(g.gwf + f, wb * dphi);
+    const double Fb = wb * dF;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        atomicAdd(g.Ebar + 3 * ft + c, -Fb * n[c]);
+}
+
+template <typename R> cudaError_t launch_adjoint_sp(cudaStream_t s, const AdjStep<R> &g)
+{
+    if (g.n <= 0)
+        return cudaSuccess;
+    k_adjoint_sp<R><<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 #define PF_INSTANTIATE(R)                                                                      \
     template cudaError_t launch_inject_count<R>(cudaStream_t, int, MeshView<R>, RunConst,      \
                                                 const long long *, int *, int *);              \
@@ -938,7 +1079,7 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
                                                Particles<R>, DevState *);                      \
     template cudaError_t launch_push_relocate<R>(cudaStream_t, int, MeshView<R>, RunConst,     \
                                                  Particles<R>, Particles<R>, int, DevState *,  \
-                                                 pic_step_stats *);                            \
+                                                 pic_step_stats *, int *);                     \
     template cudaError_t launch_deposit<R>(cudaStream_t, int, MeshView<R>, RunConst,           \
                                            Particles<R>, int, DevState *,                      \
                                            unsigned long long *);                              \
@@ -957,5 +1098,7 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
 
 PF_INSTANTIATE(double)
 PF_INSTANTIATE(float)
+template cudaError_t launch_adjoint_sp<double>(cudaStream_t, const AdjStep<double> &);
+template cudaError_t launch_adjoint_sp<float>(cudaStream_t, const AdjStep<float> &);
 
 }  // namespace pf

@@ -181,6 +181,8 @@ __device__ bool grid_sum(const double (&v)[NV], int set, const PcgArgs &a, doubl
 // padding rows (no node)
 __device__ __forceinline__ double rhs_entry(const PcgArgs &a, int row)
 {
+    if (a.rhs)
+        return a.rhs[row];
     int node = a.dof_node[row];
     if (node < 0)
         return 0.0;
@@ -244,6 +246,61 @@ __device__ __forceinline__ void scatter_phi(const PcgArgs &a, const Span &sp, in
 // and for systems too large for the resident kernels.
 // ---------------------------------------------------------------------------
 
+// Row `lane` of a 32-row slice times a vector: sum_c val[k_c] * X(col[k_c]),
+// accumulated in column order.  Eight columns' loads are issued before their
+// products so each warp keeps many loads in flight (the kernels are bound by
+// memory latency).  When the matrix is much larger than L2 it is streamed once
+// per product, and its loads are marked evict-first (__ldcs) so that the
+// vectors, which the gathers re-read, stay in L2; a matrix that fits is read
+// through the read-only path and stays in L2 across products.
+template <bool STREAM, typename T>
+__device__ __forceinline__ T ld_mat(const T *p)
+{
+    if constexpr (STREAM)
+        return __ldcs(p);
+    else
+        return __ldg(p);
+}
+
+template <typename ACC, bool STREAM, typename V, typename LoadX>
+__device__ __forceinline__ ACC sell_row_u(const V *__restrict__ val, const int *__restrict__ col,
+                                          int b, int width, int lane, LoadX X)
+{
+    constexpr int U = 8;
+    ACC sum = 0;
+    int c = 0;
+    for (; c + U <= width; c += U) {
+        const int k = b + c * 32 + lane;
+        V v[U];
+        int j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = ld_mat<STREAM>(val + k + 32 * u);
+            j[u] = ld_mat<STREAM>(col + k + 32 * u);
+        }
+        ACC x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            x[u] = X(j[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            sum += (ACC)v[u] * x[u];
+    }
+    for (; c < width; ++c) {
+        const int k = b + c * 32 + lane;
+        sum += (ACC)ld_mat<STREAM>(val + k) * X(ld_mat<STREAM>(col + k));
+    }
+    return sum;
+}
+
+template <typename ACC, typename V, typename LoadX>
+__device__ __forceinline__ ACC sell_row(const PcgArgs &a, const V *__restrict__ val, int b,
+                                        int width, int lane, LoadX X)
+{
+    return a.stream_matrix ? sell_row_u<ACC, true>(val, a.col, b, width, lane, X)
+                           : sell_row_u<ACC, false>(val, a.col, b, width, lane, X);
+}
+
 // FP64 Jacobi-PCG (the plain FP64 form)
 __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
 {
@@ -257,11 +314,9 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
     {
         int row = s * 32 + lane;
         int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-        double ax = 0.0;
-        for (int c = 0; c < width; ++c) {
-            int k = b + c * 32 + lane;
-            ax += a.val64[k] * a.x[a.col[k]];
-        }
+        const double *xv = a.x;
+        double ax = sell_row<double>(a, a.val64, b, width, lane,
+                                     [xv](int j) { return __ldcg(xv + j); });
         double f = rhs_entry(a, row);
         double r = f - ax;
         double z = a.dinv64[row] * r;
@@ -298,12 +353,10 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
         {
             int row = s * 32 + lane;
             int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-            double ap = 0.0;
-            for (int c = 0; c < width; ++c) {
-                int k = b + c * 32 + lane;
-                int j = a.col[k];
-                ap += a.val64[k] * (__ldcg(a.z + j) + beta * __ldcg(pold + j));
-            }
+            const double *zv = a.z, *pv = pold;
+            double ap = sell_row<double>(a, a.val64, b, width, lane, [zv, pv, beta](int j) {
+                return __ldcg(zv + j) + beta * __ldcg(pv + j);
+            });
             double p = a.z[row] + beta * pold[row];
             pnew[row] = p;
             a.ap[row] = ap;
@@ -376,11 +429,8 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
         {
             int row = s * 32 + lane;
             int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-            float ad = 0.f;
-            for (int c = 0; c < width; ++c) {
-                int k = b + c * 32 + lane;
-                ad += a.val32[k] * __ldcg(cur + a.col[k]);
-            }
+            float ad = sell_row<float>(a, a.val32, b, width, lane,
+                                       [cur](int j) { return __ldcg(cur + j); });
             float rc = a.ap32[row] - ad;
             float d = c1 * cur[row] + c2 * (a.dinv32[row] * rc);
             a.z32[row] = a.z32[row] + d;
@@ -414,11 +464,9 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
         {
             int row = s * 32 + lane;
             int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-            double ax = 0.0;
-            for (int c = 0; c < width; ++c) {
-                int k = b + c * 32 + lane;
-                ax += a.val64[k] * __ldcg(a.x + a.col[k]);
-            }
+            const double *xv = a.x;
+            double ax = sell_row<double>(a, a.val64, b, width, lane,
+                                         [xv](int j) { return __ldcg(xv + j); });
             double f = a.f[row];
             double r = f - ax;
             a.r[row] = r;
@@ -480,12 +528,10 @@ __global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
             {
                 int row = s * 32 + lane;
                 int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-                float ap = 0.f;
-                for (int c = 0; c < width; ++c) {
-                    int k = b + c * 32 + lane;
-                    int j = a.col[k];
-                    ap += a.val32[k] * (__ldcg(a.z32 + j) + b32 * __ldcg(pold + j));
-                }
+                const float *zv = a.z32, *pv = pold;
+                float ap = sell_row<float>(a, a.val32, b, width, lane, [zv, pv, b32](int j) {
+                    return __ldcg(zv + j) + b32 * __ldcg(pv + j);
+                });
                 float p = a.z32[row] + b32 * pold[row];
                 pnew[row] = p;
                 a.ap32[row] = ap;

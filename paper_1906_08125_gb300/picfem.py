@@ -21,10 +21,10 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_CUDA", -3: "PIC_ERR_MESH", -4: "PIC_ER
 PREC_FP64, PREC_FP32_IR = 0, 1
 
 EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_load",
-            "mesh_load_batch", "pic_get_tuning", "pic_set_tuning",
+            "mesh_load_batch", "pic_get_tuning", "pic_set_tuning", "pic_replica_info",
             "pic_mesh_info",
             "pic_init_potential", "inject", "push_relocate", "deposit", "poisson_solve",
-            "pic_step", "pic_adjoint", "pic_get_step", "pic_set_step", "pic_get_potential",
+            "pic_step", "pic_adjoint", "pic_set_applied_field", "pic_get_step", "pic_set_step", "pic_get_potential",
             "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
             "pic_get_particles", "pic_set_particles", "pic_set_work_function",
             "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync",
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "mesh_load_batch": [P, I32, P, P, P, I32, P, I32, P, P, P, P, I32, P, P, P],
         "pic_mesh_info": [P, C.POINTER(MeshInfo)],
         "pic_get_tuning": [P, C.POINTER(Tuning)],
+        "pic_replica_info": [P, P, P, P, P],
         "pic_set_tuning": [P, C.POINTER(Tuning)],
         "pic_init_potential": [P, C.POINTER(I32), C.POINTER(D)],
         "inject": [P, I64, C.POINTER(I64)],
@@ -117,7 +118,8 @@ def load(build_if_missing: bool = True):
         "deposit": [P, P],
         "poisson_solve": [P, P, C.POINTER(I32), C.POINTER(D)],
         "pic_step": [P, I64, C.POINTER(StepStats)],
-        "pic_adjoint": [P, I64, I32, P, P],
+        "pic_adjoint": [P, I64, I32, P, P, P],
+        "pic_set_applied_field": [P, P],
         "pic_get_step": [P, C.POINTER(I64)],
         "pic_set_step": [P, I64],
         "pic_get_potential": [P, P],
@@ -215,6 +217,15 @@ class Context:
         self.mesh = mesh
         return self
 
+    def replica_info(self) -> dict:
+        """Per replica: last solve's CG iterations (batches), stored matrix
+        entries, solver rows, free DOFs."""
+        R = self.info()["n_rep"]
+        it, st = np.zeros(R, np.int32), np.zeros(R, np.int64)
+        rows, free = np.zeros(R, np.int32), np.zeros(R, np.int32)
+        self._check(self.L.pic_replica_info(self.h, _ptr(it), _ptr(st), _ptr(rows), _ptr(free)))
+        return {"pcg_iters": it, "stored": st, "rows": rows, "free_dofs": free}
+
     def tuning(self) -> dict:
         t = Tuning()
         self._check(self.L.pic_get_tuning(self.h, C.byref(t)))
@@ -269,7 +280,23 @@ class Context:
         return list(arr)[:n] if stats else None
 
     def adjoint(self, n_steps, ckpt_every=20):
-        self._check(self.L.pic_adjoint(self.h, int(n_steps), int(ckpt_every), None, None))
+        """Collected charge Q over n_steps steps and (dQ/dE0 per replica,
+        dQ/dphi per face) by reverse mode (pic_adjoint); leaves the context
+        after the n_steps steps."""
+        Q = np.zeros(1)
+        gE0 = np.zeros(self.info()["n_rep"])
+        gwf = np.zeros(max(1, self.mesh.n_faces))
+        self._check(self.L.pic_adjoint(self.h, int(n_steps), int(ckpt_every), _ptr(Q), _ptr(gE0),
+                                       _ptr(gwf)))
+        return float(Q[0]), gE0, gwf[:self.mesh.n_faces]
+
+    def set_applied_field(self, E0):
+        """E0 of each replica (a scalar for a single mesh); rebuilds the
+        Neumann load, does not re-solve."""
+        e = np.ascontiguousarray(np.atleast_1d(np.asarray(E0, np.float64)))
+        if len(e) != self.info()["n_rep"]:
+            raise ValueError("one E0 per replica")
+        self._check(self.L.pic_set_applied_field(self.h, _ptr(e)))
 
     # state ---------------------------------------------------------------
     @property

@@ -1,0 +1,144 @@
+"""Parity of pic_adjoint (the reverse-mode derivative of the collected charge
+with respect to E0 and the per-face work functions) with the oracle's FP64
+reverse pass (oracle/adjoint.py, itself pinned by central finite differences
+and a closed form): same collected charge, gradients within 1e-6 relative in
+FP64; independence of the checkpoint interval; the FP32_IR form; replicas of
+a batch; the torch.autograd bridge; and the state the call leaves behind."""
+import numpy as np
+import pytest
+
+from paper_1906_08125_gb300 import configs as K
+from paper_1906_08125_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N_STEPS = 6
+
+
+@pytest.fixture(scope="module")
+def picfem():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_08125_gb300 import picfem as P
+    P.load()
+    return P
+
+
+def case(seed=1):
+    mesh = inputs.plate_mesh(nx=4, ny=4, nz=8, lx=20e-9, ly=20e-9, lz=40e-9,
+                             work_function=4.5, name="plate_tiny")
+    mesh.work_function = 4.5 + 0.2 * np.random.default_rng(5).uniform(-1, 1, mesh.n_faces)
+    parts = inputs.random_particles(mesh, 300, seed=seed, v_scale=2e6, v_up=4e6)
+    p = K.params(E0=1e10, w_sp=0.02, pcg_rtol=1e-13, pcg_max_iter=50000, capacity=200_000,
+                 seed=seed, precision=K.PREC_FP64, pcg_cheb_degree=0)
+    return mesh, parts, p
+
+
+@pytest.fixture(scope="module")
+def oracle_grad(oracle_mod):
+    from oracle import adjoint as A
+    mesh, parts, p = case()
+    orc = oracle_mod.Oracle(mesh, p)
+    orc.set_particles(*parts)
+    tape = A.record(orc, N_STEPS)
+    g = A.prepare(orc, tape)
+    return A.gradient(g, tape), tape
+
+
+def gpu_adjoint(picfem, ckpt, **over):
+    mesh, parts, p = case()
+    c = picfem.Context(dict(p, **over)).mesh_load(mesh)
+    c.set_particles(*parts)
+    return c, c.adjoint(N_STEPS, ckpt_every=ckpt)
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+def test_adjoint_fp64_matches_oracle(picfem, oracle_grad):
+    (Qo, gE0o, gwfo), tape = oracle_grad
+    c, (Q, gE0, gwf) = gpu_adjoint(picfem, ckpt=4)      # segments of 4 and 2 steps
+    assert Q == pytest.approx(tape.Q_recorded, rel=1e-14)
+    assert gE0[0] == pytest.approx(gE0o, rel=1e-6)
+    assert rel(gwf, gwfo) <= 1e-6
+    assert np.abs(gwfo).max() > 0 and gE0o != 0
+
+
+def test_adjoint_independent_of_checkpoint_interval(picfem):
+    ref = gpu_adjoint(picfem, ckpt=100)[1]
+    for ck in (1, 3):
+        Q, gE0, gwf = gpu_adjoint(picfem, ckpt=ck)[1]
+        assert Q == ref[0]
+        assert gE0[0] == pytest.approx(ref[1][0], rel=1e-11)
+        assert rel(gwf, ref[2]) <= 1e-11
+
+
+def test_adjoint_leaves_the_forward_state(picfem):
+    """After pic_adjoint the context holds the state of n_steps ordinary steps."""
+    mesh, parts, p = case()
+    a = picfem.Context(p).mesh_load(mesh)
+    a.set_particles(*parts)
+    a.adjoint(N_STEPS, ckpt_every=4)
+    b = picfem.Context(p).mesh_load(mesh)
+    b.set_particles(*parts)
+    b.deposit()
+    b.poisson_solve()
+    b.step(N_STEPS)
+    assert a.step_index == b.step_index == N_STEPS
+    sa, sb = a.particles(), b.particles()
+    oa, ob = np.argsort(sa[3]), np.argsort(sb[3])
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x[oa], y[ob])
+    assert np.abs(a.potential() - b.potential()).max() <= 1e-9 * np.abs(b.potential()).max()
+
+
+def test_adjoint_fp32ir_close_to_fp64(picfem, oracle_grad):
+    (Qo, gE0o, gwfo), tape = oracle_grad
+    c, (Q, gE0, gwf) = gpu_adjoint(picfem, ckpt=4, precision=K.PREC_FP32_IR, pcg_rtol=1e-8,
+                                   pcg_cheb_degree=4)
+    assert abs(Q - tape.Q_recorded) <= 2 * abs(tape.Q_recorded) / 100
+    assert gE0[0] == pytest.approx(gE0o, rel=2e-2)
+    assert rel(gwf, gwfo) <= 5e-2
+
+
+def test_adjoint_batch_replicas(picfem):
+    """Each replica's dQ/dE0 and dQ/dphi equal a one-replica adjoint of its
+    mesh with seed + r (FP64)."""
+    mesh, parts, p = case()
+    E0 = [1.0e10, 9.0e9]
+    b = inputs.batch_meshes([mesh, mesh], E0)
+    cb = picfem.Context(dict(p, seed=3)).mesh_load_batch(b)
+    cat = (np.concatenate([parts[0], parts[0]]), np.concatenate([parts[1], parts[1]]),
+           np.concatenate([parts[2], parts[2] + mesh.n_tets]).astype(np.int32),
+           np.concatenate([parts[3], parts[3] + (1 << 32)]))
+    cb.set_particles(*cat)
+    Qb, gE0b, gwfb = cb.adjoint(N_STEPS, ckpt_every=4)
+    Qs = 0.0
+    for r in range(2):
+        c = picfem.Context(dict(p, seed=3 + r, E0=E0[r])).mesh_load(mesh)
+        pr = (parts[0], parts[1], parts[2], parts[3] + (r << 32))
+        c.set_particles(*pr)
+        Q, gE0, gwf = c.adjoint(N_STEPS, ckpt_every=4)
+        Qs += Q
+        assert gE0b[r] == pytest.approx(gE0[0], rel=1e-8)
+        sl = slice(b.face_off[r], b.face_off[r + 1])
+        assert rel(gwfb[sl], gwf) <= 1e-8
+    assert Qb == pytest.approx(Qs, rel=1e-14)
+
+
+def test_autograd_bridge(picfem):
+    import torch
+    from paper_1906_08125_gb300.autograd import collected_charge
+    mesh, parts, p = case()
+    c = picfem.Context(p).mesh_load(mesh)
+    c.set_particles(*parts)
+    E0 = torch.tensor([1e10], dtype=torch.float64, requires_grad=True)
+    wf = torch.tensor(mesh.work_function, dtype=torch.float64, requires_grad=True)
+    Q = collected_charge(c, E0, wf, N_STEPS, ckpt_every=4)
+    (2.0 * Q).backward()
+    ref = gpu_adjoint(picfem, ckpt=4)[1]
+    assert float(Q.detach()) == ref[0]
+    assert E0.grad.item() == pytest.approx(2 * ref[1][0], rel=1e-11)
+    assert rel(wf.grad.numpy(), 2 * ref[2]) <= 1e-11

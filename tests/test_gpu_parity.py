@@ -313,8 +313,8 @@ def test_empty_and_error_paths(picfem, oracle_mod, plate_small):
         P.Context(K.params()).mesh_load(bad)
     assert e.value.code == -1
     with pytest.raises(P.PicError) as e:
-        P.Context(K.params()).mesh_load(plate_small).adjoint(10)
-    assert e.value.code == -7
+        P.Context(K.params()).mesh_load(plate_small).adjoint(0)
+    assert e.value.code == -1
 
 
 def test_profile_and_launch_count(picfem, plate_small):

@@ -60,8 +60,10 @@ def test_null_arguments_are_rejected(lib):
     lib.pic_last_error.argtypes = [ctypes.c_void_p]
     assert b"null" in lib.pic_last_error(None)
     lib.pic_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
-                                ctypes.c_void_p]
-    assert lib.pic_adjoint(None, 1, 20, None, None) == -7
+                                ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.pic_adjoint(None, 1, 20, None, None, None) == -1
+    lib.pic_set_applied_field.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.pic_set_applied_field(None, None) == -1
 
 
 def test_product_path_does_not_import_the_oracle():
