@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--ensemble", type=int, default=64, help="replicas of the batched ensemble")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=20, help="0 skips the adjoint timing")
     return ap.parse_args()
 
 
@@ -423,6 +424,42 @@ def run_ensemble(n_rep, steps, warmup):
     return out
 
 
+def run_adjoint_bench(workload, steps, ckpt_every):
+    """pic_adjoint on the benchmark workload: the collected charge over
+    `steps` steps and its gradient in E0 and every face's work function, timed
+    against the same steps run forward only (both from the same state)."""
+    import torch
+    from paper_1906_08125_gb300 import configs as K
+    from paper_1906_08125_gb300 import picfem
+    mesh, p, _ = K.workload(workload)
+    ctx = picfem.Context(p).mesh_load(mesh)
+    ctx.init_potential()
+    ctx.set_particles(*bench_population(mesh, K.WORKLOADS[workload]["target_sp"], seed=1000))
+    ctx.deposit()
+    ctx.poisson_solve()
+    ctx.step(5, stats=False)
+    phi, parts, k = ctx.potential(), ctx.particles(), ctx.step_index
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.step(steps, stats=False)
+    ctx.sync()
+    fwd = (time.perf_counter() - t0) * 1e3
+    ctx.set_potential(phi)
+    ctx.set_particles(*parts)
+    ctx.step_index = k
+    ctx.sync()
+    t0 = time.perf_counter()
+    Q, gE0, gwf = ctx.adjoint(steps, ckpt_every=ckpt_every)
+    adj = (time.perf_counter() - t0) * 1e3
+    ctx.close()
+    return {"workload": workload, "steps": steps, "ckpt_every": ckpt_every,
+            "precision": "fp32_ir", "faces": int(mesh.n_faces),
+            "forward_ms": round(fwd, 2), "adjoint_ms": round(adj, 2),
+            "adjoint_over_forward": round(adj / fwd, 2), "Q_C": Q,
+            "dQ_dE0": float(gE0[0]), "dQ_dphi_l2": float(np.linalg.norm(gwf)),
+            "dQ_dphi_nonzero_faces": int((gwf != 0).sum())}
+
+
 def run_e2e(res, steps):
     """The same metric through the C ABI with host buffers: per step the
     per-face work function goes host->device, one cycle runs, and the step
@@ -537,6 +574,9 @@ def main():
     ens = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         ens = run_ensemble(args.ensemble, steps=10, warmup=10)
+    adj = None
+    if rank == 0 and world == 1 and args.adjoint_steps > 0:
+        adj = run_adjoint_bench(args.workload, args.adjoint_steps, 10)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle(args.workload, args.cpu_steps)
@@ -548,7 +588,7 @@ def main():
                 "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp,
-                "ensemble": ens, **extra}
+                "ensemble": ens, "adjoint": adj, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
