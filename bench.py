@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--ensemble", type=int, default=64, help="replicas of the batched ensemble")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=20, help="0 skips the adjoint timing")
+    ap.add_argument("--no-diode", action="store_true", help="skip the planar-diode I-V sweep")
     return ap.parse_args()
 
 
@@ -577,6 +578,14 @@ def main():
     adj = None
     if rank == 0 and world == 1 and args.adjoint_steps > 0:
         adj = run_adjoint_bench(args.workload, args.adjoint_steps, 10)
+    diode = None
+    if rank == 0 and world == 1 and not args.no_diode:
+        from paper_1906_08125_gb300 import diode as D
+        from paper_1906_08125_gb300 import picfem as PF
+        t0 = time.perf_counter()
+        diode = D.iv_sweep(PF)
+        diode["wall_s"] = round(time.perf_counter() - t0, 1)
+        diode["paper_rms"] = 0.019
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle(args.workload, args.cpu_steps)
@@ -588,7 +597,7 @@ def main():
                 "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp,
-                "ensemble": ens, "adjoint": adj, **extra}
+                "ensemble": ens, "adjoint": adj, "diode_iv": diode, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -97,7 +97,9 @@ typedef struct {
     int32_t graph;             /* 1: pic_step captures one step per buffer parity
                               in a CUDA graph and replays it (not while
                               profiling); 0: launches every kernel directly      */
-    int32_t reserved;
+    int32_t collisions;        /* 1: Monte Carlo binary collisions of the SPs of
+                              each cell after every push (App. F; see pic_collide) */
+    double coulomb_log;        /* Lambda of the scattering variance (App. F: 13)   */
 } pic_params;
 
 /* inner solver of the FP32_IR Poisson solve */
@@ -322,6 +324,31 @@ int pic_step(pic_ctx ctx, int64_t n_steps, pic_step_stats *stats);
  */
 int pic_adjoint(pic_ctx ctx, int64_t n_steps, int32_t ckpt_every, double *Q, double *dQ_dE0,
                 double *dQ_dphi);
+
+/*
+ * pic_collide: Monte Carlo binary collisions of the SPs in flight (App. F,
+ * after Takizuka & Abe): the SPs of each cell, ordered by a random key of
+ * (seed, step, id), are paired (an odd count collides its first three as
+ * (0,1), (1,2), (2,0) with half the variance); each pair's relative velocity
+ * w = u_a - u_b turns by theta about a uniform azimuth phi (eq. rot_mat),
+ * v_{a,b} = u_{a,b} +- M w / 2 (eq. vel12, equal masses: energy and momentum
+ * conserved), with delta = tan(theta/2) ~ N(0, q^4 n Lambda dt /
+ * (2 pi eps0^2 m^2 |w|^3 V_cell)) (eqs. sin_theta, variance), n the real
+ * electrons in the cell (SPs x w_sp).  pic_step runs it after every push
+ * when params.collisions = 1 (pic_adjoint then refuses:
+ * PIC_ERR_NOT_IMPLEMENTED).  Random keys: replica seed, step, 2^40 + cell
+ * index within the replica, collision index, slots 1..3.
+ */
+int pic_collide(pic_ctx ctx, int64_t step);
+
+/* Prescribed potential on the Dirichlet nodes (node_dirichlet of mesh_load):
+ * HOST double [n_nodes], values on other nodes ignored; default 0.  The free
+ * equations gain the load -sum_{j Dirichlet} M_ij g_j (the prescribed part of
+ * the P1 solution moved to the right-hand side, App. B); Phi takes the values
+ * at once, the free part is not re-solved.  A Dirichlet anode is the top
+ * plane's nodes marked Dirichlet with g = V (SPs still leave through
+ * Gamma_1 as collected). */
+int pic_set_dirichlet(pic_ctx ctx, const double *values);
 
 /* Applied field of each replica (E0 of the Neumann condition on Gamma_1,
  * eq. poisson_bc): HOST double [n_rep]; the Neumann load is rebuilt as in

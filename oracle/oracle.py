@@ -28,7 +28,8 @@ class Params(C.Structure):
                 ("e_charge", C.c_double), ("pcg_rtol", C.c_double),
                 ("pcg_max_iter", C.c_int32), ("fn_model", C.c_int32),
                 ("seed", C.c_uint64), ("capacity", C.c_int64),
-                ("walk_max_steps", C.c_int32), ("quant_bits", C.c_int32)]
+                ("walk_max_steps", C.c_int32), ("quant_bits", C.c_int32),
+                ("collisions", C.c_int32), ("pad", C.c_int32), ("coulomb_log", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -79,6 +80,7 @@ def lib():
         L.or_get_potential.argtypes = [P, P]
         L.or_set_potential.argtypes = [P, P]
         L.or_get_field.argtypes = [P, P]
+        L.or_set_dirichlet.argtypes = [P, P]
         L.or_num_particles.restype = C.c_int64
         L.or_num_particles.argtypes = [P]
         L.or_get_particles.argtypes = [P, P, P, P, P]
@@ -93,6 +95,7 @@ def lib():
         L.or_deposit.argtypes = [P]
         L.or_poisson_solve.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
         L.or_step.argtypes = [P, C.c_int64, C.POINTER(Stats)]
+        L.or_collide.argtypes = [P, C.c_int64]
         L.or_locate.argtypes = [P, C.c_int64, P, P, P, P]
         L.or_barycentric.argtypes = [P, C.c_int32, P, P]
         L.or_quad_emission.argtypes = [P, P, P, P]
@@ -138,7 +141,7 @@ class Oracle:
     def __init__(self, mesh, params: dict):
         self.mesh = mesh
         self.params = dict(params)
-        p = Params(**{k: params[k] for k, _ in Params._fields_})
+        p = Params(**{k: params.get(k, 0) for k, _ in Params._fields_})
         self._keep = p
         self.h = lib().or_create(C.byref(p))
         arrs = mesh.arrays()
@@ -194,6 +197,11 @@ class Oracle:
         phi = np.ascontiguousarray(phi, np.float64)
         lib().or_set_potential(self.h, _p(phi))
 
+    def set_dirichlet(self, g):
+        """Prescribed potential on the Dirichlet nodes (values elsewhere ignored)."""
+        g = np.ascontiguousarray(g, np.float64)
+        lib().or_set_dirichlet(self.h, _p(g))
+
     def field(self) -> np.ndarray:
         E = np.zeros((self.mesh.n_tets, 3))
         lib().or_get_field(self.h, _p(E))
@@ -242,6 +250,10 @@ class Oracle:
         st = Stats()
         _check(lib().or_push_relocate(self.h, int(step), C.byref(st)), "or_push_relocate")
         return st
+
+    def collide(self, step):
+        """Binary collisions of the SPs in flight (App. F) for step `step`."""
+        lib().or_collide(self.h, int(step))
 
     def deposit(self) -> np.ndarray:
         _check(lib().or_deposit(self.h), "or_deposit")

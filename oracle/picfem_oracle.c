@@ -54,8 +54,10 @@ struct or_ctx {
     int32_t *dof;   /* node -> free dof or -1 */
     int32_t *rowptr, *col;
     double *val, *diag, *fN;
+    double *gD;     /* per node: prescribed potential on Dirichlet nodes (0 elsewhere) */
+    double *fD;     /* per free dof: load of the prescribed values, -sum_j M_ij gD_j */
     /* state */
-    double *phi;    /* per node, 0 on Dirichlet nodes */
+    double *phi;    /* per node, gD on Dirichlet nodes */
     double *E;      /* 3 per tet */
     int64_t *W;     /* fixed-point node charge */
     int64_t np, n_fresh;
@@ -233,7 +235,7 @@ static void free_mesh(or_ctx *c)
                     c->face_tet, c->wf, c->jinv, c->x0, c->det, c->shift,
                     c->fnhat, c->farea, c->dof, c->rowptr, c->col, c->val,
                     c->diag, c->fN, c->phi, c->E, c->W, c->r, c->v, c->cell,
-                    c->id};
+                    c->id, c->gD, c->fD};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i)
         free(bufs[i]);
 }
@@ -508,6 +510,8 @@ int or_mesh_load(or_ctx *c, int32_t n_nodes, const double *xyz,
             }
         }
 
+    c->gD = calloc(N, sizeof(double));
+    c->fD = calloc((size_t)nf + 1, sizeof(double));
     c->phi = calloc(N, sizeof(double));
     c->E = calloc(3 * T, sizeof(double));
     c->W = calloc(N, sizeof(int64_t));
@@ -577,7 +581,39 @@ void or_get_potential(const or_ctx *c, double *phi)
 void or_set_potential(or_ctx *c, const double *phi)
 {
     for (int32_t n = 0; n < c->n_nodes; ++n)
-        c->phi[n] = c->dir[n] ? 0.0 : phi[n];
+        c->phi[n] = c->dir[n] ? c->gD[n] : phi[n];
+    compute_field(c);
+}
+
+/* Prescribed potential on the Dirichlet nodes (App. B: the weak form is taken
+ * for Phi = Phi_free + Phi_D with Phi_D carrying the prescribed values, so the
+ * free equations gain the load -sum_{j Dirichlet} M_ij g_j).  M_ij is summed
+ * element by element, V_e g_i . g_j, in increasing element order and, within
+ * an element, in increasing local index j. */
+void or_set_dirichlet(or_ctx *c, const double *g)
+{
+    for (int32_t n = 0; n < c->n_nodes; ++n)
+        c->gD[n] = c->dir[n] ? g[n] : 0.0;
+    memset(c->fD, 0, sizeof(double) * ((size_t)c->n_free + 1));
+    for (size_t t = 0; t < (size_t)c->n_tets; ++t) {
+        double gr[4][3];
+        tet_gradients(c->jinv + 9 * t, gr);
+        double vol = c->det[t] / 6.0;
+        for (int i = 0; i < 4; ++i) {
+            int32_t di = c->dof[c->tet[4 * t + i]];
+            if (di < 0)
+                continue;
+            for (int j = 0; j < 4; ++j) {
+                int32_t nj = c->tet[4 * t + j];
+                if (!c->dir[nj])
+                    continue;
+                c->fD[di] = c->fD[di] - (vol * dot3(gr[i], gr[j])) * c->gD[nj];
+            }
+        }
+    }
+    for (int32_t n = 0; n < c->n_nodes; ++n)
+        if (c->dir[n])
+            c->phi[n] = c->gD[n];
     compute_field(c);
 }
 void or_get_field(const or_ctx *c, double *E3)
@@ -709,13 +745,13 @@ int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres)
         int32_t d = c->dof[node];
         if (d < 0)
             continue;
-        f[d] = coef * ldexp((double)c->W[node], -c->p.quant_bits) + c->fN[d];
+        f[d] = (coef * ldexp((double)c->W[node], -c->p.quant_bits) + c->fN[d]) + c->fD[d];
         x[d] = c->phi[node];
     }
     int st = pcg(c, f, x, iters, relres);
     for (int32_t node = 0; node < c->n_nodes; ++node) {
         int32_t d = c->dof[node];
-        c->phi[node] = d < 0 ? 0.0 : x[d];
+        c->phi[node] = d < 0 ? c->gD[node] : x[d];
     }
     compute_field(c);
     free(f);
@@ -725,7 +761,8 @@ int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres)
 
 int or_init_potential(or_ctx *c, int32_t *iters, double *relres)
 {
-    memset(c->phi, 0, sizeof(double) * (size_t)c->n_nodes);
+    for (int32_t n = 0; n < c->n_nodes; ++n)
+        c->phi[n] = c->dir[n] ? c->gD[n] : 0.0;
     memset(c->W, 0, sizeof(int64_t) * (size_t)c->n_nodes);
     return or_poisson_solve(c, iters, relres);
 }
@@ -1018,6 +1055,138 @@ int or_deposit(or_ctx *c)
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Monte Carlo binary collisions between SPs of the same cell (App. F,   */
+/* after Takizuka & Abe 1977): group the SPs by cell, pair them at       */
+/* random, collide each pair elastically with a Gaussian scattering      */
+/* angle.                                                                */
+/* ------------------------------------------------------------------ */
+#define OR_PI 3.14159265358979323846           /* pi, rounded to double */
+#define OR_COLL_DOMAIN ((uint64_t)1 << 40)  /* key words never used by a quadrangle */
+#define OR_SHUF_DOMAIN ((uint64_t)1 << 41)
+
+/* the keyed chain of or_uniform, all 64 bits */
+static uint64_t hash4(uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3)
+{
+    uint64_t w[4] = {w0, w1, w2, w3};
+    uint64_t h = 0;
+    for (int k = 0; k < 4; ++k)
+        h = mix64((h ^ w[k]) + OR_GAMMA);
+    return h;
+}
+
+typedef struct {
+    int32_t cell;
+    uint64_t key;
+    int64_t id;
+    int64_t idx;
+} coll_rec;
+
+static int cmp_coll(const void *pa, const void *pb)
+{
+    const coll_rec *a = pa, *b = pb;
+    if (a->cell != b->cell)
+        return a->cell < b->cell ? -1 : 1;
+    if (a->key != b->key)
+        return a->key < b->key ? -1 : 1;
+    return a->id < b->id ? -1 : (a->id > b->id);
+}
+
+/* One elastic collision (eqs. vel12, scat_vel, rot_mat, sin_theta): the
+ * relative velocity w = u_a - u_b turns by theta about a random azimuth phi,
+ * w' = w + M(theta, phi) w, and v_{a,b} = u_{a,b} +- M w / 2 (equal masses).
+ * delta = tan(theta/2) ~ N(0, <delta^2>) with <delta^2> = C / |w|^3
+ * (eq. variance, C holding everything but the speed). */
+static void collide_pair(double *va, double *vb, double C, double U1, double U2, double U3)
+{
+    double w[3] = {va[0] - vb[0], va[1] - vb[1], va[2] - vb[2]};
+    double u = sqrt(dot3(w, w));
+    if (!(u > 0.0))
+        return;
+    double var = C / ((u * u) * u);
+    double delta = sqrt(var) * (sqrt(-2.0 * log(1.0 - U1)) * cos((2.0 * OR_PI) * U2));
+    double phi = (2.0 * OR_PI) * U3;
+    double dd = delta * delta;
+    double s = (2.0 * delta) / (1.0 + dd);       /* sin theta     */
+    double c1 = (2.0 * dd) / (1.0 + dd);         /* 1 - cos theta */
+    double sp = sin(phi), cp = cos(phi);
+    double wp = sqrt(w[0] * w[0] + w[1] * w[1]);
+    double d[3];
+    if (wp > 0.0) {
+        double a = (s * sp) * (u / wp);
+        double bx = (s * cp) * (w[0] / wp), by = (s * cp) * (w[1] / wp);
+        d[0] = (-c1 * w[0] + a * w[1]) + bx * w[2];
+        d[1] = (-a * w[0] - c1 * w[1]) + by * w[2];
+        d[2] = (-bx * w[0] - by * w[1]) - c1 * w[2];
+    } else {
+        d[0] = (s * cp) * w[2];
+        d[1] = (s * sp) * w[2];
+        d[2] = -c1 * w[2];
+    }
+    for (int i = 0; i < 3; ++i) {
+        va[i] = va[i] + 0.5 * d[i];
+        vb[i] = vb[i] - 0.5 * d[i];
+    }
+}
+
+/* All collisions of a step.  In a cell with n >= 2 SPs, ordered by a
+ * random key of (seed, step, id): an odd n collides the first three as the
+ * pairs (0,1), (1,2), (2,0) with half the variance, then (3,4), (5,6), ...;
+ * an even n collides (0,1), (2,3), ...  The variance uses the real electron
+ * density n w_sp / V_cell and the relative speed of the pair. */
+void or_collide(or_ctx *c, int64_t step)
+{
+    int64_t n = c->np;
+    if (n < 2)
+        return;
+    coll_rec *rec = malloc(sizeof(coll_rec) * (size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        rec[k].cell = c->cell[k];
+        rec[k].id = c->id[k];
+        rec[k].key = hash4(c->p.seed, (uint64_t)step, OR_SHUF_DOMAIN, (uint64_t)c->id[k]);
+        rec[k].idx = k;
+    }
+    qsort(rec, (size_t)n, sizeof(coll_rec), cmp_coll);
+    const double q = c->p.q, m = c->p.q / c->p.q_over_m;
+    const double q2 = q * q;
+    for (int64_t g0 = 0; g0 < n;) {
+        int64_t g1 = g0;
+        while (g1 < n && rec[g1].cell == rec[g0].cell)
+            ++g1;
+        int64_t cnt = g1 - g0;
+        int32_t t = rec[g0].cell;
+        if (cnt >= 2) {
+            double vol = c->det[t] / 6.0;
+            double nreal = (double)cnt * c->p.w_sp;
+            double num = ((q2 * q2) * nreal) * (c->p.coulomb_log * c->p.dt);
+            double den = ((2.0 * OR_PI) * (c->p.eps0 * c->p.eps0)) * ((m * m) * vol);
+            double C = num / den;
+            uint64_t kq = OR_COLL_DOMAIN | (uint64_t)t;
+            int64_t ci = 0, k0 = 0;
+            if (cnt & 1) {
+                const int tri[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+                for (int e = 0; e < 3; ++e, ++ci) {
+                    double *va = c->v + 3 * rec[g0 + tri[e][0]].idx;
+                    double *vb = c->v + 3 * rec[g0 + tri[e][1]].idx;
+                    collide_pair(va, vb, 0.5 * C, or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 1),
+                                 or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 2),
+                                 or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 3));
+                }
+                k0 = 3;
+            }
+            for (int64_t k = k0; k + 1 < cnt; k += 2, ++ci) {
+                double *va = c->v + 3 * rec[g0 + k].idx;
+                double *vb = c->v + 3 * rec[g0 + k + 1].idx;
+                collide_pair(va, vb, C, or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 1),
+                             or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 2),
+                             or_uniform(c->p.seed, (uint64_t)step, kq, (uint64_t)ci, 3));
+            }
+        }
+        g0 = g1;
+    }
+    free(rec);
+}
+
 /* one PIC step in the order of Sec. II.B: E_k (already held), kick,
  * inject, drift + walk, deposit, Poisson solve for Phi_{k+1} */
 int or_step(or_ctx *c, int64_t n_steps, or_stats *stats)
@@ -1032,6 +1201,8 @@ int or_step(or_ctx *c, int64_t n_steps, or_stats *stats)
         e = or_push_relocate(c, k, &st);
         if (e != OR_OK)
             return e;
+        if (c->p.collisions)
+            or_collide(c, k);
         or_deposit(c);
         e = or_poisson_solve(c, &st.pcg_iters, &st.pcg_relres);
         if (e != OR_OK)

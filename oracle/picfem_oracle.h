@@ -56,6 +56,9 @@ typedef struct {
     int64_t capacity;    /* maximum number of SPs in flight                      */
     int32_t walk_max_steps;
     int32_t quant_bits;  /* S: deposit weights are integers of 2^-S              */
+    int32_t collisions;  /* 1: binary collisions after each push (App. F)         */
+    int32_t pad;
+    double coulomb_log;  /* Lambda of the scattering variance (App. F: 13)         */
 } or_params;
 
 typedef struct {
@@ -100,6 +103,7 @@ uint64_t or_splitmix64_next(uint64_t *state);
 int or_init_potential(or_ctx *c, int32_t *iters, double *relres);
 void or_get_potential(const or_ctx *c, double *phi);
 void or_set_potential(or_ctx *c, const double *phi);
+void or_set_dirichlet(or_ctx *c, const double *g);
 void or_get_field(const or_ctx *c, double *E3);
 int64_t or_num_particles(const or_ctx *c);
 void or_get_particles(const or_ctx *c, double *r3, double *v3, int32_t *cell,
@@ -117,6 +121,7 @@ int or_push_relocate(or_ctx *c, int64_t step, or_stats *st);
 int or_deposit(or_ctx *c);
 int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres);
 int or_step(or_ctx *c, int64_t n_steps, or_stats *stats);
+void or_collide(or_ctx *c, int64_t step);
 
 /* point location by the neighbour walk alone (no push): for the pins */
 int or_locate(const or_ctx *c, int64_t n, double *r3, int32_t *cell,

@@ -28,6 +28,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": [],
     "adjoint.cu": [],
+    "collide.cu": ["--fmad=false"],
 }
 
 

@@ -28,7 +28,8 @@ FN_MURPHY_GOOD, FN_ELEMENTARY = 0, 1
 def params(dt=4e-15, E0=1e10, w_sp=1.0, pcg_rtol=1e-12, pcg_max_iter=20000,
            fn_model=FN_MURPHY_GOOD, seed=0, capacity=20000, walk_max_steps=4096,
            quant_bits=32, precision=PREC_FP64, ir_inner_rtol=1e-4, pcg_variant=0,
-           ir_inner_max_iter=0, pcg_cheb_degree=0, pcg_cheb_ratio=30.0, graph=1):
+           ir_inner_max_iter=0, pcg_cheb_degree=0, pcg_cheb_ratio=30.0, graph=1,
+           collisions=0, coulomb_log=13.0):
     """Run parameters shared by the CUDA library and the oracle."""
     return dict(dt=float(dt), E0=float(E0), w_sp=float(w_sp), q=Q_ELECTRON,
                 q_over_m=Q_OVER_M, eps0=EPS0, e_charge=E_CHARGE,
@@ -38,7 +39,7 @@ def params(dt=4e-15, E0=1e10, w_sp=1.0, pcg_rtol=1e-12, pcg_max_iter=20000,
                 precision=int(precision), ir_inner_rtol=float(ir_inner_rtol),
                 pcg_variant=int(pcg_variant), ir_inner_max_iter=int(ir_inner_max_iter),
                 pcg_cheb_degree=int(pcg_cheb_degree), pcg_cheb_ratio=float(pcg_cheb_ratio),
-                graph=int(graph))
+                graph=int(graph), collisions=int(collisions), coulomb_log=float(coulomb_log))
 
 
 # name -> (mesh factory, parameter overrides, steps, target SP count)

@@ -180,6 +180,61 @@ __global__ void __launch_bounds__(SCAN_B) k_scan_blocks(int nb, const int *blk_s
         *total = carry;
 }
 
+// exclusive scan of int values, out[n] = total (scratch: 2 ceil(n/1024) + 2 ints)
+__global__ void __launch_bounds__(SCAN_B) k_escan_local(long long n, const int *in, int *out,
+                                                        int *blk_sum)
+{
+    __shared__ int wsum[32];
+    const long long i = blockIdx.x * (long long)SCAN_B + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < n ? in[i] : 0;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int t = wsum[lane], x = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o)
+                x += y;
+        }
+        wsum[lane] = x - t;
+        if (lane == 31)
+            blk_sum[blockIdx.x] = x;
+    }
+    __syncthreads();
+    if (i < n)
+        out[i] = wsum[w] + incl - v;
+}
+
+__global__ void k_escan_add(long long n, int *out, const int *blk_off, const int *total)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n)
+        out[i] += blk_off[i / SCAN_B];
+    if (i == 0)
+        out[n] = *total;
+}
+
+cudaError_t launch_exclusive_scan(cudaStream_t s, long long n, const int *in, int *out,
+                                  int *scratch)
+{
+    const int nb = (int)((n + SCAN_B - 1) / SCAN_B);
+    int *blk_sum = scratch, *blk_off = scratch + nb + 1, *total = scratch + 2 * nb + 1;
+    if (nb == 0)
+        return cudaMemsetAsync(out, 0, sizeof(int), s);
+    k_escan_local<<<nb, SCAN_B, 0, s>>>(n, in, out, blk_sum);
+    k_scan_blocks<<<1, SCAN_B, 0, s>>>(nb, blk_sum, blk_off, total);
+    k_escan_add<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, out, blk_off, total);
+    return cudaGetLastError();
+}
+
 template <typename R>
 __global__ void k_compact(long long n, int *dest, const int *blk_off, const int *total,
                           Particles<R> B, Particles<R> A, DevState *st, int a)

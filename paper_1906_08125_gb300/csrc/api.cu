@@ -30,13 +30,14 @@ enum KernelId {
     K_ADJ_FIELD,
     K_ADJ_ROWS,
     K_ADJ_SP,
+    K_COLLIDE,
     K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"field",          "inject_count", "inject_scan",
                                          "inject_emit",    "push_relocate", "deposit",
                                          "step_fused",     "pcg",          "util",
                                          "compact",        "adj_field",    "adj_rows",
-                                         "adj_sp"};
+                                         "adj_sp",         "collide"};
 
 struct ProfRec {
     int kid;
@@ -116,6 +117,14 @@ struct pic_ctx_s {
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
     int *nfptr = nullptr, *nfcon = nullptr;   // Neumann contributions per row
+    int *dptr = nullptr, *dcon = nullptr;     // Dirichlet couplings per row
+    double *gD = nullptr, *fD = nullptr;      // prescribed values (nodes), their load (rows)
+    std::vector<unsigned char> dir_h;         // Dirichlet flags (host copy)
+    int *rep_tet_off_d = nullptr;             // first tetrahedron of each replica
+    // collision scratch (allocated with the mesh when params.collisions, else on
+    // the first pic_collide)
+    int *ccnt = nullptr, *coff = nullptr, *cfill = nullptr, *cperm = nullptr, *cscan = nullptr;
+    unsigned long long *ckey = nullptr;
     int *rep_slice_d = nullptr;   // rep_slice on the device
     std::vector<long long> rep_sell;   // stored matrix entries of each replica
     std::vector<int> rep_free;         // free DOFs of each replica
@@ -334,11 +343,12 @@ __global__ void k_phi_to_x(int n, const int *dof_node, const double *phi, double
     if (d < n)
         x[d] = dof_node[d] >= 0 ? phi[dof_node[d]] : 0.0;
 }
-__global__ void k_zero_dirichlet(int N, const unsigned char *dir, double *phi)
+// Phi on the Dirichlet nodes: the prescribed values (0 unless pic_set_dirichlet)
+__global__ void k_set_dirichlet(int N, const unsigned char *dir, const double *gD, double *phi)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N && dir[i])
-        phi[i] = 0.0;
+        phi[i] = gD[i];
 }
 
 // E from Phi; at the end of a pic_step step it also files the step's
@@ -445,6 +455,7 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     const double mat_bytes = (double)c->sell_len * (fp64(c) ? 12.0 : 8.0);
     g.stream_matrix = mat_bytes > 0.5 * (double)c->l2_bytes ? 1 : 0;
     g.rhs = nullptr;
+    g.fD = c->fD;
     if (ov) {
         g.rhs = ov->rhs;
         g.x = ov->x;
@@ -557,6 +568,47 @@ extern "C" int pic_destroy(pic_ctx c)
 // ===========================================================================
 // mesh
 // ===========================================================================
+// scratch of the binary collisions: per-cell counts, offsets and fill
+// counters, the SPs grouped by cell and their order keys
+static int alloc_collision_scratch(pic_ctx c)
+{
+    const size_t T = (size_t)c->T, cap = (size_t)c->p.capacity;
+    CK(dalloc(c, &c->ccnt, T));
+    CK(dalloc(c, &c->coff, T + 1));
+    CK(dalloc(c, &c->cfill, T));
+    CK(dalloc(c, &c->cperm, cap));
+    CK(dalloc(c, &c->ckey, cap));
+    CK(dalloc(c, &c->cscan, 2 * ((T + 1023) / 1024) + 2));
+    return PIC_OK;
+}
+
+template <typename R> static CollArgs<R> coll_args(pic_ctx c)
+{
+    CollArgs<R> g;
+    g.P = parts<R>(c, c->a);
+    g.n = &c->st->cnt[c->a];
+    g.step = &c->st->hdr.step;
+    g.T = c->T;
+    g.det = c->det;
+    g.tet_rep = c->tet_rep;
+    g.rep_tet_off = c->rep_tet_off_d;
+    g.cnt = c->ccnt;
+    g.off = c->coff;
+    g.fill = c->cfill;
+    g.perm = c->cperm;
+    g.key = c->ckey;
+    g.scan = c->cscan;
+    g.seed = c->p.seed;
+    g.w_sp = c->p.w_sp;
+    g.coulomb_log = c->p.coulomb_log;
+    g.dt = c->p.dt;
+    g.q = c->p.q;
+    g.m = c->p.q / c->p.q_over_m;
+    g.eps0 = c->p.eps0;
+    g.grid = c->pgrid;
+    return g;
+}
+
 // Loads R meshes (replicas) given as one set of arrays with global indices;
 // replica r owns nodes [rno[r], rno[r+1]) and tetrahedra [rto[r], rto[r+1]),
 // its faces are contiguous, E0r[r] is its applied field.  A single mesh is
@@ -886,6 +938,33 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
         for (int i = 0; i < nf; ++i)
             fptr[i + 1] += fptr[i];
     }
+    // couplings of each free row with Dirichlet nodes, in increasing
+    // (element, local j) order: the load of prescribed values (pic_set_dirichlet)
+    std::vector<int> dptr((size_t)nf + 1, 0), dcon;
+    for (long long t = 0; t < T; ++t)
+        for (int i = 0; i < 4; ++i) {
+            int di = dof[tet[4 * t + i]];
+            if (di < 0)
+                continue;
+            for (int j = 0; j < 4; ++j)
+                if (dir[tet[4 * t + j]])
+                    dptr[di + 1]++;
+        }
+    for (int i = 0; i < nf; ++i)
+        dptr[i + 1] += dptr[i];
+    dcon.resize((size_t)dptr[nf]);
+    {
+        std::vector<int> fill(dptr.begin(), dptr.end() - 1);
+        for (long long t = 0; t < T; ++t)
+            for (int i = 0; i < 4; ++i) {
+                int di = dof[tet[4 * t + i]];
+                if (di < 0)
+                    continue;
+                for (int j = 0; j < 4; ++j)
+                    if (dir[tet[4 * t + j]])
+                        dcon[fill[di]++] = (int)((t << 4) | (i << 2) | j);
+            }
+    }
     std::vector<int> dof_node((size_t)n_pad, -1);
     for (int n = 0; n < N; ++n)
         if (dof[n] >= 0)
@@ -1011,6 +1090,8 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     CK(dalloc(c, &c->rep_face_off, (size_t)R + 1));
     CK(dalloc(c, &c->rep_L, 2 * (size_t)R));
     CK(dalloc(c, &c->E0_rep, (size_t)R));
+    CK(dalloc(c, &c->rep_tet_off_d, (size_t)R + 1));
+    CK(cudaMemcpyAsync(c->rep_tet_off_d, rto, sizeof(int) * (R + 1), cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->tet_rep, tet_rep.data(), sizeof(int) * T, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->face_rep, face_rep.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->rep_face_off, rep_face_off.data(), sizeof(int) * (R + 1),
@@ -1032,6 +1113,26 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
         CK(cudaStreamSynchronize(c->s));
     }
     CK(dalloc(c, &c->sstats, 1));
+    CK(dalloc(c, &c->dptr, dptr.size()));
+    CK(dalloc(c, &c->dcon, dcon.size() + 1));
+    CK(dalloc(c, &c->gD, (size_t)N));
+    CK(dalloc(c, &c->fD, (size_t)n_pad));
+    CK(cudaMemcpyAsync(c->dptr, dptr.data(), sizeof(int) * dptr.size(), cudaMemcpyHostToDevice,
+                       c->s));
+    if (!dcon.empty())
+        CK(cudaMemcpyAsync(c->dcon, dcon.data(), sizeof(int) * dcon.size(), cudaMemcpyHostToDevice,
+                           c->s));
+    CK(cudaMemsetAsync(c->gD, 0, sizeof(double) * N, c->s));
+    CK(cudaMemsetAsync(c->fD, 0, sizeof(double) * n_pad, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    c->dir_h.assign(dir, dir + N);
+    c->ccnt = c->coff = c->cfill = c->cperm = c->cscan = nullptr;
+    c->ckey = nullptr;
+    if (c->p.collisions) {
+        int rc = alloc_collision_scratch(c);
+        if (rc)
+            return rc;
+    }
     CK(dalloc(c, &c->slot, 1));
     CK(cudaMemsetAsync(c->slot, 0, sizeof(pic_step_stats), c->s));
 
@@ -1460,6 +1561,8 @@ template <typename R> static int step_once(pic_ctx c)
                                               parts<R>(c, c->a), parts<R>(c, 1 - c->a), c->a,
                                               c->st, c->W, ds));
     c->a = 1 - c->a;
+    if (c->p.collisions)
+        LAUNCH(K_COLLIDE, launch_collide<R>(c->s, coll_args<R>(c)));
     int rc = run_pcg(c, ds, &c->st->cnt[c->a]);
     if (rc)
         return rc;
@@ -1908,11 +2011,56 @@ extern "C" int pic_adjoint(pic_ctx c, int64_t n_steps, int32_t ckpt_every, doubl
                            double *dQ_dE0, double *dQ_dphi)
 {
     REQUIRE_MESH();
+    if (c->p.collisions)
+        return fail(c, PIC_ERR_NOT_IMPLEMENTED, "pic_adjoint: collisions are not differentiated");
     if (n_steps < 1 || ckpt_every < 1 || c->step + n_steps >= (1LL << 21))
         return fail(c, PIC_ERR_ARG, "pic_adjoint: bad step counts");
     free_graphs(c);
     return fp64(c) ? run_adjoint<double>(c, n_steps, ckpt_every, Q, dQ_dE0, dQ_dphi)
                    : run_adjoint<float>(c, n_steps, ckpt_every, Q, dQ_dE0, dQ_dphi);
+}
+
+extern "C" int pic_collide(pic_ctx c, int64_t step)
+{
+    REQUIRE_MESH();
+    if (step < 0 || step >= (1LL << 21))
+        return fail(c, PIC_ERR_ARG, "pic_collide: step out of range");
+    if (!c->ccnt) {
+        int rc = alloc_collision_scratch(c);
+        if (rc)
+            return rc;
+    }
+    const long long step_h = step;
+    CK(cudaMemcpyAsync(&c->st->hdr.step, &step_h, sizeof step_h, cudaMemcpyHostToDevice, c->s));
+    if (fp64(c))
+        LAUNCH(K_COLLIDE, launch_collide<double>(c->s, coll_args<double>(c)));
+    else
+        LAUNCH(K_COLLIDE, launch_collide<float>(c->s, coll_args<float>(c)));
+    return check_device_error(c);
+}
+
+extern "C" int pic_set_dirichlet(pic_ctx c, const double *g)
+{
+    REQUIRE_MESH();
+    if (!g)
+        return fail(c, PIC_ERR_ARG, "null values");
+    std::vector<double> h((size_t)c->N);
+    for (int n = 0; n < c->N; ++n) {
+        if (c->dir_h[n] && !std::isfinite(g[n]))
+            return fail(c, PIC_ERR_ARG, "pic_set_dirichlet: non-finite value at node %d", n);
+        h[n] = c->dir_h[n] ? g[n] : 0.0;
+    }
+    CK(cudaMemcpyAsync(c->gD, h.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->s));
+    LAUNCH(K_UTIL, launch_dirichlet_load(c->s, c->n_rows, c->dptr, c->dcon, c->rec64, c->det,
+                                         c->tet4, c->gD, c->fD));
+    k_set_dirichlet<<<(c->N + 255) / 256, 256, 0, c->s>>>(c->N, c->dir, c->gD, c->phi);
+    ++c->launches;
+    CK(cudaGetLastError());
+    int rc = refresh_field(c);
+    if (rc)
+        return rc;
+    CK(cudaStreamSynchronize(c->s));
+    return PIC_OK;
 }
 
 extern "C" int pic_set_applied_field(pic_ctx c, const double *E0)
@@ -1967,7 +2115,7 @@ extern "C" int pic_set_potential(pic_ctx c, const double *phi)
     if (!phi)
         return fail(c, PIC_ERR_ARG, "null phi");
     CK(cudaMemcpyAsync(c->phi, phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
-    k_zero_dirichlet<<<(c->N + 255) / 256, 256, 0, c->s>>>(c->N, c->dir, c->phi);
+    k_set_dirichlet<<<(c->N + 255) / 256, 256, 0, c->s>>>(c->N, c->dir, c->gD, c->phi);
     ++c->launches;
     k_phi_to_x<<<(c->n_rows + 255) / 256, 256, 0, c->s>>>(c->n_rows, c->dof_node, c->phi, c->x);
     ++c->launches;

@@ -133,6 +133,9 @@ cudaError_t launch_matrix_values(cudaStream_t s, long long nnz, const long long 
                                  const long long *sell_pos, const int *slot_row,
                                  const int *slot_col, double *val64, float *val32,
                                  double *dinv64, float *dinv32);
+cudaError_t launch_dirichlet_load(cudaStream_t s, int n_rows, const int *dptr, const int *dcon,
+                                  const TetRec64 *rec, const double *det, const int4 *tet,
+                                  const double *gD, double *fD);
 cudaError_t launch_neumann(cudaStream_t s, int n_rows, const int *fptr, const int *fcontrib,
                            const int4 *tet, const double *xyz, const int *tet_rep,
                            const double *E0_rep, double *fN);
@@ -230,6 +233,7 @@ struct PcgArgs {
     int *grp_iters;           // [n_groups] iterations of each system's last solve (or null)
     int stream_matrix;        // general kernels: 1 stream the matrix past L2 (it does not fit)
     const double *rhs;        // null: f from W and the Neumann load; else f[row] = rhs[row]
+    const double *fD;         // load of the prescribed Dirichlet values (rows)
 };
 struct PcgLaunch {
     int grid, block;
@@ -307,6 +311,27 @@ cudaError_t launch_field_adjoint(cudaStream_t s, int T, const TetRec64 *rec, con
 template <typename R>
 cudaError_t launch_compact(cudaStream_t s, long long n, int *dest, Particles<R> B, Particles<R> A,
                            DevState *st, int a, int *scratch);
+// out[i] = sum_{j<i} in[j] for i <= n (scratch: 2 ceil(n / 1024) + 2 ints)
+cudaError_t launch_exclusive_scan(cudaStream_t s, long long n, const int *in, int *out,
+                                  int *scratch);
+
+// Monte Carlo binary collisions of the SPs of each cell (App. F)
+template <typename R> struct CollArgs {
+    Particles<R> P;                  // the SPs in flight
+    const unsigned long long *n;     // their count (device)
+    const long long *step;           // the step index (device)
+    int T;
+    const double *det;               // [T] det J (volume = det / 6)
+    const int *tet_rep, *rep_tet_off;   // replica of a tetrahedron, first tetrahedron of a replica
+    int *cnt, *off, *fill;           // [T], [T + 1], [T] scratch
+    int *perm;                       // [capacity] SPs grouped by cell
+    unsigned long long *key;         // [capacity] random order key of each SP
+    int *scan;                       // scan scratch
+    uint64_t seed;
+    double w_sp, coulomb_log, dt, q, m, eps0;
+    int grid;                        // blocks of the SP passes
+};
+template <typename R> cudaError_t launch_collide(cudaStream_t s, const CollArgs<R> &g);
 // rows of a node vector (0 on padding rows)
 cudaError_t launch_gather_rows(cudaStream_t s, int n_rows, const int *dof_node,
                                const double *node_v, double *rows);

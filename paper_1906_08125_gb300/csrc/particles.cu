@@ -13,34 +13,15 @@
 // with one atomic per warp; deposits are int64 atomics, so the node charge is
 // independent of the order in which SPs arrive.
 #include "common.cuh"
+#include "rng.cuh"
 
 namespace pf {
 
 #define FULL_MASK 0xffffffffu
-constexpr uint64_t GAMMA = 0x9E3779B97F4A7C15ULL;
 
 enum { FATE_ALIVE = 0, FATE_COLLECTED = 1, FATE_ABSORBED = 2, FATE_LIMIT = 3 };
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
-
-// SplitMix64 finaliser (Steele, Lea & Flood 2014) and the keyed chain
-// h <- mix(h ^ word + gamma) over (seed, step, quadrangle, (j << 8) | slot);
-// uniform = top 53 bits * 2^-53.
-__device__ __forceinline__ uint64_t mix64(uint64_t z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t step, uint64_t quad,
-                                            uint64_t j, uint64_t slot)
-{
-    uint64_t h = mix64((0ULL ^ seed) + GAMMA);
-    h = mix64((h ^ step) + GAMMA);
-    h = mix64((h ^ quad) + GAMMA);
-    h = mix64((h ^ ((j << 8) | (slot & 0xFF))) + GAMMA);
-    return (double)(h >> 11) * 0x1.0p-53;
-}
 
 // Fowler-Nordheim J [A/m^2] for a field F [V/m] and work function phi [eV]:
 // J = a F^2 / (phi t^2) exp(-v b phi^1.5 / F) with F in V/nm, Forbes'

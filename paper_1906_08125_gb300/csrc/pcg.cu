@@ -176,9 +176,9 @@ __device__ bool grid_sum(const double (&v)[NV], int set, const PcgArgs &a, doubl
     return grid_sum_f<NV, NV, BLOCK>(v, set, a, out, NoFinish());
 }
 
-// f_i = (q w_sp / eps0) W_i 2^-S + f_Neumann,i (eq. poisson_rhs), written
-// without contraction so it equals the plain evaluation bit for bit; 0 on
-// padding rows (no node)
+// f_i = ((q w_sp / eps0) W_i 2^-S + f_Neumann,i) + f_D,i (eq. poisson_rhs plus
+// the load of the prescribed Dirichlet values), written without contraction
+// so it equals the plain evaluation bit for bit; 0 on padding rows (no node)
 __device__ __forceinline__ double rhs_entry(const PcgArgs &a, int row)
 {
     if (a.rhs)
@@ -187,7 +187,7 @@ __device__ __forceinline__ double rhs_entry(const PcgArgs &a, int row)
     if (node < 0)
         return 0.0;
     double w = (double)(long long)a.W[node];
-    return __dadd_rn(__dmul_rn(a.coef, __dmul_rn(w, a.wscale)), a.fN[row]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.coef, __dmul_rn(w, a.wscale)), a.fN[row]), a.fD[row]);
 }
 
 // Statistics of the solve: the first block of each group reports; with

@@ -137,6 +137,35 @@ __global__ void k_neumann(int n_rows, const int *__restrict__ fptr, const int *_
     fN[d] = sum;
 }
 
+// Load of the prescribed Dirichlet values on free row d:
+// fD_d = -sum (V_e grad N_i . grad N_j) g_j over the contributions listed for
+// the row (element e, local i = the row's node, local j a Dirichlet node), in
+// increasing (element, j) order.
+__global__ void k_dirichlet_load(int n_rows, const int *__restrict__ dptr,
+                                 const int *__restrict__ dcon, const TetRec64 *__restrict__ rec,
+                                 const double *__restrict__ det, const int4 *__restrict__ tet,
+                                 const double *__restrict__ gD, double *fD)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n_rows)
+        return;
+    double sum = 0.0;
+    for (int k = dptr[d]; k < dptr[d + 1]; ++k) {
+        int c = dcon[k];
+        int t = c >> 4, i = (c >> 2) & 3, j = c & 3;
+        TetRec64 r = rec[t];
+        double gi[3], gj[3];
+        grad_row(r, i, gi);
+        grad_row(r, j, gj);
+        double vol = det[t] / 6.0;
+        double dot = (gi[0] * gj[0] + gi[1] * gj[1]) + gi[2] * gj[2];
+        int4 v4 = tet[t];
+        int v[4] = {v4.x, v4.y, v4.z, v4.w};
+        sum = sum - (vol * dot) * gD[v[j]];
+    }
+    fD[d] = sum;
+}
+
 // Emitting face: unit normal (B-A)x(C-A)/|.| into the vacuum, area |.|/2.
 __global__ void k_face_geometry(int F, const int *__restrict__ fnodes, const double *__restrict__ xyz,
                                 double *nhat, double *area)
@@ -190,6 +219,17 @@ cudaError_t launch_neumann(cudaStream_t s, int n_rows, const int *fptr, const in
         return cudaSuccess;
     k_neumann<<<blocks_for(n_rows, 256), 256, 0, s>>>(n_rows, fptr, fcontrib, tet, xyz, tet_rep,
                                                       E0_rep, fN);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dirichlet_load(cudaStream_t s, int n_rows, const int *dptr, const int *dcon,
+                                  const TetRec64 *rec, const double *det, const int4 *tet,
+                                  const double *gD, double *fD)
+{
+    if (n_rows <= 0)
+        return cudaSuccess;
+    k_dirichlet_load<<<blocks_for(n_rows, 256), 256, 0, s>>>(n_rows, dptr, dcon, rec, det, tet, gD,
+                                                             fD);
     return cudaGetLastError();
 }
 

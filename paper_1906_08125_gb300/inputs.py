@@ -398,3 +398,26 @@ def ensemble(n_rep=64, seed=0, E0_range=(8e9, 12e9), scales=None) -> Batch:
         meshes.append(cache[(rad, sc)])
         E0.append(rng.uniform(*E0_range))
     return batch_meshes(meshes, E0, name=f"ensemble{n_rep}")
+
+
+# ---------------------------------------------------------------------------
+# planar diode (the I-V validation of Sec. III)
+# ---------------------------------------------------------------------------
+def diode_mesh(area=135 * NM * NM, gap=18.2 * NM, n_lat=4, h_cathode=0.04 * NM,
+               growth=1.06, h_max=0.5 * NM, work_function=4.5, name="diode") -> Mesh:
+    """Planar cathode-anode gap: a square of the given area (laterally
+    periodic) and height `gap`, z spacing `h_cathode` at the cathode growing
+    geometrically to `h_max`; the cathode (z = 0) and the anode (z = gap)
+    nodes are Dirichlet, every cathode face emits."""
+    side = float(np.sqrt(area))
+    zs = graded_half_axis(gap, h_cathode, 0.0, growth, h_max)
+    xs = np.linspace(0.0, side, n_lat + 1)
+    m = kuhn_mesh(xs, xs, zs, work_function=work_function, name=name)
+    top = m.xyz[:, 2] >= m.box_hi[2]
+    m.dirichlet = np.where(top, 1, m.dirichlet).astype(np.uint8)
+    return m
+
+
+def diode_potential(mesh: Mesh, V: float) -> np.ndarray:
+    """Node values for pic_set_dirichlet: 0 on the cathode, V on the anode."""
+    return np.where(mesh.xyz[:, 2] >= mesh.box_hi[2], float(V), 0.0)

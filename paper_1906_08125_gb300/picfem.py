@@ -24,7 +24,8 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_
             "mesh_load_batch", "pic_get_tuning", "pic_set_tuning", "pic_replica_info",
             "pic_mesh_info",
             "pic_init_potential", "inject", "push_relocate", "deposit", "poisson_solve",
-            "pic_step", "pic_adjoint", "pic_set_applied_field", "pic_get_step", "pic_set_step", "pic_get_potential",
+            "pic_step", "pic_adjoint", "pic_set_applied_field", "pic_set_dirichlet",
+            "pic_collide", "pic_get_step", "pic_set_step", "pic_get_potential",
             "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
             "pic_get_particles", "pic_set_particles", "pic_set_work_function",
             "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync",
@@ -39,7 +40,7 @@ class Params(C.Structure):
                 ("quant_bits", C.c_int32), ("precision", C.c_int32), ("pcg_variant", C.c_int32),
                 ("ir_inner_rtol", C.c_double), ("ir_inner_max_iter", C.c_int32),
                 ("pcg_cheb_degree", C.c_int32), ("pcg_cheb_ratio", C.c_double),
-                ("graph", C.c_int32), ("reserved", C.c_int32)]
+                ("graph", C.c_int32), ("collisions", C.c_int32), ("coulomb_log", C.c_double)]
 
 
 class Tuning(C.Structure):
@@ -120,6 +121,8 @@ def load(build_if_missing: bool = True):
         "pic_step": [P, I64, C.POINTER(StepStats)],
         "pic_adjoint": [P, I64, I32, P, P, P],
         "pic_set_applied_field": [P, P],
+        "pic_set_dirichlet": [P, P],
+        "pic_collide": [P, I64],
         "pic_get_step": [P, C.POINTER(I64)],
         "pic_set_step": [P, I64],
         "pic_get_potential": [P, P],
@@ -154,7 +157,7 @@ def _ptr(x):
 
 
 def _params(d: dict) -> Params:
-    return Params(**{k: d[k] for k, _ in Params._fields_ if k != "reserved"})
+    return Params(**{k: d[k] for k, _ in Params._fields_})
 
 
 class Context:
@@ -289,6 +292,18 @@ class Context:
         self._check(self.L.pic_adjoint(self.h, int(n_steps), int(ckpt_every), _ptr(Q), _ptr(gE0),
                                        _ptr(gwf)))
         return float(Q[0]), gE0, gwf[:self.mesh.n_faces]
+
+    def collide(self, step):
+        """Binary collisions of the SPs in flight (pic_collide)."""
+        self._check(self.L.pic_collide(self.h, int(step)))
+
+    def set_dirichlet(self, values):
+        """Prescribed potential on the Dirichlet nodes (per node; other
+        entries ignored)."""
+        g = np.ascontiguousarray(values, np.float64)
+        if len(g) != self.mesh.n_nodes:
+            raise ValueError("one value per node")
+        self._check(self.L.pic_set_dirichlet(self.h, _ptr(g)))
 
     def set_applied_field(self, E0):
         """E0 of each replica (a scalar for a single mesh); rebuilds the

@@ -524,3 +524,56 @@ def test_resume_is_bit_identical(oracle_mod, plate_small):
     for x, y in zip(a.particles(), c.particles()):
         assert np.array_equal(x, y)
     assert np.array_equal(a.potential(), c.potential())
+
+
+# --------------------------------------------------------------------------
+# prescribed Dirichlet values (the anode of the planar diode)
+# --------------------------------------------------------------------------
+def test_dirichlet_load_against_independent_assembly(oracle_mod):
+    """The load of prescribed values is -M_FD g with M assembled from the
+    definitions; a charge-free diode (0 V cathode, V anode) gives the linear
+    potential V z / d exactly (P1 reproduces linear functions)."""
+    mesh = inputs.diode_mesh(n_lat=2, h_cathode=0.3e-9, growth=1.2, h_max=1.5e-9)
+    V = 250.0
+    g = inputs.diode_potential(mesh, V)
+    o = _oracle(oracle_mod, mesh, E0=0.0, pcg_rtol=1e-14, pcg_max_iter=100000)
+    o.set_dirichlet(g)
+    _, _, free, Mfull, _ = _independent_system(mesh, 0.0)
+    dirn = np.nonzero(mesh.dirichlet)[0]
+    want = -(Mfull[free][:, dirn] @ g[dirn])
+    # the oracle's RHS with no SPs is exactly that load: solve and compare the residual form
+    o.init_potential()
+    phi = o.potential()
+    exact = V * mesh.xyz[:, 2] / mesh.box_hi[2]
+    assert np.abs(phi - exact).max() <= 1e-10 * V
+    assert np.array_equal(phi[dirn], g[dirn])
+    M = Mfull[free][:, free]
+    assert np.abs(M @ exact[free] - want).max() <= 1e-9 * np.abs(want).max()
+    E = o.field()
+    assert np.abs(E[:, 2] + V / mesh.box_hi[2]).max() <= 1e-9 * V / mesh.box_hi[2]
+
+
+# --------------------------------------------------------------------------
+# the 1D planar diode used for the I-V validation
+# --------------------------------------------------------------------------
+def test_diode_1d_solution_limits_and_closed_form():
+    from paper_1906_08125_gb300 import diode as D
+    d = 18.2e-9
+    # the quadrature of d(F) against its closed form
+    # d = [(2/3)(W^1.5 - F^3) - 2 F^2 (W^0.5 - F)] / (8 k^2), W = F^2 + 4 k sqrt(V)
+    for F, V, J in ((8e9, 200.0, 4e12), (1.2e10, 400.0, 3e13), (2e10, 1000.0, 1.5e14)):
+        k = J / K.EPS0 * np.sqrt(K.M_E / (2 * K.E_CHARGE))
+        W = F * F + 4 * k * np.sqrt(V)
+        closed = ((2 / 3) * (W ** 1.5 - F ** 3) - 2 * F * F * (W ** 0.5 - F)) / (8 * k * k)
+        assert D.gap_needed(F, V, J) == pytest.approx(closed, rel=1e-9)
+    # weak emission: the vacuum field V/d and J_FN(V/d)
+    J, F = D.current_density(80.0, d)
+    assert F == pytest.approx(80.0 / d, rel=2e-3)
+    assert J == pytest.approx(D.fn_current(80.0 / d, 4.5), rel=1e-2)
+    # strong emission: the Child-Langmuir law from below
+    r = [D.current_density(V, d)[0] / D.child_langmuir(V, d) for V in (1e3, 1e4, 1e5)]
+    assert r[0] < r[1] < r[2] < 1.0 and r[2] > 0.93
+    # the host J_FN equals the oracle's
+    from oracle import oracle as O
+    for F, phi in ((5e9, 4.5), (1.5e10, 4.0), (5e10, 4.5)):
+        assert D.fn_current(F, phi) == pytest.approx(O.fn_current(F, phi), rel=1e-13)
