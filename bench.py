@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=20, help="0 skips the adjoint timing")
     ap.add_argument("--no-diode", action="store_true", help="skip the planar-diode I-V sweep")
+    ap.add_argument("--no-large", action="store_true", help="skip the 8M-tet tip")
     return ap.parse_args()
 
 
@@ -461,6 +462,51 @@ def run_adjoint_bench(workload, steps, ckpt_every):
             "dQ_dphi_nonzero_faces": int((gwf != 0).sum())}
 
 
+def run_large(workload, steps, warmup):
+    """A few steps of a workload larger than the resident solver holds (the
+    8M-tet tip: the matrix and vectors exceed L2, the solver runs the general
+    kernels), from the seeded starting population."""
+    import torch
+    from paper_1906_08125_gb300 import configs as K
+    from paper_1906_08125_gb300 import picfem
+    t0 = time.perf_counter()
+    mesh, p, _ = K.workload(workload)
+    ctx = picfem.Context(p).mesh_load(mesh)
+    info = ctx.info()
+    ctx.init_potential()
+    ctx.set_particles(*bench_population(mesh, K.WORKLOADS[workload]["target_sp"], seed=2000))
+    ctx.deposit()
+    ctx.poisson_solve()
+    ctx.step(warmup, stats=False)
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = ctx.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.profile(True)
+    ctx.step(2, stats=False)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.close()
+    pcg_ms = prof["pcg"][1] / prof["pcg"][0]
+    row = {"pcg_iters": int(np.median([s.pcg_iters for s in st])),
+           "pcg_outer": int(np.median([s.pcg_outer for s in st]))}
+    alg = bytes_pcg(row, info, False, p["pcg_cheb_degree"])
+    peak, kind = peaks()
+    gbs = alg / (pcg_ms * 1e-3) / 1e9
+    return {"workload": workload, "tets": info["n_tets"], "free_dofs": info["n_free"],
+            "nnz": info["nnz"], "resident_solver": bool(info["pcg_resident"]),
+            "sp_in_flight": int(st[-1].alive), "steps": steps, "warmup": warmup,
+            "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 2), "unit": METRIC,
+            "pcg_ms_per_step": round(pcg_ms, 3), "pcg_iters": row["pcg_iters"],
+            "roofline_pcg": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": kind},
+            "setup_s": round(setup_s, 1)}
+
+
 def run_e2e(res, steps):
     """The same metric through the C ABI with host buffers: per step the
     per-face work function goes host->device, one cycle runs, and the step
@@ -578,6 +624,9 @@ def main():
     adj = None
     if rank == 0 and world == 1 and args.adjoint_steps > 0:
         adj = run_adjoint_bench(args.workload, args.adjoint_steps, 10)
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        large = run_large("tip_8m", steps=5, warmup=5)
     diode = None
     if rank == 0 and world == 1 and not args.no_diode:
         from paper_1906_08125_gb300 import diode as D
@@ -597,7 +646,7 @@ def main():
                 "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp,
-                "ensemble": ens, "adjoint": adj, "diode_iv": diode, **extra}
+                "ensemble": ens, "adjoint": adj, "diode_iv": diode, "tip_8m": large, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -217,6 +217,17 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           proportion to each replica's slices x the CG
  *                           iterations of its last solve, re-planned at the
  *                           start of every pic_step call; 0 by slices only
+ *   pcg_cheb_local          one-system (resident) solver: 0 applies the
+ *                           Chebyshev polynomial (or Jacobi) to the whole
+ *                           matrix; 1 to each solver block's own diagonal block
+ *                           of D^-1 M (no grid barrier inside the
+ *                           preconditioner); 2 adds to 1 the coarse correction
+ *                           R0^T A0^-1 R0 r over the blocks (R0 sums a block's
+ *                           rows, A0 = R0 M R0^T; one grid barrier); 3 is the
+ *                           whole-matrix polynomial plus that coarse
+ *                           correction (the default when pcg_cheb_degree >= 2;
+ *                           otherwise 0).  All are SPD; the stopping rule is
+ *                           unchanged
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -226,6 +237,7 @@ typedef struct {
     int32_t pcg_blocks_per_sm;
     int32_t pcg_cheb_degree;
     int32_t pcg_balance;
+    int32_t pcg_cheb_local;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);

@@ -88,6 +88,8 @@ struct pic_ctx_s {
     double *d0 = nullptr, *d1 = nullptr;
     float *d32_0 = nullptr, *d32_1 = nullptr;
     double cheb_b = 2.0;   // Gershgorin bound of D^-1 M
+    const float *coarse_inv = nullptr;   // two-level preconditioner: A0^-1 of the blocks
+    double *coarse_r = nullptr;
     // replicas of a batch (1 for a single mesh)
     int n_rep = 1, n_rows = 0;
     int *tet_rep = nullptr, *face_rep = nullptr, *rep_face_off = nullptr;
@@ -113,7 +115,7 @@ struct pic_ctx_s {
     long long launches = 0;
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
-    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1;
+    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0;
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
     int *nfptr = nullptr, *nfcon = nullptr;   // Neumann contributions per row
@@ -456,6 +458,9 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.stream_matrix = mat_bytes > 0.5 * (double)c->l2_bytes ? 1 : 0;
     g.rhs = nullptr;
     g.fD = c->fD;
+    g.cheb_local = c->cheb_local;
+    g.coarse_inv = c->coarse_inv;
+    g.coarse_r = c->coarse_r;
     if (ov) {
         g.rhs = ov->rhs;
         g.x = ov->x;
@@ -536,6 +541,9 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         return fail(nullptr, PIC_ERR_CUDA, "pic_create: device lacks cooperative launch");
     }
     c->pgrid = c->num_sms * 8;
+    // a Chebyshev-preconditioned solve gets the coarse correction over the
+    // solver blocks by default (the plain Jacobi form stays plain)
+    c->cheb_local = q.pcg_cheb_degree >= 2 ? 3 : 0;
     cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->dev);
     *out = c;
     return PIC_OK;
@@ -1237,6 +1245,73 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
             }
         }
         c->cheb_b = bmax > 0.0 ? bmax : 2.0;
+        // coarse matrix of the resident solver's blocks (two-level
+        // preconditioner): A0 = R0 M R0^T with R0 summing each block's rows,
+        // inverted here in FP64 (Cholesky)
+        c->coarse_inv = nullptr;
+        c->coarse_r = nullptr;
+        if (c->plan.resident) {
+            const int G = c->plan.grid;
+            std::vector<int> blk_of_slice((size_t)n_slices);
+            for (long long b = 0; b < G; ++b)
+                for (int sl = (int)((b * n_slices) / G); sl < (int)(((b + 1) * n_slices) / G); ++sl)
+                    blk_of_slice[sl] = (int)b;
+            std::vector<double> A0((size_t)G * G, 0.0);
+            for (int sl = 0; sl < n_slices; ++sl) {
+                const int w = (sptr[sl + 1] - sptr[sl]) / 32, bi = blk_of_slice[sl];
+                for (int l = 0; l < 32; ++l)
+                    for (int k = 0; k < w; ++k) {
+                        const size_t e = (size_t)sptr[sl] + (size_t)k * 32 + l;
+                        const double v = hv[e];
+                        if (v != 0.0)
+                            A0[(size_t)bi * G + blk_of_slice[scol[e] / 32]] += v;
+                    }
+            }
+            std::vector<double> L(A0);   // Cholesky A0 = L L^T (lower triangle)
+            bool spd = true;
+            for (int j = 0; j < G && spd; ++j) {
+                double d = L[(size_t)j * G + j];
+                for (int k = 0; k < j; ++k)
+                    d -= L[(size_t)j * G + k] * L[(size_t)j * G + k];
+                if (!(d > 0.0)) {
+                    spd = false;
+                    break;
+                }
+                d = std::sqrt(d);
+                L[(size_t)j * G + j] = d;
+                for (int i = j + 1; i < G; ++i) {
+                    double v = L[(size_t)i * G + j];
+                    for (int k = 0; k < j; ++k)
+                        v -= L[(size_t)i * G + k] * L[(size_t)j * G + k];
+                    L[(size_t)i * G + j] = v / d;
+                }
+            }
+            if (spd) {
+                std::vector<float> inv((size_t)G * G);
+                std::vector<double> col((size_t)G);
+                for (int c0 = 0; c0 < G; ++c0) {   // solve L L^T x = e_c0
+                    for (int i = 0; i < G; ++i) {
+                        double v = i == c0 ? 1.0 : 0.0;
+                        for (int k = 0; k < i; ++k)
+                            v -= L[(size_t)i * G + k] * col[k];
+                        col[i] = v / L[(size_t)i * G + i];
+                    }
+                    for (int i = G - 1; i >= 0; --i) {
+                        double v = col[i];
+                        for (int k = i + 1; k < G; ++k)
+                            v -= L[(size_t)k * G + i] * col[k];
+                        col[i] = v / L[(size_t)i * G + i];
+                    }
+                    for (int i = 0; i < G; ++i)
+                        inv[(size_t)i * G + c0] = (float)col[i];
+                }
+                float *ci = nullptr;
+                CK(dalloc(c, &ci, inv.size()));
+                CK(cudaMemcpy(ci, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice));
+                c->coarse_inv = ci;
+                CK(dalloc(c, &c->coarse_r, (size_t)G));
+            }
+        }
     }
     c->loaded = true;
     c->a = 0;
@@ -1353,6 +1428,7 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->pcg_blocks_per_sm = c->pcg_bps;
     t->pcg_cheb_degree = c->p.pcg_cheb_degree;
     t->pcg_balance = c->pcg_balance;
+    t->pcg_cheb_local = c->cheb_local;
     return PIC_OK;
 }
 
@@ -1363,7 +1439,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     if (t->particle_blocks_per_sm < 1 || t->particle_blocks_per_sm > 64 || t->walk_form < 0 ||
         t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
-        t->pcg_balance > 1 ||
+        t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 3 ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
@@ -1373,6 +1449,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->walk_form = t->walk_form;
     c->pcg_bps = t->pcg_blocks_per_sm;
     c->pcg_balance = t->pcg_balance;
+    c->cheb_local = t->pcg_cheb_local;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)

@@ -232,6 +232,10 @@ struct PcgArgs {
     unsigned *grp_bar;        // [n_groups] barrier counters, zero at launch
     int *grp_iters;           // [n_groups] iterations of each system's last solve (or null)
     int stream_matrix;        // general kernels: 1 stream the matrix past L2 (it does not fit)
+    int cheb_local;           // resident kernels: 1 block-local Chebyshev preconditioner,
+                              // 2 block-local + coarse correction over the blocks
+    const float *coarse_inv;  // [G*G] inverse of the blocks' coarse matrix (or null)
+    double *coarse_r;         // [G] the blocks' residual sums
     const double *rhs;        // null: f from W and the Neumann load; else f[row] = rhs[row]
     const double *fD;         // load of the prescribed Dirichlet values (rows)
 };

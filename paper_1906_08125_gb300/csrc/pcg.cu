@@ -68,11 +68,18 @@ __device__ __forceinline__ Grp grp_of(const PcgArgs &a)
 // counter is cleared before each launch).  Each block waits for the flip
 // with an iteration limit; a block that waits too long records
 // PIC_ERR_TIMEOUT and the whole kernel returns.
-__device__ bool grid_sync(const PcgArgs &a)
+__device__ bool grid_sync(const PcgArgs &a, const double *pre_part = nullptr, int n_part = 0,
+                          double *pre_dst = nullptr)
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (pre_part) {   // finish a block sum and publish it before arriving
+            double v = 0.0;
+            for (int i = 0; i < n_part; ++i)
+                v += pre_part[i];
+            *pre_dst = v;
+        }
         const Grp g = grp_of(a);
         int ok = 1;
         unsigned inc = g.rank == 0 ? 0x80000000u - (unsigned)(g.nb - 1) : 1u;
@@ -693,6 +700,16 @@ template <> __device__ __forceinline__ double cheb_coef<double>(double d, float)
 template <> __device__ __forceinline__ float cheb_coef<float>(double, float f) { return f; }
 
 template <int RPT, typename T>
+__device__ bool coarse_correction(const Rows<RPT> &t, const PcgArgs &a, const T (&dinv)[RPT],
+                                  const T (&r)[RPT], T (&z)[RPT]);
+template <int RPT, typename T>
+__device__ void coarse_publish(const Rows<RPT> &t, const PcgArgs &a, const T (&dinv)[RPT],
+                               const T (&r)[RPT]);
+__device__ bool coarse_sync(const PcgArgs &a);
+__device__ void coarse_apply(const PcgArgs &a);
+__device__ double *coarse_z0();
+
+template <int RPT, typename T>
 __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
                               const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT],
                               T (&z)[RPT], T *s_d0, T *s_d1, T *g_d0, T *g_d1)
@@ -701,8 +718,15 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
             z[k] = dinv[k] * r[k];
+        if (a.cheb_local >= 2 && a.coarse_inv)
+            return coarse_correction<RPT, T>(t, a, dinv, r, z);
         return true;
     }
+    // the whole-matrix polynomial with the coarse correction: the blocks'
+    // residual sums cross the polynomial's first grid barrier (no barrier of
+    // their own); the correction is added at the end
+    const bool fused_coarse = a.cheb_local == 3 && a.coarse_inv;
+    T z0 = (T)0;
     T rc[RPT], d[RPT];
     const T inv_theta = cheb_coef<T>(a.cheb_inv_theta, a.cheb_inv_thetaf);
 #pragma unroll
@@ -719,17 +743,38 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             break;
         T *s_d = (j & 1) ? s_d1 : s_d0;
         T *g_d = (j & 1) ? g_d1 : g_d0;
+        if (a.cheb_local == 1 || a.cheb_local == 2) {
+            // block-local form: the polynomial in the block's own diagonal block
+            // of D^-1 M (couplings to other blocks' rows dropped): still a fixed
+            // symmetric positive definite operator, and no grid barrier
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            if (!t.ok[k])
-                continue;
-            s_d[t.o[k]] = d[k];
-            g_d[t.row[k]] = d[k];
+            for (int k = 0; k < RPT; ++k)
+                if (t.ok[k])
+                    s_d[t.o[k]] = d[k];
+            for (int i = threadIdx.x; i < g.nh; i += blockDim.x)
+                s_d[g.nrows + i] = (T)0;
+            __syncthreads();
+        } else {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (!t.ok[k])
+                    continue;
+                s_d[t.o[k]] = d[k];
+                g_d[t.row[k]] = d[k];
+            }
+            if (fused_coarse && j == 1) {
+                coarse_publish<RPT, T>(t, a, dinv, r);
+                if (!coarse_sync(a))
+                    return false;
+                coarse_apply(a);   // overlaps the halo staging; read after the block barrier
+            } else if (!grid_sync(a)) {
+                return false;
+            }
+            stage_halo(s_d, (const T *)g_d, a, g);
+            __syncthreads();
+            if (fused_coarse && j == 1)
+                z0 = (T)*coarse_z0();
         }
-        if (!grid_sync(a))
-            return false;
-        stage_halo(s_d, (const T *)g_d, a, g);
-        __syncthreads();
         const T c1 = cheb_coef<T>(a.cheb_c1[j - 1], a.cheb_c1f[j - 1]);
         const T c2 = cheb_coef<T>(a.cheb_c2[j - 1], a.cheb_c2f[j - 1]);
 #pragma unroll
@@ -746,6 +791,88 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             d[k] = c1 * d[k] + c2 * (dinv[k] * rc[k]);
         }
     }
+    if (fused_coarse) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (t.ok[k] && dinv[k] != (T)0)
+                z[k] = z[k] + z0;
+        return true;
+    }
+    if (a.cheb_local == 2 && a.coarse_inv)
+        return coarse_correction<RPT, T>(t, a, dinv, r, z);
+    return true;
+}
+
+// Two-level form: z += R0^T A0^-1 R0 r with R0 summing the rows of each block
+// (one constant coarse vector per block, A0 = R0 M R0^T factored on the host).
+// The blocks' residual sums cross one grid barrier; each block then needs only
+// its own row of A0^-1.
+// The block's residual sum (R0 r)_b: each warp's share to coarse_part(); the
+// grid barrier's arriving thread adds them up and publishes the sum
+// (grid_sync with pre_part), so no block barrier of its own.
+__device__ __noinline__ double *coarse_part()
+{
+    __shared__ double part[RW];
+    return part;
+}
+__device__ __noinline__ double *coarse_z0()
+{
+    __shared__ double z0;
+    return &z0;
+}
+
+template <int RPT, typename T>
+__device__ void coarse_publish(const Rows<RPT> &t, const PcgArgs &a, const T (&dinv)[RPT],
+                               const T (&r)[RPT])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (t.ok[k] && dinv[k] != (T)0)
+            s += (double)r[k];
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0)
+        coarse_part()[w] = s;
+}
+
+__device__ __forceinline__ bool coarse_sync(const PcgArgs &a)
+{
+    return grid_sync(a, coarse_part(), RW, a.coarse_r + blockIdx.x);
+}
+
+// After the barrier: warp 0 forms (A0^-1 R0 r)_b in shared memory; it is
+// visible to the block after the next block barrier.
+__device__ void coarse_apply(const PcgArgs &a)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {
+        const float *row = a.coarse_inv + (size_t)blockIdx.x * gridDim.x;
+        double v = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32)
+            v += (double)row[c] * __ldcg(a.coarse_r + c);
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            *coarse_z0() = v;
+    }
+}
+
+template <int RPT, typename T>
+__device__ bool coarse_correction(const Rows<RPT> &t, const PcgArgs &a, const T (&dinv)[RPT],
+                                  const T (&r)[RPT], T (&z)[RPT])
+{
+    coarse_publish<RPT, T>(t, a, dinv, r);
+    if (!coarse_sync(a))
+        return false;
+    coarse_apply(a);
+    __syncthreads();
+    const T z0 = (T)*coarse_z0();
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (t.ok[k] && dinv[k] != (T)0)
+            z[k] = z[k] + z0;
     return true;
 }
 
