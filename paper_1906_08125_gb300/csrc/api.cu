@@ -90,6 +90,11 @@ struct pic_ctx_s {
     double cheb_b = 2.0;   // Gershgorin bound of D^-1 M
     const float *coarse_inv = nullptr;   // two-level preconditioner: A0^-1 of the blocks
     double *coarse_r = nullptr;
+    // general kernels' coarse correction: aggregates per group and their A0^-1
+    const int *agg_off = nullptr;
+    const long long *inv_off = nullptr;
+    const float *agg_inv = nullptr;
+    double *slice_r = nullptr, *agg_r = nullptr, *agg_z = nullptr;
     // replicas of a batch (1 for a single mesh)
     int n_rep = 1, n_rows = 0;
     int *tet_rep = nullptr, *face_rep = nullptr, *rep_face_off = nullptr;
@@ -461,6 +466,12 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.cheb_local = c->cheb_local;
     g.coarse_inv = c->coarse_inv;
     g.coarse_r = c->coarse_r;
+    g.agg_inv = c->cheb_local == 3 ? c->agg_inv : nullptr;
+    g.agg_off = c->agg_off;
+    g.inv_off = c->inv_off;
+    g.slice_r = c->slice_r;
+    g.agg_r = c->agg_r;
+    g.agg_z = c->agg_z;
     if (ov) {
         g.rhs = ov->rhs;
         g.x = ov->x;
@@ -576,6 +587,47 @@ extern "C" int pic_destroy(pic_ctx c)
 // ===========================================================================
 // mesh
 // ===========================================================================
+// Inverse of a symmetric positive definite n x n matrix (row-major, FP64) by
+// Cholesky A = L L^T and one forward/back substitution per column; false if
+// A is not positive definite.
+static bool spd_inverse(const std::vector<double> &A, int n, float *inv)
+{
+    std::vector<double> L(A);
+    for (int j = 0; j < n; ++j) {
+        double d = L[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k)
+            d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(d > 0.0))
+            return false;
+        d = std::sqrt(d);
+        L[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = L[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k)
+                v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = v / d;
+        }
+    }
+    std::vector<double> col((size_t)n);
+    for (int c0 = 0; c0 < n; ++c0) {
+        for (int i = 0; i < n; ++i) {
+            double v = i == c0 ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k)
+                v -= L[(size_t)i * n + k] * col[k];
+            col[i] = v / L[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double v = col[i];
+            for (int k = i + 1; k < n; ++k)
+                v -= L[(size_t)k * n + i] * col[k];
+            col[i] = v / L[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; ++i)
+            inv[(size_t)i * n + c0] = (float)col[i];
+    }
+    return true;
+}
+
 // scratch of the binary collisions: per-cell counts, offsets and fill
 // counters, the SPs grouped by cell and their order keys
 static int alloc_collision_scratch(pic_ctx c)
@@ -1267,49 +1319,62 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
                             A0[(size_t)bi * G + blk_of_slice[scol[e] / 32]] += v;
                     }
             }
-            std::vector<double> L(A0);   // Cholesky A0 = L L^T (lower triangle)
-            bool spd = true;
-            for (int j = 0; j < G && spd; ++j) {
-                double d = L[(size_t)j * G + j];
-                for (int k = 0; k < j; ++k)
-                    d -= L[(size_t)j * G + k] * L[(size_t)j * G + k];
-                if (!(d > 0.0)) {
-                    spd = false;
-                    break;
-                }
-                d = std::sqrt(d);
-                L[(size_t)j * G + j] = d;
-                for (int i = j + 1; i < G; ++i) {
-                    double v = L[(size_t)i * G + j];
-                    for (int k = 0; k < j; ++k)
-                        v -= L[(size_t)i * G + k] * L[(size_t)j * G + k];
-                    L[(size_t)i * G + j] = v / d;
-                }
-            }
-            if (spd) {
-                std::vector<float> inv((size_t)G * G);
-                std::vector<double> col((size_t)G);
-                for (int c0 = 0; c0 < G; ++c0) {   // solve L L^T x = e_c0
-                    for (int i = 0; i < G; ++i) {
-                        double v = i == c0 ? 1.0 : 0.0;
-                        for (int k = 0; k < i; ++k)
-                            v -= L[(size_t)i * G + k] * col[k];
-                        col[i] = v / L[(size_t)i * G + i];
-                    }
-                    for (int i = G - 1; i >= 0; --i) {
-                        double v = col[i];
-                        for (int k = i + 1; k < G; ++k)
-                            v -= L[(size_t)k * G + i] * col[k];
-                        col[i] = v / L[(size_t)i * G + i];
-                    }
-                    for (int i = 0; i < G; ++i)
-                        inv[(size_t)i * G + c0] = (float)col[i];
-                }
+            std::vector<float> inv((size_t)G * G);
+            if (spd_inverse(A0, G, inv.data())) {
                 float *ci = nullptr;
                 CK(dalloc(c, &ci, inv.size()));
                 CK(cudaMemcpy(ci, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice));
                 c->coarse_inv = ci;
                 CK(dalloc(c, &c->coarse_r, (size_t)G));
+            }
+        }
+        // general kernels (batches, large systems): aggregates of
+        // PCG_AGG_SLICES slices within each group, A0 of each group inverted
+        c->agg_inv = nullptr;
+        if (!c->plan.resident) {
+            const int NG = c->plan.n_groups > 0 ? c->plan.n_groups : 1;
+            auto g_s0 = [&](int g) { return c->plan.n_groups > 0 ? rep_slice[g] : 0; };
+            auto g_s1 = [&](int g) { return c->plan.n_groups > 0 ? rep_slice[g + 1] : n_slices; };
+            std::vector<int> agg_off((size_t)NG + 1, 0);
+            std::vector<long long> inv_off((size_t)NG + 1, 0);
+            for (int g = 0; g < NG; ++g) {
+                const int na = (g_s1(g) - g_s0(g) + PCG_AGG_SLICES - 1) / PCG_AGG_SLICES;
+                agg_off[g + 1] = agg_off[g] + na;
+                inv_off[g + 1] = inv_off[g] + (long long)na * na;
+            }
+            std::vector<float> inv((size_t)inv_off[NG]);
+            bool ok = true;
+            for (int g = 0; g < NG && ok; ++g) {
+                const int s0 = g_s0(g), na = agg_off[g + 1] - agg_off[g];
+                std::vector<double> A0((size_t)na * na, 0.0);
+                for (int sl = s0; sl < g_s1(g); ++sl) {
+                    const int w = (sptr[sl + 1] - sptr[sl]) / 32, ai = (sl - s0) / PCG_AGG_SLICES;
+                    for (int l = 0; l < 32; ++l)
+                        for (int k = 0; k < w; ++k) {
+                            const size_t e = (size_t)sptr[sl] + (size_t)k * 32 + l;
+                            if (hv[e] != 0.0)
+                                A0[(size_t)ai * na + (scol[e] / 32 - s0) / PCG_AGG_SLICES] += hv[e];
+                        }
+                }
+                ok = spd_inverse(A0, na, inv.data() + inv_off[g]);
+            }
+            if (ok) {
+                int *ao = nullptr;
+                long long *io = nullptr;
+                float *ai = nullptr;
+                CK(dalloc(c, &ao, agg_off.size()));
+                CK(dalloc(c, &io, inv_off.size()));
+                CK(dalloc(c, &ai, inv.size()));
+                CK(dalloc(c, &c->slice_r, (size_t)n_slices));
+                CK(dalloc(c, &c->agg_r, (size_t)agg_off[NG]));
+                CK(dalloc(c, &c->agg_z, (size_t)agg_off[NG]));
+                CK(cudaMemcpy(ao, agg_off.data(), sizeof(int) * agg_off.size(), cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(io, inv_off.data(), sizeof(long long) * inv_off.size(),
+                              cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(ai, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice));
+                c->agg_off = ao;
+                c->inv_off = io;
+                c->agg_inv = ai;
             }
         }
     }

@@ -98,6 +98,9 @@ struct RunConst {
 };
 
 // Device-side bookkeeping of one context.
+// slices per aggregate of the general solver's coarse correction
+constexpr int PCG_AGG_SLICES = 32;
+
 // Step bookkeeping kept on the device, so that a whole step can be captured
 // in a CUDA graph and replayed: the index of the step being run (key of the
 // random numbers and part of the SP ids) and the per-step statistics array of
@@ -236,6 +239,11 @@ struct PcgArgs {
                               // 2 block-local + coarse correction over the blocks
     const float *coarse_inv;  // [G*G] inverse of the blocks' coarse matrix (or null)
     double *coarse_r;         // [G] the blocks' residual sums
+    // general kernels' coarse correction (null agg_inv: none)
+    const int *agg_off;       // [groups + 1] first aggregate of each group
+    const long long *inv_off; // [groups] offset of each group's A0^-1 in agg_inv
+    const float *agg_inv;     // the groups' A0^-1, row-major
+    double *slice_r, *agg_r, *agg_z;   // [n_slices], [n_agg], [n_agg]
     const double *rhs;        // null: f from W and the Neumann load; else f[row] = rhs[row]
     const double *fD;         // load of the prescribed Dirichlet values (rows)
 };

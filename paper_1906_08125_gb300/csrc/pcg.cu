@@ -223,18 +223,49 @@ __device__ __forceinline__ void finish(const PcgArgs &a, int it, double relres, 
 // strided by the group's warps (the whole matrix when there are no groups).
 struct Span {
     int s0, s1, gw, nw;
+    int g;   // the group (0 without groups)
 };
 
 __device__ __forceinline__ Span row_span(const PcgArgs &a)
 {
     const int w = threadIdx.x >> 5;
     if (a.n_groups <= 0)
-        return Span{0, a.n_slices, (int)blockIdx.x * PCG_WARPS + w, (int)gridDim.x * PCG_WARPS};
+        return Span{0, a.n_slices, (int)blockIdx.x * PCG_WARPS + w, (int)gridDim.x * PCG_WARPS, 0};
     int g = a.blk_grp[blockIdx.x];
     const int *d = a.grp + 4 * g;
-    return Span{d[0], d[1], ((int)blockIdx.x - d[2]) * PCG_WARPS + w, d[3] * PCG_WARPS};
+    return Span{d[0], d[1], ((int)blockIdx.x - d[2]) * PCG_WARPS + w, d[3] * PCG_WARPS, g};
 }
 #define FOR_SLICES(sp, s) for (int s = (sp).s0 + (sp).gw; s < (sp).s1; s += (sp).nw)
+
+// Coarse correction of the general kernels: the group's slices in
+// aggregates of AGG_SLICES consecutive slices (R0 sums an aggregate's rows),
+// A0 = R0 M R0^T of the group inverted on the host.  Stage 1 (after the first
+// barrier): each aggregate's residual from its slices' sums, in slice order;
+// stage 2 (after the second): z0 = A0^-1 r0 for each aggregate; the slices add
+// z0 after the third.  Each aggregate is owned by one warp of the group.
+constexpr int AGG_SLICES = PCG_AGG_SLICES;
+
+__device__ void coarse_stage(const PcgArgs &a, const Span &sp, int lane, int stage)
+{
+    const int base = a.agg_off[sp.g];
+    const int n_agg = a.agg_off[sp.g + 1] - base;
+    for (int ag = sp.gw; ag < n_agg; ag += sp.nw) {
+        double v = 0.0;
+        if (stage == 1) {
+            const int s = sp.s0 + ag * AGG_SLICES + lane;
+            if (lane < AGG_SLICES && s < sp.s1)
+                v = __ldcg(a.slice_r + s);
+        } else {
+            const float *row = a.agg_inv + a.inv_off[sp.g] + (size_t)ag * n_agg;
+            for (int b = lane; b < n_agg; b += 32)
+                v += (double)row[b] * __ldcg(a.agg_r + base + b);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            (stage == 1 ? a.agg_r : a.agg_z)[base + ag] = v;
+    }
+}
 
 __device__ __forceinline__ void scatter_phi(const PcgArgs &a, const Span &sp, int lane)
 {
@@ -417,6 +448,10 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
         return true;
     }
     const int kdeg = a.cheb_degree;
+    // coarse correction over aggregates of AGG_SLICES slices of the group (see
+    // coarse_stage); its three steps ride on the polynomial's first three grid
+    // barriers, so it needs degree >= 4
+    const bool coarse = a.agg_inv != nullptr && kdeg >= 4;
     FOR_SLICES(sp, s)
     {
         int row = s * 32 + lane;
@@ -425,6 +460,13 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
         a.z32[row] = d;
         a.ap32[row] = rc;
         a.d32_1[row] = d;
+        if (coarse) {
+            double v = a.dinv32[row] != 0.f ? (double)rc : 0.0;
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                a.slice_r[s] = v;
+        }
     }
     for (int j = 1; j < kdeg; ++j) {
         const float *cur = (j & 1) ? a.d32_1 : a.d32_0;
@@ -432,6 +474,8 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
         const float c1 = a.cheb_c1f[j - 1], c2 = a.cheb_c2f[j - 1];
         if (!grid_sync(a))
             return false;
+        if (coarse && j <= 2)
+            coarse_stage(a, sp, lane, j);
         FOR_SLICES(sp, s)
         {
             int row = s * 32 + lane;
@@ -444,6 +488,15 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
             a.ap32[row] = rc;
             if (j + 1 < kdeg)
                 nxt[row] = d;
+        }
+    }
+    if (coarse) {   // after the third barrier every aggregate's correction is ready
+        const int base = a.agg_off[sp.g];
+        FOR_SLICES(sp, s)
+        {
+            int row = s * 32 + lane;
+            if (a.dinv32[row] != 0.f)
+                a.z32[row] = a.z32[row] + (float)__ldcg(a.agg_z + base + (s - sp.s0) / AGG_SLICES);
         }
     }
     return true;
