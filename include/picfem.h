@@ -228,6 +228,11 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           correction (the default when pcg_cheb_degree >= 2;
  *                           otherwise 0).  All are SPD; the stopping rule is
  *                           unchanged
+ *   sort_cells              pic_step: 1 (default) orders the surviving SPs by
+ *                           cell after every step (a counting sort; the
+ *                           neighbouring SPs' walks then share walk records in
+ *                           L1); 0 leaves them in the order the step appended
+ *                           them.  Nothing computed depends on the order
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -238,6 +243,7 @@ typedef struct {
     int32_t pcg_cheb_degree;
     int32_t pcg_balance;
     int32_t pcg_cheb_local;
+    int32_t sort_cells;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);

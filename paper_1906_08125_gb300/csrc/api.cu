@@ -31,13 +31,14 @@ enum KernelId {
     K_ADJ_ROWS,
     K_ADJ_SP,
     K_COLLIDE,
+    K_SORT,
     K_NUM
 };
 const char *const kKernelNames[K_NUM] = {"field",          "inject_count", "inject_scan",
                                          "inject_emit",    "push_relocate", "deposit",
                                          "step_fused",     "pcg",          "util",
                                          "compact",        "adj_field",    "adj_rows",
-                                         "adj_sp",         "collide"};
+                                         "adj_sp",         "collide",      "sort"};
 
 struct ProfRec {
     int kid;
@@ -112,6 +113,7 @@ struct pic_ctx_s {
     cudaStream_t cap_s = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     long long glaunch[2] = {0, 0};
+    int gnext[2] = {1, 0};   // buffer parity after a replay of each graph
     int graph_state = 0;
     // staging
     void *stage[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -120,7 +122,8 @@ struct pic_ctx_s {
     long long launches = 0;
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
-    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0;
+    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1;
+    int *scnt = nullptr, *soff = nullptr, *srank = nullptr, *sscan = nullptr;   // sort scratch
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
     int *nfptr = nullptr, *nfcon = nullptr;   // Neumann contributions per row
@@ -1186,6 +1189,10 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     CK(cudaMemsetAsync(c->fD, 0, sizeof(double) * n_pad, c->s));
     CK(cudaStreamSynchronize(c->s));
     c->dir_h.assign(dir, dir + N);
+    CK(dalloc(c, &c->scnt, (size_t)T));
+    CK(dalloc(c, &c->soff, (size_t)T + 1));
+    CK(dalloc(c, &c->srank, cap));
+    CK(dalloc(c, &c->sscan, 2 * (((size_t)T + 1023) / 1024) + 2));
     c->ccnt = c->coff = c->cfill = c->cperm = c->cscan = nullptr;
     c->ckey = nullptr;
     if (c->p.collisions) {
@@ -1494,6 +1501,7 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->pcg_cheb_degree = c->p.pcg_cheb_degree;
     t->pcg_balance = c->pcg_balance;
     t->pcg_cheb_local = c->cheb_local;
+    t->sort_cells = c->sort_cells;
     return PIC_OK;
 }
 
@@ -1505,6 +1513,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 3 ||
+        t->sort_cells < 0 || t->sort_cells > 1 ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
@@ -1515,6 +1524,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->pcg_bps = t->pcg_blocks_per_sm;
     c->pcg_balance = t->pcg_balance;
     c->cheb_local = t->pcg_cheb_local;
+    c->sort_cells = t->sort_cells;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)
@@ -1702,7 +1712,15 @@ template <typename R> static int step_once(pic_ctx c)
                                               c->qoff,
                                               parts<R>(c, c->a), parts<R>(c, 1 - c->a), c->a,
                                               c->st, c->W, ds));
-    c->a = 1 - c->a;
+    if (c->sort_cells) {
+        // survivors back into this buffer, ordered by cell
+        LAUNCH(K_SORT, launch_sort_by_cell<R>(c->s, c->pgrid, c->T, parts<R>(c, 1 - c->a),
+                                              parts<R>(c, c->a), &c->st->cnt[1 - c->a],
+                                              &c->st->cnt[c->a], c->scnt, c->soff, c->srank,
+                                              c->sscan));
+    } else {
+        c->a = 1 - c->a;
+    }
     if (c->p.collisions)
         LAUNCH(K_COLLIDE, launch_collide<R>(c->s, coll_args<R>(c)));
     int rc = run_pcg(c, ds, &c->st->cnt[c->a]);
@@ -1752,6 +1770,7 @@ static void capture_step(pic_ctx c)
     c->s = c->cap_s;
     const std::string err = c->err;
     int rc = step_direct(c);
+    const int a_after = c->a;
     cudaError_t e = cudaStreamEndCapture(c->cap_s, &g);
     c->s = user;
     const long long per_step = c->launches - launches;
@@ -1763,6 +1782,7 @@ static void capture_step(pic_ctx c)
         cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
         c->gexec[a] = x;
         c->glaunch[a] = per_step;
+        c->gnext[a] = a_after;
         c->graph_state = 1;
     } else {
         cudaGetLastError();
@@ -1782,7 +1802,7 @@ static int run_step(pic_ctx c)
         if (c->gexec[a]) {
             CK(cudaGraphLaunch(c->gexec[a], c->s));
             c->launches += c->glaunch[a];
-            c->a = 1 - a;
+            c->a = c->gnext[a];
             c->step = c->step + 1;
             return PIC_OK;
         }

@@ -158,4 +158,62 @@ template <typename R> cudaError_t launch_collide(cudaStream_t s, const CollArgs<
 template cudaError_t launch_collide<double>(cudaStream_t, const CollArgs<double> &);
 template cudaError_t launch_collide<float>(cudaStream_t, const CollArgs<float> &);
 
+// ---------------------------------------------------------------------------
+// SPs ordered by cell (a counting sort): neighbouring SPs then walk through
+// the same walk records, which the L1 keeps.  The order inside a cell is
+// whatever the atomics gave; nothing computed depends on the SPs' order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_sort_count(Particles<R> B, const unsigned long long *nB, int *cnt, int *rank)
+{
+    const long long n = (long long)*nB;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        rank[i] = atomicAdd(cnt + B.cell[i], 1);
+}
+
+template <typename R>
+__global__ void k_sort_move(Particles<R> B, Particles<R> A, const unsigned long long *nB,
+                            unsigned long long *nA, const int *off, const int *rank)
+{
+    const long long n = (long long)*nB;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *nA = (unsigned long long)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int t = B.cell[i];
+        const long long o = (long long)off[t] + rank[i];
+        A.x[o] = B.x[i];
+        A.y[o] = B.y[i];
+        A.z[o] = B.z[i];
+        A.vx[o] = B.vx[i];
+        A.vy[o] = B.vy[i];
+        A.vz[o] = B.vz[i];
+        A.cell[o] = t;
+        A.id[o] = B.id[i];
+    }
+}
+
+template <typename R>
+cudaError_t launch_sort_by_cell(cudaStream_t s, int grid, int T, Particles<R> B, Particles<R> A,
+                                const unsigned long long *nB, unsigned long long *nA, int *cnt,
+                                int *off, int *rank, int *scan)
+{
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)T, s);
+    if (e != cudaSuccess)
+        return e;
+    k_sort_count<R><<<grid, 256, 0, s>>>(B, nB, cnt, rank);
+    e = launch_exclusive_scan(s, T, cnt, off, scan);
+    if (e != cudaSuccess)
+        return e;
+    k_sort_move<R><<<grid, 256, 0, s>>>(B, A, nB, nA, off, rank);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sort_by_cell<double>(cudaStream_t, int, int, Particles<double>,
+                                                 Particles<double>, const unsigned long long *,
+                                                 unsigned long long *, int *, int *, int *, int *);
+template cudaError_t launch_sort_by_cell<float>(cudaStream_t, int, int, Particles<float>,
+                                                Particles<float>, const unsigned long long *,
+                                                unsigned long long *, int *, int *, int *, int *);
+
 }  // namespace pf

@@ -344,6 +344,12 @@ template <typename R> struct CollArgs {
     int grid;                        // blocks of the SP passes
 };
 template <typename R> cudaError_t launch_collide(cudaStream_t s, const CollArgs<R> &g);
+// B (count *nB) -> A ordered by cell, *nA = *nB; scratch cnt [T], off [T + 1],
+// rank [capacity], scan (scan scratch for T)
+template <typename R>
+cudaError_t launch_sort_by_cell(cudaStream_t s, int grid, int T, Particles<R> B, Particles<R> A,
+                                const unsigned long long *nB, unsigned long long *nA, int *cnt,
+                                int *off, int *rank, int *scan);
 // rows of a node vector (0 on padding rows)
 cudaError_t launch_gather_rows(cudaStream_t s, int n_rows, const int *dof_node,
                                const double *node_v, double *rows);

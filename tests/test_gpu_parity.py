@@ -324,6 +324,11 @@ def test_profile_and_launch_count(picfem, plate_small):
     ctx.profile(True)
     ctx.step(3)
     rep = ctx.profile_read()
-    assert ctx.launch_count() - n0 == 3 * 5
-    for k in ("inject_count", "inject_scan", "step_fused", "pcg", "field"):
+    assert ctx.launch_count() - n0 == 3 * 6
+    for k in ("inject_count", "inject_scan", "step_fused", "sort", "pcg", "field"):
         assert rep[k][0] == 3 and rep[k][1] > 0
+    ctx.profile(False)
+    ctx.set_tuning(sort_cells=0)
+    n1 = ctx.launch_count()
+    ctx.step(2)
+    assert ctx.launch_count() - n1 == 2 * 5
