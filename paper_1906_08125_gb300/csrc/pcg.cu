@@ -340,7 +340,7 @@ __device__ __forceinline__ ACC sell_row(const PcgArgs &a, const V *__restrict__ 
 }
 
 // FP64 Jacobi-PCG (the plain FP64 form)
-__global__ void __launch_bounds__(PCG_BLOCK) k_pcg64(PcgArgs a)
+__global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
 {
     const int lane = threadIdx.x & 31;
     const Span sp = row_span(a);
@@ -503,7 +503,7 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
 }
 
 // FP32 PCG inside FP64 iterative refinement (see the resident form below)
-__global__ void __launch_bounds__(PCG_BLOCK) k_pcg32ir(PcgArgs a)
+__global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
 {
     const int lane = threadIdx.x & 31;
     const Span sp = row_span(a);
