@@ -20,8 +20,9 @@
 // FP64 dot products; the outer loop recomputes the residual f - M x in FP64
 // and applies the correction in FP64 (iterative refinement).
 //
-// The grid barrier waits with an iteration limit: a block that waits too
-// long records PIC_ERR_TIMEOUT and the whole kernel returns.
+// The grid barrier (a release reduction and an acquire spin per block) waits
+// with an iteration limit: a block that waits too long records
+// PIC_ERR_TIMEOUT and the whole kernel returns.
 #include <algorithm>
 
 #include "common.cuh"
@@ -61,13 +62,37 @@ __device__ __forceinline__ Grp grp_of(const PcgArgs &a)
     return Grp{a.grp_bar + g, a.grp[4 * g + 3], (int)blockIdx.x - b0, b0};
 }
 
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barriers this block has passed in the current launch; thread 0 alone reads
+// and writes it, and grid_sync_init() clears it at the start of every kernel
+// that calls grid_sync().
+__device__ __noinline__ unsigned *bar_gen()
+{
+    __shared__ unsigned gen;
+    return &gen;
+}
+
+__device__ __forceinline__ void grid_sync_init()
+{
+    if (threadIdx.x == 0)
+        *bar_gen() = 0u;
+}
+
 // Barrier over the blocks of one group (all blocks are co-resident: the
-// launch is cooperative), one atomic per block: the group's first block adds
-// 2^31 - (nb - 1), every other block adds 1, so the counter's top bit flips
-// exactly when the last block arrives and the low bits return to zero (the
-// counter is cleared before each launch).  Each block waits for the flip
-// with an iteration limit; a block that waits too long records
-// PIC_ERR_TIMEOUT and the whole kernel returns.
+// launch is cooperative).  The group's counter is zero at launch and every
+// block adds 1 per barrier with a release reduction, so barrier number k
+// (counted from 1) is complete once the counter has reached k * nb; thread 0
+// spins on it with acquire loads and the block barrier hands the ordering to
+// the other threads.  Two dependent trips to L2 per barrier (the reduction
+// needs no reply), no fences.  The comparison is taken modulo 2^32, so the
+// counter may wrap.  The wait has an iteration limit: a block that waits too
+// long records PIC_ERR_TIMEOUT and the whole kernel returns; a block also
+// gives up when it sees that error recorded by another block (read once
+// before the wait, off the critical path, and every 1024 spins).
 __device__ bool grid_sync(const PcgArgs &a, const double *pre_part = nullptr, int n_part = 0,
                           double *pre_dst = nullptr)
 {
@@ -81,21 +106,22 @@ __device__ bool grid_sync(const PcgArgs &a, const double *pre_part = nullptr, in
             *pre_dst = v;
         }
         const Grp g = grp_of(a);
-        int ok = 1;
-        unsigned inc = g.rank == 0 ? 0x80000000u - (unsigned)(g.nb - 1) : 1u;
-        __threadfence();
-        unsigned old = atomicAdd(g.ctr, inc);
+        const int err0 = ld_volatile_i32(&a.st->err);
+        const unsigned gen = *bar_gen() + 1u;
+        *bar_gen() = gen;
+        const unsigned target = gen * (unsigned)g.nb;
+        red_release_add_u32(g.ctr, 1u);
+        int ok = err0 != PIC_ERR_TIMEOUT;
         long long spins = 0;
-        while (((old ^ ld_acquire_u32(g.ctr)) & 0x80000000u) == 0) {
-            if (++spins > SPIN_LIMIT) {
+        while ((int)(ld_acquire_u32(g.ctr) - target) < 0) {
+            ++spins;
+            if (spins > SPIN_LIMIT ||
+                ((spins & 1023) == 0 && ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)) {
                 atomicCAS(&a.st->err, 0, PIC_ERR_TIMEOUT);
                 ok = 0;
                 break;
             }
         }
-        __threadfence();
-        if (ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)
-            ok = 0;
         ok_s = ok;
     }
     __syncthreads();
@@ -342,6 +368,7 @@ __device__ __forceinline__ ACC sell_row(const PcgArgs &a, const V *__restrict__ 
 // FP64 Jacobi-PCG (the plain FP64 form)
 __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
 {
+    grid_sync_init();
     const int lane = threadIdx.x & 31;
     const Span sp = row_span(a);
     int set = 0;
@@ -505,6 +532,7 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
 // FP32 PCG inside FP64 iterative refinement (see the resident form below)
 __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
 {
+    grid_sync_init();
     const int lane = threadIdx.x & 31;
     const Span sp = row_span(a);
     int set = 0;
@@ -935,6 +963,7 @@ __device__ bool coarse_correction(const Rows<RPT> &t, const PcgArgs &a, const T 
 template <int RPT, bool SM>
 __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
 {
+    grid_sync_init();
     extern __shared__ __align__(16) unsigned char smem[];
     const Seg g = block_seg(a);
     double *s_val = (double *)smem;
@@ -1278,6 +1307,7 @@ __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const Pc
 template <int RPT, bool SM, bool PIPE>
 __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
 {
+    grid_sync_init();
     extern __shared__ __align__(16) unsigned char smem[];
     const Seg g = block_seg(a);
     float *s_val = (float *)smem;
