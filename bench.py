@@ -30,6 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PIC cycles/s"
 WORKLOAD = "tip_1m"
+# inner FP32 solver forms (PIC_PCG_*)
+PCG_VARIANTS = {"standard": 0, "pipelined": 1, "merged": 2}
 STAT_DTYPE = np.dtype([("injected", "<i8"), ("collected", "<i8"), ("absorbed", "<i8"),
                        ("wrapped", "<i8"), ("crossings", "<i8"), ("alive", "<i8"),
                        ("max_walk", "<i4"), ("pcg_iters", "<i4"), ("pcg_relres", "<f8"),
@@ -44,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--pcg-variant", default="standard", choices=list(PCG_VARIANTS),
+                    help="inner FP32 solver form of the main line")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -214,6 +218,8 @@ def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True
     if prec == K.PREC_FP64:
         # the plain FP64 form: FP64 throughout, Jacobi-PCG
         p = dict(p, pcg_rtol=1e-6, pcg_cheb_degree=0)
+    else:
+        p = dict(p, pcg_variant=PCG_VARIANTS[args.pcg_variant])
     target = K.WORKLOADS[args.workload]["target_sp"]
     stream = torch.cuda.current_stream()
     ctx = picfem.Context(p, stream=stream).mesh_load(mesh)
@@ -598,6 +604,7 @@ def main():
            "nnz": res["info"]["nnz"], "emitting_faces": res["info"]["n_faces"],
            "sp_in_flight_mean": int(st["alive"].mean()), "target_sp": int(res["n0"]),
            "dt_fs": 4.0, "precision": args.precision, "pcg_rtol": res["params"]["pcg_rtol"],
+           "pcg_variant": args.pcg_variant if args.precision == "fp32_ir" else "standard",
            "l2": "flushed before every timed step (256 MB write)", "parallelism":
            f"replicas x{world}"}
     extra = {"pushes_per_s": round(push_rate, 1),

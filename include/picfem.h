@@ -82,8 +82,8 @@ typedef struct {
     int32_t walk_max_steps;/* face crossings per SP per step -> PIC_ERR_WALK_LIMIT */
     int32_t quant_bits;    /* S: deposit weights in units of 2^-S, 1 <= S <= 40 */
     int32_t precision;     /* PIC_PREC_*                                        */
-    int32_t pcg_variant;   /* FP32_IR inner solver: PIC_PCG_STANDARD or
-                              PIC_PCG_PIPELINED                                 */
+    int32_t pcg_variant;   /* FP32_IR inner solver: PIC_PCG_STANDARD,
+                              PIC_PCG_PIPELINED or PIC_PCG_MERGED              */
     double ir_inner_rtol;  /* FP32_IR: the most the inner FP32 PCG is asked to
                               reduce its residual in one refinement (e.g. 1e-4);
                               it stops earlier once the FP64 target is met     */
@@ -105,6 +105,13 @@ typedef struct {
 /* inner solver of the FP32_IR Poisson solve */
 #define PIC_PCG_STANDARD 0   /* two grid reductions per iteration            */
 #define PIC_PCG_PIPELINED 1  /* one (Ghysels & Vanroose 2014), less accurate  */
+#define PIC_PCG_MERGED 2     /* the standard iteration with p.Ap summed on the
+                                Chebyshev polynomial's first grid barrier (its
+                                first step split by linearity into D^-1 r and
+                                D^-1 A p): degree k >= 2 over the whole matrix,
+                                k grid barriers per iteration instead of k + 1.
+                                Single systems on the resident solver only;
+                                otherwise the standard form runs            */
 
 typedef struct {
     int64_t injected;         /* SPs injected in the step                      */
@@ -233,6 +240,12 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           neighbouring SPs' walks then share walk records in
  *                           L1); 0 leaves them in the order the step appended
  *                           them.  Nothing computed depends on the order
+ *   pcg_halo_sync           one-system FP32 solver, whole-matrix Chebyshev
+ *                           steps: 1 (default) exchanges the step directions
+ *                           with the neighbouring blocks through tagged
+ *                           64-bit words (value | step tag), each block
+ *                           waiting only for the values it reads; 0 with a
+ *                           grid barrier per step.  Identical results
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -244,6 +257,7 @@ typedef struct {
     int32_t pcg_balance;
     int32_t pcg_cheb_local;
     int32_t sort_cells;
+    int32_t pcg_halo_sync;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);

@@ -88,6 +88,8 @@ struct pic_ctx_s {
           *dx32 = nullptr;
     double *d0 = nullptr, *d1 = nullptr;
     float *d32_0 = nullptr, *d32_1 = nullptr;
+    unsigned long long *dtag = nullptr;   // [2 * n_pad] tagged Chebyshev halo values
+    unsigned *pcg_epoch = nullptr;        // launches of the resident solver (mod 255)
     double cheb_b = 2.0;   // Gershgorin bound of D^-1 M
     const float *coarse_inv = nullptr;   // two-level preconditioner: A0^-1 of the blocks
     double *coarse_r = nullptr;
@@ -122,7 +124,8 @@ struct pic_ctx_s {
     long long launches = 0;
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
-    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1;
+    int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1,
+        halo_sync = 1;
     int *scnt = nullptr, *soff = nullptr, *srank = nullptr, *sscan = nullptr;   // sort scratch
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
@@ -455,6 +458,12 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.d1 = c->d1;
     g.d32_0 = c->d32_0;
     g.d32_1 = c->d32_1;
+    g.dtag[0] = g.dtag[1] = nullptr;
+    if (c->dtag && c->halo_sync == 1 && c->plan.resident && c->plan.halo_symmetric) {
+        g.dtag[0] = c->dtag;
+        g.dtag[1] = c->dtag + c->n_pad;
+    }
+    g.epoch = c->pcg_epoch;
     g.inner_max = c->p.ir_inner_max_iter;
     g.n_groups = c->plan.n_groups;
     g.grp = c->grp;
@@ -535,7 +544,7 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         (q.precision != PIC_PREC_FP64 && q.precision != PIC_PREC_FP32_IR) ||
         (q.fn_model != PIC_FN_MURPHY_GOOD && q.fn_model != PIC_FN_ELEMENTARY) ||
         (q.precision == PIC_PREC_FP32_IR && !(q.ir_inner_rtol > 0 && q.ir_inner_rtol < 1)) ||
-        (q.pcg_variant != PIC_PCG_STANDARD && q.pcg_variant != PIC_PCG_PIPELINED) ||
+        (q.pcg_variant < PIC_PCG_STANDARD || q.pcg_variant > PIC_PCG_MERGED) ||
         q.ir_inner_max_iter < 0 || q.pcg_cheb_degree < 0 || q.pcg_cheb_degree > 32 ||
         (q.pcg_cheb_degree >= 2 && !(q.pcg_cheb_ratio > 1.0)))
         return fail(nullptr, PIC_ERR_ARG, "pic_create: invalid parameters");
@@ -1113,6 +1122,8 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
     CK(dalloc(c, &c->d1, (size_t)n_pad));
     CK(dalloc(c, &c->d32_0, (size_t)n_pad));
     CK(dalloc(c, &c->d32_1, (size_t)n_pad));
+    CK(dalloc(c, &c->dtag, 2 * (size_t)n_pad));
+    CK(dalloc(c, &c->pcg_epoch, 1));
     PcgHalo halo;
     c->lcol = c->halo_ptr = c->halo_idx = nullptr;
     CK(pcg_plan(sptr.data(), scol.data(), n_slices, c->num_sms, c->p.precision, c->p.pcg_variant,
@@ -1232,6 +1243,9 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
         CK(cudaMemsetAsync(v, 0, sizeof(double) * n_pad, c->s));
     for (float *v : {c->r32, c->z32, c->p32_0, c->p32_1, c->ap32, c->dx32, c->d32_0, c->d32_1})
         CK(cudaMemsetAsync(v, 0, sizeof(float) * n_pad, c->s));
+    // all-ones tags: no epoch (< 255) produces them
+    CK(cudaMemsetAsync(c->dtag, 0xFF, sizeof(unsigned long long) * 2 * n_pad, c->s));
+    CK(cudaMemsetAsync(c->pcg_epoch, 0, sizeof(unsigned), c->s));
 
     // temporaries of the assembly
     std::vector<void *> tmp;
@@ -1332,7 +1346,7 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
                 CK(dalloc(c, &ci, inv.size()));
                 CK(cudaMemcpy(ci, inv.data(), sizeof(float) * inv.size(), cudaMemcpyHostToDevice));
                 c->coarse_inv = ci;
-                CK(dalloc(c, &c->coarse_r, (size_t)G));
+                CK(dalloc(c, &c->coarse_r, (size_t)2 * G));   // sums of r, of A p
             }
         }
         // general kernels (batches, large systems): aggregates of
@@ -1502,6 +1516,7 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->pcg_balance = c->pcg_balance;
     t->pcg_cheb_local = c->cheb_local;
     t->sort_cells = c->sort_cells;
+    t->pcg_halo_sync = c->halo_sync;
     return PIC_OK;
 }
 
@@ -1513,7 +1528,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 3 ||
-        t->sort_cells < 0 || t->sort_cells > 1 ||
+        t->sort_cells < 0 || t->sort_cells > 1 || t->pcg_halo_sync < 0 || t->pcg_halo_sync > 1 ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
@@ -1525,6 +1540,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->pcg_balance = t->pcg_balance;
     c->cheb_local = t->pcg_cheb_local;
     c->sort_cells = t->sort_cells;
+    c->halo_sync = t->pcg_halo_sync;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)

@@ -226,6 +226,13 @@ struct PcgArgs {
     float cheb_c1f[32], cheb_c2f[32], cheb_inv_thetaf;
     double *d0, *d1;          // FP64 halo buffers of the Chebyshev steps [n_pad]
     float *d32_0, *d32_1;     // FP32 halo buffers of the Chebyshev steps [n_pad]
+    // resident FP32 kernels: the Chebyshev steps' neighbour exchange without a
+    // grid barrier.  dtag[k][row] = value bits | tag << 32, written in one
+    // 64-bit store; readers poll until the tag is the one they expect.  Tags
+    // carry a per-launch epoch (*epoch, advanced once per launch, never
+    // saved or restored with the state).  null: grid barriers instead.
+    unsigned long long *dtag[2];
+    unsigned *epoch;
     // independent systems solved side by side (a batch of replicas): group g
     // owns slices [grp[4g], grp[4g+1]) and blocks [grp[4g+2], +grp[4g+3]);
     // n_groups == 0 means one system over the whole grid
@@ -238,7 +245,7 @@ struct PcgArgs {
     int cheb_local;           // resident kernels: 1 block-local Chebyshev preconditioner,
                               // 2 block-local + coarse correction over the blocks
     const float *coarse_inv;  // [G*G] inverse of the blocks' coarse matrix (or null)
-    double *coarse_r;         // [G] the blocks' residual sums
+    double *coarse_r;         // [2G] the blocks' sums of r (and of A p: merged form)
     // general kernels' coarse correction (null agg_inv: none)
     const int *agg_off;       // [groups + 1] first aggregate of each group
     const long long *inv_off; // [groups] offset of each group's A0^-1 in agg_inv
@@ -256,6 +263,7 @@ struct PcgLaunch {
     int max_rows;          // resident: 32 * most slices owned by one block
     long long max_chunk;   // resident: most stored matrix entries owned by one block
     int max_local;         // resident: most own rows + halo columns of one block
+    int halo_symmetric;    // resident: block b reads block o's rows iff o reads b's
     int n_groups;          // general: independent systems (0: one system, whole grid)
 };
 // Host-side tables: local column indices and halos of the resident kernels;

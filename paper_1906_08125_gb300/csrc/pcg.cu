@@ -93,17 +93,29 @@ __device__ __forceinline__ void grid_sync_init()
 // long records PIC_ERR_TIMEOUT and the whole kernel returns; a block also
 // gives up when it sees that error recorded by another block (read once
 // before the wait, off the critical path, and every 1024 spins).
-__device__ bool grid_sync(const PcgArgs &a, const double *pre_part = nullptr, int n_part = 0,
-                          double *pre_dst = nullptr)
+// A block sum that crosses a barrier on the way: thread 0 adds the n
+// per-warp partials part[] (shared memory, in warp order) and publishes the
+// sum to dst before arriving, so the sum needs no barrier of its own.
+struct Ride {
+    const double *part = nullptr;
+    int n = 0;
+    double *dst = nullptr;
+};
+
+__device__ bool grid_sync(const PcgArgs &a, Ride r1 = Ride(), Ride r2 = Ride(),
+                          Ride r3 = Ride())
 {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (pre_part) {   // finish a block sum and publish it before arriving
+        const Ride *rides[3] = {&r1, &r2, &r3};
+        for (int k = 0; k < 3; ++k) {
+            if (!rides[k]->part)
+                continue;
             double v = 0.0;
-            for (int i = 0; i < n_part; ++i)
-                v += pre_part[i];
-            *pre_dst = v;
+            for (int i = 0; i < rides[k]->n; ++i)
+                v += rides[k]->part[i];
+            *rides[k]->dst = v;
         }
         const Grp g = grp_of(a);
         const int err0 = ld_volatile_i32(&a.st->err);
@@ -207,6 +219,124 @@ template <int NV, int BLOCK = PCG_BLOCK>
 __device__ bool grid_sum(const double (&v)[NV], int set, const PcgArgs &a, double (&out)[NV])
 {
     return grid_sum_f<NV, NV, BLOCK>(v, set, a, out, NoFinish());
+}
+
+// Double-float accumulation: the unevaluated sum hi + lo of two floats
+// (about 48 significant bits).  A product enters exactly (the fused
+// multiply-add gives the rounding error of the float product) and a sum
+// through Knuth's two-sum, so the FP32 solver's dot products take no FP64
+// instruction per row: on this part the FP64 rate is a small fraction of the
+// FP32 rate, and the per-row FP64 products and conversions were a visible
+// share of an iteration.  The intrinsics keep the compiler from contracting
+// or reordering the error terms.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DF &s, float x)
+{
+    const float t = __fadd_rn(s.hi, x);
+    const float bp = __fsub_rn(t, s.hi);
+    const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, e);
+}
+
+__device__ __forceinline__ void df_add_prod(DF &s, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    df_add(s, p);
+    s.lo = __fadd_rn(s.lo, pe);
+}
+
+__device__ __forceinline__ void df_add_df(DF &s, const DF &o)
+{
+    df_add(s, o.hi);
+    s.lo = __fadd_rn(s.lo, o.lo);
+}
+
+__device__ __forceinline__ double df_value(const DF &s)
+{
+    return (double)s.hi + (double)s.lo;
+}
+
+// butterfly over the warp in double-float; the FP64 value of lane 0's sum
+__device__ __forceinline__ double df_warp_sum(DF x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF y;
+        y.hi = __shfl_xor_sync(FULL_MASK, x.hi, o);
+        y.lo = __shfl_xor_sync(FULL_MASK, x.lo, o);
+        df_add_df(x, y);
+    }
+    return df_value(x);
+}
+
+// The block reduction of grid_sum_f for double-float per-thread values: a
+// butterfly in every warp (FP32 instructions), the warp sums to FP64 in
+// shared memory, warp 0 adds them in warp order.  Then the same grid step.
+template <int NV, int NO, int BLOCK, typename F>
+__device__ bool grid_sum_df(const DF (&v)[NV], int set, const PcgArgs &a, double (&out)[NO],
+                            F fin)
+{
+    constexpr int NWB = BLOCK / 32;
+    static_assert(NV <= 3 && NO <= 4 && NWB <= 32, "reduction buffer size");
+    double *vals = reduction_buffer();
+    double *res = vals + 3 * 512;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double x = df_warp_sum(v[k]);
+        if (lane == 0)
+            vals[k * NWB + wid] = x;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < NWB ? vals[k * NWB + lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0)
+                a.partials[((size_t)set * gridDim.x + blockIdx.x) * 4 + k] = s;
+        }
+    }
+    if (!grid_sync(a))
+        return false;
+    if (wid == 0) {
+        const Grp g = grp_of(a);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int b = lane; b < g.nb; b += 32)
+                s += __ldcg(a.partials + ((size_t)set * gridDim.x + g.b0 + b) * 4 + k);
+            s = warp_sum(s);
+            if (lane == 0)
+                res[k] = s;
+        }
+        if (lane == 0)
+            fin(res);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NO; ++k)
+        out[k] = res[k];
+    return true;
+}
+
+// The FP32 inner solve of a refinement works on r / sc with sc the power of
+// two nearest below ||r||_2: whatever the scale of the system (adjoint right
+// sides included) its values and dot products stay far inside the FP32
+// range, and since power-of-two scaling is exact and every step of the inner
+// solve is homogeneous, the result is the unscaled one bit for bit wherever
+// that did not overflow or underflow.  0 when ||r|| is not finite.
+__device__ __forceinline__ double refinement_scale(double rr)
+{
+    const double nr = sqrt(rr);
+    if (!(nr > 0.0) || !(nr < 1.0e300))
+        return 0.0;
+    return scalbn(1.0, ilogb(nr));
 }
 
 // f_i = ((q w_sp / eps0) W_i 2^-S + f_Neumann,i) + f_D,i (eq. poisson_rhs plus
@@ -582,14 +712,20 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
         double itol = 0.5 * a.rtol * sqrt(ff / rr64);
         if (itol < a.inner_rtol)
             itol = a.inner_rtol;
-        // inner FP32 PCG on M d = r, d = 0
+        const double sc = refinement_scale(rr64), inv_sc = 1.0 / sc;
+        if (sc == 0.0) {
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
+        // inner FP32 PCG on M d = r / sc, d = 0
         FOR_SLICES(sp, s)
         {
             int row = s * 32 + lane;
-            a.r32[row] = (float)a.r[row];
+            a.r32[row] = (float)(a.r[row] * inv_sc);
             a.dx32[row] = 0.f;
             a.p32_0[row] = 0.f;
         }
+        const int it0 = it;
         if (!precond_global(a, sp, lane))
             return;
         double acc2[2] = {0.0, 0.0}, t2[2];
@@ -658,11 +794,15 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
             pold = pnew;
             pnew = tmp;
         }
+        if (it == it0) {   // no inner iteration: no progress possible
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
         // refinement update in FP64
         FOR_SLICES(sp, s)
         {
             int row = s * 32 + lane;
-            a.x[row] = a.x[row] + (double)a.dx32[row];
+            a.x[row] = a.x[row] + sc * (double)a.dx32[row];
         }
         if (!grid_sync(a))
             return;
@@ -726,16 +866,22 @@ __device__ __forceinline__ void stage_halo(V *s, const V *glob, const PcgArgs &a
         s[g.nrows + i] = __ldcg(glob + a.halo_idx[g.h0 + i]);
 }
 
-// per-thread row slots
+// per-thread row slots; pub and epoch make the tags of the neighbour
+// exchange (every thread of every block runs the same sequence of exchanges,
+// so its own count is the block's and the grid's)
 template <int RPT> struct Rows {
     int row[RPT], o[RPT], le[RPT], ge[RPT], wd[RPT];
     bool ok[RPT];
+    mutable unsigned pub;   // tagged exchanges so far in this launch
+    unsigned epoch;         // this launch's epoch, < 255
 };
 
 template <int RPT, bool SM>
 __device__ __forceinline__ void init_rows(Rows<RPT> &t, const PcgArgs &a, const Seg &g)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    t.pub = 0u;
+    t.epoch = a.epoch ? (unsigned)ld_volatile_i32((const int *)a.epoch) : 0u;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         int s = g.s0 + w + k * RW;
@@ -768,6 +914,73 @@ __device__ __forceinline__ ACC spmv_local(const Rows<RPT> &t, int k, const int *
     return sum;
 }
 
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Neighbour exchange of a Chebyshev step direction without a grid barrier.
+// The block writes its own values to its shared segment and, with the step's
+// tag, to the tagged buffer (one 64-bit store per row: value and tag arrive
+// together); then it reads each halo value from the owner's word until the
+// tag is the current one.  Two buffers alternate: when a block overwrites
+// its word of step n - 2 with step n, every block that reads it has already
+// published step n - 1, which it does only after it has read step n - 2 (the
+// halo relation of a symmetric matrix is symmetric; the host checks it).
+// Tags: epoch << 24 | step count; stale words hold another step count or
+// another epoch.  Each wait has an iteration limit and gives up when another
+// block has recorded PIC_ERR_TIMEOUT.
+template <int RPT>
+__device__ bool tagged_exchange(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, float *s_d,
+                                const float (&d)[RPT])
+{
+    const unsigned tag = (t.epoch << 24) | (t.pub & 0xFFFFFFu);
+    unsigned long long *buf = a.dtag[t.pub & 1u];
+    ++t.pub;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        s_d[t.o[k]] = d[k];
+        st_relaxed_u64(buf + t.row[k],
+                       (unsigned long long)__float_as_uint(d[k]) | ((unsigned long long)tag << 32));
+    }
+    int bad = 0;
+    for (int i = threadIdx.x; i < g.nh && !bad; i += blockDim.x) {
+        const unsigned long long *src = buf + a.halo_idx[g.h0 + i];
+        unsigned long long v = ld_relaxed_u64(src);
+        long long spins = 0;
+        while ((unsigned)(v >> 32) != tag) {
+            ++spins;
+            if (spins > SPIN_LIMIT ||
+                ((spins & 1023) == 0 && ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)) {
+                bad = 1;
+                break;
+            }
+            v = ld_relaxed_u64(src);
+        }
+        s_d[g.nrows + i] = __uint_as_float((unsigned)v);
+    }
+    if (bad)
+        atomicCAS(&a.st->err, 0, PIC_ERR_TIMEOUT);
+    return __syncthreads_or(bad) == 0;
+}
+
+template <int RPT, typename T>
+__device__ __forceinline__ bool tagged_exchange_t(const Rows<RPT> &t, const PcgArgs &a,
+                                                  const Seg &g, T *s_d, const T (&d)[RPT])
+{
+    if constexpr (sizeof(T) == 4)
+        return tagged_exchange<RPT>(t, a, g, s_d, d);
+    return false;
+}
+
 // z = M^-1 r for the preconditioner.  Jacobi: z = D^-1 r.  Chebyshev of
 // degree k: z = p_k(D^-1 M) D^-1 r, computed as k steps of the Chebyshev
 // iteration for M y = r from y = 0 on the interval [a, b] (Saad, Iterative
@@ -780,6 +993,30 @@ template <typename T> __device__ __forceinline__ T cheb_coef(double d, float f);
 template <> __device__ __forceinline__ double cheb_coef<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float cheb_coef<float>(double, float f) { return f; }
 
+// One Chebyshev step after the direction d_j has been staged in s_d (own
+// rows and halo): rc -= M d_j, d_{j+1} = c1 d_j + c2 D^-1 rc.
+template <int RPT, typename T>
+__device__ __forceinline__ void cheb_update(const Rows<RPT> &t, const PcgArgs &a, const int *LC,
+                                            const T *VAL, const T (&dinv)[RPT], const T *s_d,
+                                            int j, T (&rc)[RPT], T (&d)[RPT])
+{
+    const T c1 = cheb_coef<T>(a.cheb_c1[j - 1], a.cheb_c1f[j - 1]);
+    const T c2 = cheb_coef<T>(a.cheb_c2[j - 1], a.cheb_c2f[j - 1]);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        T ad = 0;
+#pragma unroll 4
+        for (int c = 0; c < t.wd[k]; ++c) {
+            int lc = LC[t.le[k] + c * 32];
+            ad += VAL[t.le[k] + c * 32] * s_d[lc];
+        }
+        rc[k] = rc[k] - ad;
+        d[k] = c1 * d[k] + c2 * (dinv[k] * rc[k]);
+    }
+}
+
 template <int RPT, typename T>
 __device__ bool coarse_correction(const Rows<RPT> &t, const PcgArgs &a, const T (&dinv)[RPT],
                                   const T (&r)[RPT], T (&z)[RPT]);
@@ -790,10 +1027,35 @@ __device__ bool coarse_sync(const PcgArgs &a);
 __device__ void coarse_apply(const PcgArgs &a);
 __device__ double *coarse_z0();
 
+// Per-warp partials of a sum that rides on the polynomial's first grid
+// barrier, and ([RW]) its grid total.
+__device__ __noinline__ double *ride_part()
+{
+    __shared__ double part[RW + 1];
+    return part;
+}
+
+// After the barrier: warp 1 adds the blocks' partials of the ride in block
+// order (the same order in every block) into ride_part()[RW].
+__device__ __forceinline__ void ride_gather(const PcgArgs &a, int set)
+{
+    if ((threadIdx.x >> 5) != 1)
+        return;
+    const int lane = threadIdx.x & 31;
+    const Grp g = grp_of(a);
+    double v = 0.0;
+    for (int b = lane; b < g.nb; b += 32)
+        v += __ldcg(a.partials + ((size_t)set * gridDim.x + g.b0 + b) * 4);
+    v = warp_sum(v);
+    if (lane == 0)
+        ride_part()[RW] = v;
+}
+
 template <int RPT, typename T>
 __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
                               const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT],
-                              T (&z)[RPT], T *s_d0, T *s_d1, T *g_d0, T *g_d1)
+                              T (&z)[RPT], T *s_d0, T *s_d1, T *g_d0, T *g_d1,
+                              bool have_z0 = false, double z0_given = 0.0)
 {
     if (a.cheb_degree < 2) {
 #pragma unroll
@@ -806,8 +1068,12 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
     // the whole-matrix polynomial with the coarse correction: the blocks'
     // residual sums cross the polynomial's first grid barrier (no barrier of
     // their own); the correction is added at the end
+    // have_z0: the caller already formed this block's coarse correction
+    // (A0^-1 R0 r)_b on an earlier barrier, so the polynomial's first step
+    // needs no grid barrier either
     const bool fused_coarse = a.cheb_local == 3 && a.coarse_inv;
-    T z0 = (T)0;
+    const bool coarse_j1 = fused_coarse && !have_z0;
+    T z0 = have_z0 ? (T)z0_given : (T)0;
     T rc[RPT], d[RPT];
     const T inv_theta = cheb_coef<T>(a.cheb_inv_theta, a.cheb_inv_thetaf);
 #pragma unroll
@@ -835,6 +1101,9 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             for (int i = threadIdx.x; i < g.nh; i += blockDim.x)
                 s_d[g.nrows + i] = (T)0;
             __syncthreads();
+        } else if (sizeof(T) == 4 && a.dtag[0] && !(coarse_j1 && j == 1)) {
+            if (!tagged_exchange_t<RPT, T>(t, a, g, s_d, d))
+                return false;
         } else {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
@@ -843,7 +1112,7 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
                 s_d[t.o[k]] = d[k];
                 g_d[t.row[k]] = d[k];
             }
-            if (fused_coarse && j == 1) {
+            if (coarse_j1 && j == 1) {
                 coarse_publish<RPT, T>(t, a, dinv, r);
                 if (!coarse_sync(a))
                     return false;
@@ -853,24 +1122,10 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
             }
             stage_halo(s_d, (const T *)g_d, a, g);
             __syncthreads();
-            if (fused_coarse && j == 1)
+            if (coarse_j1 && j == 1)
                 z0 = (T)*coarse_z0();
         }
-        const T c1 = cheb_coef<T>(a.cheb_c1[j - 1], a.cheb_c1f[j - 1]);
-        const T c2 = cheb_coef<T>(a.cheb_c2[j - 1], a.cheb_c2f[j - 1]);
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            if (!t.ok[k])
-                continue;
-            T ad = 0;
-#pragma unroll 4
-            for (int c = 0; c < t.wd[k]; ++c) {
-                int lc = LC[t.le[k] + c * 32];
-                ad += VAL[t.le[k] + c * 32] * s_d[lc];
-            }
-            rc[k] = rc[k] - ad;
-            d[k] = c1 * d[k] + c2 * (dinv[k] * rc[k]);
-        }
+        cheb_update<RPT, T>(t, a, LC, VAL, dinv, s_d, j, rc, d);
     }
     if (fused_coarse) {
 #pragma unroll
@@ -890,7 +1145,7 @@ __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g
 // its own row of A0^-1.
 // The block's residual sum (R0 r)_b: each warp's share to coarse_part(); the
 // grid barrier's arriving thread adds them up and publishes the sum
-// (grid_sync with pre_part), so no block barrier of its own.
+// (a Ride of grid_sync), so no block barrier of its own.
 __device__ __noinline__ double *coarse_part()
 {
     __shared__ double part[RW];
@@ -908,19 +1163,28 @@ __device__ void coarse_publish(const Rows<RPT> &t, const PcgArgs &a, const T (&d
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double s = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        DF x = {0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < RPT; ++k)
-        if (t.ok[k] && dinv[k] != (T)0)
-            s += (double)r[k];
-    for (int o = 16; o > 0; o >>= 1)
-        s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int k = 0; k < RPT; ++k)
+            if (t.ok[k] && dinv[k] != (T)0)
+                df_add(x, (float)r[k]);
+        s = df_warp_sum(x);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (t.ok[k] && dinv[k] != (T)0)
+                s += (double)r[k];
+        for (int o = 16; o > 0; o >>= 1)
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
     if (lane == 0)
         coarse_part()[w] = s;
 }
 
 __device__ __forceinline__ bool coarse_sync(const PcgArgs &a)
 {
-    return grid_sync(a, coarse_part(), RW, a.coarse_r + blockIdx.x);
+    return grid_sync(a, Ride{coarse_part(), RW, a.coarse_r + blockIdx.x});
 }
 
 // After the barrier: warp 0 forms (A0^-1 R0 r)_b in shared memory; it is
@@ -955,6 +1219,39 @@ __device__ bool coarse_correction(const Rows<RPT> &t, const PcgArgs &a, const T 
         if (t.ok[k] && dinv[k] != (T)0)
             z[k] = z[k] + z0;
     return true;
+}
+
+// The merged form's coarse sums: the blocks' sums of r (coarse_part(),
+// published to coarse_r[b]) and of A p (coarse_part2(), to coarse_r[G + b]);
+// after the barrier warp 0 forms both (A0^-1 R0 .)_b.
+__device__ __noinline__ double *coarse_part2()
+{
+    __shared__ double part[RW];
+    return part;
+}
+__device__ __noinline__ double *coarse_z0_pair()
+{
+    __shared__ double z0[2];
+    return z0;
+}
+__device__ void coarse_apply_pair(const PcgArgs &a)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {
+        const float *row = a.coarse_inv + (size_t)blockIdx.x * gridDim.x;
+        double v = 0.0, u = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32) {
+            const double ic = (double)row[c];
+            v += ic * __ldcg(a.coarse_r + c);
+            u += ic * __ldcg(a.coarse_r + gridDim.x + c);
+        }
+        v = warp_sum(v);
+        u = warp_sum(u);
+        if (lane == 0) {
+            coarse_z0_pair()[0] = v;
+            coarse_z0_pair()[1] = u;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1130,6 +1427,71 @@ template <int RPT> struct In32 {
     float dinv[RPT];
 };
 
+// The p.Ap reduction of the standard iteration carrying the coarse
+// correction of the preconditioner application that follows it: with
+// r' = r - alpha A p, R0 r' = R0 r - alpha R0 A p, so every block publishes
+// its sums of r and of A p (rows with a nonzero diagonal) beside its p.Ap
+// partial, and after the same barrier forms its rows of A0^-1 R0 r and
+// A0^-1 R0 A p (warp 1) while warp 0 totals p.Ap (resident solver, one
+// system).  out: [0] p.Ap, [1] alpha = rz / p.Ap, [2] (A0^-1 R0 r)_b,
+// [3] (A0^-1 R0 A p)_b.
+__device__ bool grid_sum_pap_coarse(const DF &pap, const DF &sr, const DF &sq, int set,
+                                    const PcgArgs &a, double rz, double (&out)[4])
+{
+    double *vals = reduction_buffer();
+    double *res = vals + 3 * 512;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const DF v[3] = {pap, sr, sq};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double x = df_warp_sum(v[k]);
+        if (lane == 0)
+            vals[k * RW + wid] = x;
+    }
+    __syncthreads();
+    const size_t G = gridDim.x;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double x = lane < RW ? vals[k * RW + lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0)
+                a.partials[((size_t)set * G + blockIdx.x) * 4 + k] = x;
+        }
+    }
+    if (!grid_sync(a))
+        return false;
+    if (wid == 0) {
+        double x = 0.0;
+        for (size_t b = lane; b < G; b += 32)
+            x += __ldcg(a.partials + ((size_t)set * G + b) * 4);
+        x = warp_sum(x);
+        if (lane == 0) {
+            res[0] = x;
+            res[1] = rz / x;
+        }
+    } else if (wid == 1) {
+        const float *row = a.coarse_inv + (size_t)blockIdx.x * G;
+        double v1 = 0.0, v2 = 0.0;
+        for (size_t c = lane; c < G; c += 32) {
+            const double ic = (double)row[c];
+            v1 += ic * __ldcg(a.partials + ((size_t)set * G + c) * 4 + 1);
+            v2 += ic * __ldcg(a.partials + ((size_t)set * G + c) * 4 + 2);
+        }
+        v1 = warp_sum(v1);
+        v2 = warp_sum(v2);
+        if (lane == 0) {
+            res[2] = v1;
+            res[3] = v2;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        out[k] = res[k];
+    return true;
+}
+
 template <int RPT>
 __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
                                const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_z,
@@ -1137,7 +1499,8 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
                                double itol, int &set, int &it)
 {
     float z[RPT], p[RPT], ap[RPT];
-    double acc[2] = {0.0, 0.0}, tot[2];
+    DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    double tot[2];
     if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1, a.d32_0,
                                    a.d32_1))
         return false;
@@ -1150,14 +1513,17 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         s_p0[t.o[k]] = 0.f;
         a.z32[t.row[k]] = z[k];
         a.p32_0[t.row[k]] = 0.f;
-        acc[0] += (double)rv[k] * (double)z[k];
-        acc[1] += (double)rv[k] * (double)rv[k];
+        df_add_prod(acc[0], rv[k], z[k]);
+        df_add_prod(acc[1], rv[k], rv[k]);
     }
-    if (!grid_sum<2, RB>(acc, set, a, tot))
+    if (!grid_sum_df<2, 2, RB>(acc, set, a, tot, NoFinish()))
         return false;
     set ^= 1;
     double rz = tot[0], rr = tot[1];
     const double itol2 = itol * itol * rr;
+    // the coarse correction of the whole-matrix polynomial rides on the
+    // p.Ap barrier (one grid barrier fewer per iteration)
+    const bool coarse_ride = a.cheb_local == 3 && a.coarse_inv && a.cheb_degree >= 2;
     double beta = 0.0;
     int cur = 0;
     for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
@@ -1171,7 +1537,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         stage_halo(sp_old, gp_old, a, g);
         __syncthreads();
         float b32 = (float)beta;
-        double pap[1] = {0.0};
+        DF pap[1] = {{0.f, 0.f}}, sr = {0.f, 0.f}, sq = {0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -1186,15 +1552,27 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             ap[k] = sum;
             sp_new[t.o[k]] = p[k];
             gp_new[t.row[k]] = p[k];
-            pap[0] += (double)p[k] * (double)sum;
+            df_add_prod(pap[0], p[k], sum);
+            if (coarse_ride && m.dinv[k] != 0.f) {
+                df_add(sr, rv[k]);
+                df_add(sq, sum);
+            }
         }
         double pt2[2];
-        if (!grid_sum_f<1, 2, RB>(pap, set, a, pt2,
-                                  [rz](double *q) { q[1] = rz / q[0]; }))
+        double z0 = 0.0;
+        if (coarse_ride) {
+            double o4[4];
+            if (!grid_sum_pap_coarse(pap[0], sr, sq, set, a, rz, o4))
+                return false;
+            pt2[1] = o4[1];
+            z0 = o4[2] - o4[1] * o4[3];
+        } else if (!grid_sum_df<1, 2, RB>(pap, set, a, pt2,
+                                          [rz](double *q) { q[1] = rz / q[0]; })) {
             return false;
+        }
         set ^= 1;
         float a32 = (float)pt2[1];
-        double acc2[2] = {0.0, 0.0};
+        DF acc2[2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
@@ -1203,7 +1581,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             rv[k] = rv[k] - a32 * ap[k];
         }
         if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1,
-                                       a.d32_0, a.d32_1))
+                                       a.d32_0, a.d32_1, coarse_ride, z0))
             return false;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -1211,12 +1589,194 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
                 continue;
             s_z[t.o[k]] = z[k];
             a.z32[t.row[k]] = z[k];
-            acc2[0] += (double)rv[k] * (double)z[k];
-            acc2[1] += (double)rv[k] * (double)rv[k];
+            df_add_prod(acc2[0], rv[k], z[k]);
+            df_add_prod(acc2[1], rv[k], rv[k]);
         }
         double t3[3];
-        if (!grid_sum_f<2, 3, RB>(acc2, set, a, t3,
+        if (!grid_sum_df<2, 3, RB>(acc2, set, a, t3,
                                   [rz](double *q) { q[2] = q[0] / rz; }))
+            return false;
+        set ^= 1;
+        beta = t3[2];
+        rz = t3[0];
+        rr = t3[1];
+        ++it;
+        cur ^= 1;
+    }
+    return true;
+}
+
+// The standard CG with one grid barrier fewer per iteration (a global
+// Chebyshev polynomial of degree k >= 2: k barriers instead of k + 1).  The
+// new preconditioned residual z' = M^-1 (r - alpha A p) is computed afresh
+// as in the standard form; only the polynomial's first step, which is local,
+// is split by linearity: each block publishes D^-1 r / theta and
+// D^-1 A p / theta (and, with the coarse correction, its sums of r and of
+// A p) before alpha is known, the block partials of p.Ap cross the same
+// barrier, and after it every block forms alpha and combines the staged
+// halves, d_1 = D^-1 r / theta - alpha D^-1 A p / theta, own rows and halo
+// alike.  The polynomial then continues from d_1 with its remaining
+// barriers.  Nothing is carried by recurrence beyond what the standard form
+// carries (r and p), so the rounding is that of the standard form.
+template <int RPT>
+__device__ bool inner_merged(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
+                             const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_z,
+                             float *s_p0, float *s_p1, float *s_d0, float *s_d1, double itol,
+                             int &set, int &it)
+{
+    float z[RPT], p[RPT], ap[RPT];
+    DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    double tot[2];
+    if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1, a.d32_0,
+                                   a.d32_1))
+        return false;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        p[k] = ap[k] = 0.f;
+        if (!t.ok[k])
+            continue;
+        s_z[t.o[k]] = z[k];
+        s_p0[t.o[k]] = 0.f;
+        a.z32[t.row[k]] = z[k];
+        a.p32_0[t.row[k]] = 0.f;
+        df_add_prod(acc[0], rv[k], z[k]);
+        df_add_prod(acc[1], rv[k], rv[k]);
+    }
+    if (!grid_sum_df<2, 2, RB>(acc, set, a, tot, NoFinish()))
+        return false;
+    set ^= 1;
+    double rz = tot[0], rr = tot[1];
+    const double itol2 = itol * itol * rr;
+    const bool coarse = a.cheb_local == 3 && a.coarse_inv;
+    const float inv_theta = a.cheb_inv_thetaf;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double beta = 0.0;
+    int cur = 0;
+    for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
+                    !(a.inner_max > 0 && i >= a.inner_max);
+         ++i) {
+        float *sp_old = cur ? s_p1 : s_p0;
+        float *sp_new = cur ? s_p0 : s_p1;
+        const float *gp_old = cur ? a.p32_1 : a.p32_0;
+        float *gp_new = cur ? a.p32_0 : a.p32_1;
+        stage_halo(s_z, (const float *)a.z32, a, g);
+        stage_halo(sp_old, gp_old, a, g);
+        __syncthreads();
+        const float b32 = (float)beta;
+        DF pap = {0.f, 0.f}, sr = {0.f, 0.f}, sq = {0.f, 0.f};
+        float dr[RPT], dq[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            dr[k] = dq[k] = 0.f;
+            if (!t.ok[k])
+                continue;
+            float sum = 0.f;
+#pragma unroll 4
+            for (int c = 0; c < t.wd[k]; ++c) {
+                int lc = m.LC[t.le[k] + c * 32];
+                sum += m.VAL[t.le[k] + c * 32] * (s_z[lc] + b32 * sp_old[lc]);
+            }
+            p[k] = z[k] + b32 * p[k];
+            ap[k] = sum;
+            sp_new[t.o[k]] = p[k];
+            gp_new[t.row[k]] = p[k];
+            df_add_prod(pap, p[k], sum);
+            // the first polynomial step of r and of A p, side by side
+            dr[k] = m.dinv[k] * rv[k] * inv_theta;
+            dq[k] = m.dinv[k] * sum * inv_theta;
+            a.d32_1[t.row[k]] = dr[k];
+            a.ap32[t.row[k]] = dq[k];
+            if (m.dinv[k] != 0.f) {
+                df_add(sr, rv[k]);
+                df_add(sq, sum);
+            }
+        }
+        const double pap_w = df_warp_sum(pap);
+        if (lane == 0)
+            ride_part()[wid] = pap_w;
+        Ride c_r, c_q;
+        if (coarse) {
+            const double sr_w = df_warp_sum(sr), sq_w = df_warp_sum(sq);
+            if (lane == 0) {
+                coarse_part()[wid] = sr_w;
+                coarse_part2()[wid] = sq_w;
+            }
+            c_r = Ride{coarse_part(), RW, a.coarse_r + blockIdx.x};
+            c_q = Ride{coarse_part2(), RW, a.coarse_r + gridDim.x + blockIdx.x};
+        }
+        if (!grid_sync(a, Ride{ride_part(), RW,
+                               a.partials + ((size_t)set * gridDim.x + blockIdx.x) * 4},
+                       c_r, c_q))
+            return false;
+        ride_gather(a, set);            // warp 1: p.Ap
+        if (coarse)
+            coarse_apply_pair(a);       // warp 0
+        set ^= 1;
+        stage_halo(s_d1, (const float *)a.d32_1, a, g);
+        stage_halo(s_d0, (const float *)a.ap32, a, g);
+        __syncthreads();
+        const double alpha = rz / ride_part()[RW];
+        const float a32 = (float)alpha;
+        for (int h = threadIdx.x; h < g.nh; h += blockDim.x)
+            s_d1[g.nrows + h] = s_d1[g.nrows + h] - a32 * s_d0[g.nrows + h];
+        float rc[RPT], dc[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            rc[k] = dc[k] = z[k] = 0.f;
+            if (!t.ok[k])
+                continue;
+            d[k] = d[k] + a32 * p[k];
+            rv[k] = rv[k] - a32 * ap[k];
+            rc[k] = rv[k];
+            dc[k] = dr[k] - a32 * dq[k];
+            s_d1[t.o[k]] = dc[k];
+            z[k] = dc[k];
+        }
+        __syncthreads();
+        for (int j = 1; j < a.cheb_degree; ++j) {
+            float *s_dj = (j & 1) ? s_d1 : s_d0;
+            float *g_dj = (j & 1) ? a.d32_1 : a.d32_0;
+            if (j > 1 && a.dtag[0]) {
+                if (!tagged_exchange<RPT>(t, a, g, s_dj, dc))
+                    return false;
+            } else if (j > 1) {
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    if (!t.ok[k])
+                        continue;
+                    s_dj[t.o[k]] = dc[k];
+                    g_dj[t.row[k]] = dc[k];
+                }
+                if (!grid_sync(a))
+                    return false;
+                stage_halo(s_dj, (const float *)g_dj, a, g);
+                __syncthreads();
+            }
+            cheb_update<RPT, float>(t, a, m.LC, m.VAL, m.dinv, s_dj, j, rc, dc);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                z[k] = z[k] + dc[k];
+        }
+        if (coarse) {
+            const float z0 = (float)(coarse_z0_pair()[0] - alpha * coarse_z0_pair()[1]);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (t.ok[k] && m.dinv[k] != 0.f)
+                    z[k] = z[k] + z0;
+        }
+        DF acc2[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            s_z[t.o[k]] = z[k];
+            a.z32[t.row[k]] = z[k];
+            df_add_prod(acc2[0], rv[k], z[k]);
+            df_add_prod(acc2[1], rv[k], rv[k]);
+        }
+        double t3[3];
+        if (!grid_sum_df<2, 3, RB>(acc2, set, a, t3,
+                                  [rz](double *q3) { q3[2] = q3[0] / rz; }))
             return false;
         set ^= 1;
         beta = t3[2];
@@ -1305,9 +1865,8 @@ __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const Pc
 }
 
 template <int RPT, bool SM, bool PIPE>
-__global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
+__device__ __forceinline__ void pcg32ir_res(const PcgArgs &a)
 {
-    grid_sync_init();
     extern __shared__ __align__(16) unsigned char smem[];
     const Seg g = block_seg(a);
     float *s_val = (float *)smem;
@@ -1344,6 +1903,9 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
     }
     int set = 0, it = 0, outer = 0, status = 0;
     double ff = -1.0, rr64 = 0.0;
+    // the merged form needs a grid barrier inside the preconditioner
+    const bool merged = a.variant == PIC_PCG_MERGED && a.cheb_degree >= 2 &&
+                        (a.cheb_local == 0 || a.cheb_local == 3);
     for (;;) {
         // FP64 residual r = f - M x (own x in s_x; halo of x staged)
         stage_halo(s_x, (const double *)a.x, a, g);
@@ -1378,10 +1940,15 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
             status = PIC_ERR_NOT_CONVERGED;
             break;
         }
+        const double sc = refinement_scale(rr64), inv_sc = 1.0 / sc;
+        if (sc == 0.0) {
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
         float rv[RPT], d[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            rv[k] = (float)r64[k];
+            rv[k] = (float)(r64[k] * inv_sc);
             d[k] = 0.f;
         }
         // ask the FP32 solve for what the FP64 target still needs (with a
@@ -1389,16 +1956,23 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
         double itol = 0.5 * a.rtol * sqrt(ff) / sqrt(rr64);
         if (itol < a.inner_rtol)
             itol = a.inner_rtol;
-        bool good = PIPE ? inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it)
-                         : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
-                                               itol, set, it);
+        const int it0 = it;
+        bool good = PIPE     ? inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it)
+                    : merged ? inner_merged<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
+                                                 itol, set, it)
+                             : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
+                                                   itol, set, it);
         if (!good)
             return;
+        if (it == it0) {   // no inner iteration: no progress possible
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
                 continue;
-            x[k] = x[k] + (double)d[k];
+            x[k] = x[k] + sc * (double)d[k];
             s_x[t.o[k]] = x[k];
             a.x[t.row[k]] = x[k];
         }
@@ -1416,6 +1990,17 @@ __global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
             a.phi[node] = x[k];
     }
     finish(a, it, sqrt(rr64) / sqrt(ff), status, outer);
+}
+
+template <int RPT, bool SM, bool PIPE>
+__global__ void __launch_bounds__(RB, 1) k_pcg32ir_res(PcgArgs a)
+{
+    grid_sync_init();
+    pcg32ir_res<RPT, SM, PIPE>(a);
+    // the next launch's tags take a new epoch, whichever way this one ended
+    // (every block has read the epoch before its first grid barrier)
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.epoch)
+        atomicInc(a.epoch, 254u);   // 0, 1, ..., 254, 0, ...: consecutive epochs differ
 }
 
 template <int RPT, bool SM> const void *res_kernel(int precision, int variant)
@@ -1440,8 +2025,19 @@ constexpr size_t SMEM_LIMIT = 200 * 1024;   // + static reduction buffers
 
 // Row ownership, local column indices and halos of the resident kernels.
 static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G, PcgHalo *h,
-                       int *max_local, long long *max_chunk)
+                       int *max_local, long long *max_chunk, int *symmetric)
 {
+    // reads[b * G + o]: block b reads rows of block o
+    std::vector<char> reads((size_t)G * G, 0);
+    auto owner = [&](int j) {
+        const long long sl = j / 32;
+        long long b = (sl * G) / n_slices;   // first guess, then adjust to the split
+        while (b > 0 && (b * n_slices) / G > sl)
+            --b;
+        while (b + 1 < G && ((b + 1) * n_slices) / G <= sl)
+            ++b;
+        return (int)b;
+    };
     h->lcol.assign((size_t)slice_ptr[n_slices], 0);
     h->halo_ptr.assign((size_t)G + 1, 0);
     h->halo_idx.clear();
@@ -1466,11 +2062,20 @@ static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G
                              ? j - row0
                              : nrows + (int)(std::lower_bound(ext.begin(), ext.end(), j) - ext.begin());
         }
+        for (int j : ext)
+            reads[(size_t)b * G + owner(j)] = 1;
         h->halo_idx.insert(h->halo_idx.end(), ext.begin(), ext.end());
         h->halo_ptr[b + 1] = (int)h->halo_idx.size();
         *max_local = std::max(*max_local, nrows + (int)ext.size());
         *max_chunk = std::max(*max_chunk, (long long)(e1 - e0));
     }
+    *symmetric = 1;
+    for (int b = 0; b < G && *symmetric; ++b)
+        for (int o = 0; o < G; ++o)
+            if (reads[(size_t)b * G + o] != reads[(size_t)o * G + b]) {
+                *symmetric = 0;
+                break;
+            }
 }
 
 int pcg_max_group_blocks(int precision, int num_sms)
@@ -1553,7 +2158,8 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
     if (rpt) {
         int max_local = 0;
         long long chunk = 0;
-        build_halo(slice_ptr, col, n_slices, G, halo, &max_local, &chunk);
+        int symmetric = 0;
+        build_halo(slice_ptr, col, n_slices, G, halo, &max_local, &chunk, &symmetric);
         bool fp64 = precision == PIC_PREC_FP64;
         size_t vec = fp64 ? (size_t)max_local * 8 * 5 : (size_t)max_local * (8 + 4 * 5);
         size_t mat = (size_t)chunk * (fp64 ? 12 : 8);
@@ -1579,6 +2185,7 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
                 plan->max_rows = 32 * max_sl;
                 plan->max_chunk = chunk;
                 plan->max_local = max_local;
+                plan->halo_symmetric = symmetric;
                 return cudaSuccess;
             }
         }
