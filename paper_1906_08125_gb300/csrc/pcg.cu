@@ -1510,9 +1510,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         if (!t.ok[k])
             continue;
         s_z[t.o[k]] = z[k];
-        s_p0[t.o[k]] = 0.f;
         a.z32[t.row[k]] = z[k];
-        a.p32_0[t.row[k]] = 0.f;
         df_add_prod(acc[0], rv[k], z[k]);
         df_add_prod(acc[1], rv[k], rv[k]);
     }
@@ -1524,17 +1522,15 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
     // the coarse correction of the whole-matrix polynomial rides on the
     // p.Ap barrier (one grid barrier fewer per iteration)
     const bool coarse_ride = a.cheb_local == 3 && a.coarse_inv && a.cheb_degree >= 2;
+    // p is needed on the block's own rows only: A p = A z + beta A p_old
+    // takes the product of z alone (its halo was published before the r.z
+    // barrier), and p itself is never exchanged.  The rounding of the
+    // recurrence is damped by beta < 1 from one iteration to the next.
     double beta = 0.0;
-    int cur = 0;
     for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
                     !(a.inner_max > 0 && i >= a.inner_max);
          ++i) {
-        float *sp_old = cur ? s_p1 : s_p0;
-        float *sp_new = cur ? s_p0 : s_p1;
-        const float *gp_old = cur ? a.p32_1 : a.p32_0;
-        float *gp_new = cur ? a.p32_0 : a.p32_1;
         stage_halo(s_z, (const float *)a.z32, a, g);
-        stage_halo(sp_old, gp_old, a, g);
         __syncthreads();
         float b32 = (float)beta;
         DF pap[1] = {{0.f, 0.f}}, sr = {0.f, 0.f}, sq = {0.f, 0.f};
@@ -1542,20 +1538,18 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         for (int k = 0; k < RPT; ++k) {
             if (!t.ok[k])
                 continue;
-            float sum = 0.f;
+            float az = 0.f;
 #pragma unroll 4
             for (int c = 0; c < t.wd[k]; ++c) {
                 int lc = m.LC[t.le[k] + c * 32];
-                sum += m.VAL[t.le[k] + c * 32] * (s_z[lc] + b32 * sp_old[lc]);
+                az += m.VAL[t.le[k] + c * 32] * s_z[lc];
             }
             p[k] = z[k] + b32 * p[k];
-            ap[k] = sum;
-            sp_new[t.o[k]] = p[k];
-            gp_new[t.row[k]] = p[k];
-            df_add_prod(pap[0], p[k], sum);
+            ap[k] = az + b32 * ap[k];
+            df_add_prod(pap[0], p[k], ap[k]);
             if (coarse_ride && m.dinv[k] != 0.f) {
                 df_add(sr, rv[k]);
-                df_add(sq, sum);
+                df_add(sq, ap[k]);
             }
         }
         double pt2[2];
@@ -1601,7 +1595,6 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
         rz = t3[0];
         rr = t3[1];
         ++it;
-        cur ^= 1;
     }
     return true;
 }
