@@ -728,71 +728,75 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
         const int it0 = it;
         if (!precond_global(a, sp, lane))
             return;
-        double acc2[2] = {0.0, 0.0}, t2[2];
+        DF acc2[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        double t2[2];
         FOR_SLICES(sp, s)
         {
             int row = s * 32 + lane;
             float r = a.r32[row], z = a.z32[row];
-            acc2[0] += (double)r * (double)z;
-            acc2[1] += (double)r * (double)r;
+            df_add_prod(acc2[0], r, z);
+            df_add_prod(acc2[1], r, r);
+            a.p32_1[row] = 0.f;
         }
-        if (!grid_sum<2>(acc2, set, a, t2))
+        if (!grid_sum_df<2, 2, PCG_BLOCK>(acc2, set, a, t2, NoFinish()))
             return;
         set ^= 1;
         double rz = t2[0], rr = t2[1];
         const double itol2 = itol * itol * rr;
+        // p and A p on own rows only: A p = A z + beta A p_old (the product
+        // of z alone; p is never gathered).  A p lives in p32_1 (ap32 is the
+        // preconditioner's scratch)
         double beta = 0.0;
-        float *pold = a.p32_0, *pnew = a.p32_1;
+        float *pv = a.p32_0, *apv = a.p32_1;
         for (int i = 0; rr > itol2 && rr > 0.0 && it < a.max_iter &&
                         !(a.inner_max > 0 && i >= a.inner_max);
              ++i) {
             float b32 = (float)beta;
-            double pap[1] = {0.0}, pt2[2];
+            DF pap[1] = {{0.f, 0.f}};
+            double pt2[2];
             FOR_SLICES(sp, s)
             {
                 int row = s * 32 + lane;
                 int b = a.slice_ptr[s], width = (a.slice_ptr[s + 1] - b) >> 5;
-                const float *zv = a.z32, *pv = pold;
-                float ap = sell_row<float>(a, a.val32, b, width, lane, [zv, pv, b32](int j) {
-                    return __ldcg(zv + j) + b32 * __ldcg(pv + j);
-                });
-                float p = a.z32[row] + b32 * pold[row];
-                pnew[row] = p;
-                a.ap32[row] = ap;
-                pap[0] += (double)p * (double)ap;
+                const float *zv = a.z32;
+                float az = sell_row<float>(a, a.val32, b, width, lane,
+                                           [zv](int j) { return __ldcg(zv + j); });
+                float p = a.z32[row] + b32 * pv[row];
+                float ap = az + b32 * apv[row];
+                pv[row] = p;
+                apv[row] = ap;
+                df_add_prod(pap[0], p, ap);
             }
-            if (!grid_sum_f<1, 2, PCG_BLOCK>(pap, set, a, pt2,
-                                             [rz](double *q) { q[1] = rz / q[0]; }))
+            if (!grid_sum_df<1, 2, PCG_BLOCK>(pap, set, a, pt2,
+                                              [rz](double *q) { q[1] = rz / q[0]; }))
                 return;
             set ^= 1;
             float alpha = (float)pt2[1];
             FOR_SLICES(sp, s)
             {
                 int row = s * 32 + lane;
-                a.dx32[row] = a.dx32[row] + alpha * pnew[row];
-                a.r32[row] = a.r32[row] - alpha * a.ap32[row];
+                a.dx32[row] = a.dx32[row] + alpha * pv[row];
+                a.r32[row] = a.r32[row] - alpha * apv[row];
             }
             if (!precond_global(a, sp, lane))
                 return;
-            double acc3[2] = {0.0, 0.0}, t3[3];
+            DF acc3[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            double t3[3];
             FOR_SLICES(sp, s)
             {
                 int row = s * 32 + lane;
                 float r = a.r32[row], z = a.z32[row];
-                acc3[0] += (double)r * (double)z;
-                acc3[1] += (double)r * (double)r;
+                df_add_prod(acc3[0], r, z);
+                df_add_prod(acc3[1], r, r);
             }
-            if (!grid_sum_f<2, 3, PCG_BLOCK>(acc3, set, a, t3,
-                                             [rz](double *q) { q[2] = q[0] / rz; }))
+            if (!grid_sum_df<2, 3, PCG_BLOCK>(acc3, set, a, t3,
+                                              [rz](double *q) { q[2] = q[0] / rz; }))
                 return;
             set ^= 1;
             beta = t3[2];
             rz = t3[0];
             rr = t3[1];
             ++it;
-            float *tmp = pold;
-            pold = pnew;
-            pnew = tmp;
         }
         if (it == it0) {   // no inner iteration: no progress possible
             status = PIC_ERR_NOT_CONVERGED;
