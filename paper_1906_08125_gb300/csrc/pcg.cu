@@ -1,28 +1,33 @@
 // pcg.cu -- the space-charge Poisson solve M Phi = f (App. B, eq. poisson_mat)
-// as one persistent cooperative kernel per solve: Jacobi-preconditioned
-// conjugate gradients, warm-started from the previous potential.
+// as one persistent cooperative kernel per solve: preconditioned conjugate
+// gradients (Jacobi, or a Chebyshev polynomial in D^-1 M with a two-level
+// coarse correction), warm-started from the previous potential.
 //
 // The matrix is stored as sliced ELLPACK with slices of 32 rows (one warp
 // per slice, one thread per row, columns of a slice interleaved so each load
 // of the warp is coalesced).  Each warp owns the same slices in every phase,
-// so a thread only ever reads its own rows' x, r, z, p; neighbours' z and p
-// are gathered after a grid barrier through L2 (ld.global.cg).
+// so a thread only ever reads its own rows' x, r, z, p; neighbours' values
+// are gathered through L2.
 //
-// One CG iteration needs two grid-wide reductions.  The search direction is
-// not materialised in a separate phase: the SpMV forms p = z + beta p_old on
-// the fly from the gathered z and p_old (double-buffered p), so two grid
-// barriers per iteration suffice.  Dot products: butterfly within the warp,
-// in warp order within the block, then every block sums the per-block
-// partials in block order -- a fixed order, so all blocks obtain identical
-// scalars and the result is reproducible run to run.
+// Two kernel families.  The resident kernels (one system that fits: one
+// block per SM, the block's rows in registers, its matrix slices and vector
+// segments in shared memory) exchange halo values either after a grid
+// barrier or, for the Chebyshev steps of the FP32 solve, through tagged
+// words that each block polls for the values it reads; the general kernels
+// (batches of systems, systems too large for the resident blocks) keep the
+// vectors in global memory and synchronise per group of blocks.
+//
+// A standard CG iteration takes two grid-wide reductions (p.Ap and r.z).
+// Reductions: within the warp, in warp order within the block, then every
+// block sums the per-block partials in block order -- a fixed order, so all
+// blocks obtain identical scalars and the result is reproducible run to run.
 //
 // FP32_IR: the inner CG runs in FP32 (matrix values, vectors, SpMV) with
-// FP64 dot products; the outer loop recomputes the residual f - M x in FP64
-// and applies the correction in FP64 (iterative refinement).
+// double-float dot products; the outer loop recomputes the residual f - M x
+// in FP64 and applies the correction in FP64 (iterative refinement).
 //
-// The grid barrier (a release reduction and an acquire spin per block) waits
-// with an iteration limit: a block that waits too long records
-// PIC_ERR_TIMEOUT and the whole kernel returns.
+// Every wait (grid barrier, tagged word) has an iteration limit: a block
+// that waits too long records PIC_ERR_TIMEOUT and the whole kernel returns.
 #include <algorithm>
 
 #include "common.cuh"
