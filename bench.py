@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "PIC cycles/s"
 WORKLOAD = "tip_1m"
 # inner FP32 solver forms (PIC_PCG_*)
-PCG_VARIANTS = {"standard": 0, "pipelined": 1, "merged": 2}
+PCG_VARIANTS = {"standard": 0, "pipelined": 1, "merged": 2, "single": 3}
 STAT_DTYPE = np.dtype([("injected", "<i8"), ("collected", "<i8"), ("absorbed", "<i8"),
                        ("wrapped", "<i8"), ("crossings", "<i8"), ("alive", "<i8"),
                        ("max_walk", "<i4"), ("pcg_iters", "<i4"), ("pcg_relres", "<f8"),

@@ -83,7 +83,8 @@ typedef struct {
     int32_t quant_bits;    /* S: deposit weights in units of 2^-S, 1 <= S <= 40 */
     int32_t precision;     /* PIC_PREC_*                                        */
     int32_t pcg_variant;   /* FP32_IR inner solver: PIC_PCG_STANDARD,
-                              PIC_PCG_PIPELINED or PIC_PCG_MERGED              */
+                              PIC_PCG_PIPELINED, PIC_PCG_MERGED or
+                              PIC_PCG_SINGLE                                    */
     double ir_inner_rtol;  /* FP32_IR: the most the inner FP32 PCG is asked to
                               reduce its residual in one refinement (e.g. 1e-4);
                               it stops earlier once the FP64 target is met     */
@@ -112,6 +113,12 @@ typedef struct {
                                 k grid barriers per iteration instead of k + 1.
                                 Single systems on the resident solver only;
                                 otherwise the standard form runs            */
+#define PIC_PCG_SINGLE 3     /* Chronopoulos & Gear: one reduction (r.u, Au.u,
+                                r.r) per iteration, A p carried as s = w + beta s;
+                                with the tagged exchange and a whole-matrix
+                                Chebyshev polynomial (degree >= 2) one grid
+                                barrier per iteration.  Single systems on the
+                                resident solver only; otherwise standard     */
 
 typedef struct {
     int64_t injected;         /* SPs injected in the step                      */

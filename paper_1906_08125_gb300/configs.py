@@ -21,7 +21,7 @@ Q_ELECTRON = -E_CHARGE
 Q_OVER_M = Q_ELECTRON / M_E     # C/kg
 
 PREC_FP64, PREC_FP32_IR = 0, 1
-PCG_STANDARD, PCG_PIPELINED, PCG_MERGED = 0, 1, 2
+PCG_STANDARD, PCG_PIPELINED, PCG_MERGED, PCG_SINGLE = 0, 1, 2, 3
 FN_MURPHY_GOOD, FN_ELEMENTARY = 0, 1
 
 

@@ -105,6 +105,7 @@ struct pic_ctx_s {
     int *grp = nullptr, *blk_grp = nullptr;
     unsigned *grp_bar = nullptr;
     double *partials = nullptr;
+    double *part8 = nullptr;   // [2][grid][8] block values of the one-reduction CG
     PcgLaunch plan{};
     pic_step_stats *dstats = nullptr;  // per-step stats of pic_step
     long long dstats_cap = 0;
@@ -421,6 +422,7 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.ap32 = c->ap32;
     g.dx32 = c->dx32;
     g.partials = c->partials;
+    g.part8 = c->part8;
     g.st = c->st;
     g.stats = stats;
     g.alive = alive;
@@ -544,7 +546,7 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         (q.precision != PIC_PREC_FP64 && q.precision != PIC_PREC_FP32_IR) ||
         (q.fn_model != PIC_FN_MURPHY_GOOD && q.fn_model != PIC_FN_ELEMENTARY) ||
         (q.precision == PIC_PREC_FP32_IR && !(q.ir_inner_rtol > 0 && q.ir_inner_rtol < 1)) ||
-        (q.pcg_variant < PIC_PCG_STANDARD || q.pcg_variant > PIC_PCG_MERGED) ||
+        (q.pcg_variant < PIC_PCG_STANDARD || q.pcg_variant > PIC_PCG_SINGLE) ||
         q.ir_inner_max_iter < 0 || q.pcg_cheb_degree < 0 || q.pcg_cheb_degree > 32 ||
         (q.pcg_cheb_degree >= 2 && !(q.pcg_cheb_ratio > 1.0)))
         return fail(nullptr, PIC_ERR_ARG, "pic_create: invalid parameters");
@@ -1144,6 +1146,7 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
                              ? std::max(c->plan.grid, pcg_max_group_blocks(c->p.precision, c->num_sms))
                              : c->plan.grid;
     CK(dalloc(c, &c->partials, (size_t)2 * max_grid * 4));
+    CK(dalloc(c, &c->part8, (size_t)2 * max_grid * 8));
     c->grp = c->blk_grp = nullptr;
     c->grp_bar = nullptr;
     if (c->plan.n_groups > 0) {

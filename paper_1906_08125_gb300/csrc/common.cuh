@@ -204,6 +204,7 @@ struct PcgArgs {
     double *f, *r, *z, *p0, *p1, *ap;          // FP64 work vectors [n_pad]
     float *r32, *z32, *p32_0, *p32_1, *ap32, *dx32;  // FP32 work vectors [n_pad]
     double *partials;         // [2][grid][4]
+    double *part8;            // [2][grid][8] (resident one-reduction CG)
     DevState *st;
     pic_step_stats *stats;    // nullable
     const unsigned long long *alive;  // nullable: SPs in flight -> stats->alive

@@ -1790,6 +1790,175 @@ __device__ bool inner_merged(const Rows<RPT> &t, const In32<RPT> &m, const PcgAr
     return true;
 }
 
+// The one reduction of an iteration of the one-reduction CG (resident
+// solver, one system): block values gamma = r.u, delta = (A u).u, rr = r.r
+// and, with the coarse correction, the block sums of r, w = A u and the
+// previous s (rows with a nonzero diagonal), in a.part8.  After the barrier
+// warp 0 totals the three dot products and lane 0 forms alpha and beta
+// (Chronopoulos & Gear; i == 0: beta = 0, alpha = gamma / delta), while warp
+// 1 forms this block's rows of A0^-1 applied to the three coarse vectors.
+// out: gamma, delta, rr, (A0^-1 R0 r)_b, (A0^-1 R0 w)_b, (A0^-1 R0 s)_b,
+// alpha, beta.
+__device__ bool grid_sum_single(const DF (&v)[3], const DF (&cs)[3], bool coarse, int set,
+                                const PcgArgs &a, int i, double gamma_old, double alpha_old,
+                                double (&out)[8])
+{
+    double *vals = reduction_buffer();
+    double *res = vals + 3 * 512 - 4;   // 8 results after 6 x RW block values
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nv = coarse ? 6 : 3;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k >= nv)
+            break;
+        const double x = df_warp_sum(k < 3 ? v[k] : cs[k - 3]);
+        if (lane == 0)
+            vals[k * RW + wid] = x;
+    }
+    __syncthreads();
+    const size_t G = gridDim.x;
+    if (wid == 0) {
+        for (int k = 0; k < nv; ++k) {
+            double x = lane < RW ? vals[k * RW + lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0)
+                a.part8[((size_t)set * G + blockIdx.x) * 8 + k] = x;
+        }
+    }
+    if (!grid_sync(a))
+        return false;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double x = 0.0;
+            for (size_t b = lane; b < G; b += 32)
+                x += __ldcg(a.part8 + ((size_t)set * G + b) * 8 + k);
+            x = warp_sum(x);
+            if (lane == 0)
+                res[k] = x;
+        }
+        if (lane == 0) {
+            const double gamma = res[0], delta = res[1];
+            double alpha, beta;
+            if (i == 0) {
+                beta = 0.0;
+                alpha = gamma / delta;
+            } else {
+                beta = gamma / gamma_old;
+                alpha = gamma / (delta - beta * gamma / alpha_old);
+            }
+            res[6] = alpha;
+            res[7] = beta;
+        }
+    } else if (wid == 1 && coarse) {
+        const float *row = a.coarse_inv + (size_t)blockIdx.x * G;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+        for (size_t c = lane; c < G; c += 32) {
+            const double ic = (double)row[c];
+            const double *pc = a.part8 + ((size_t)set * G + c) * 8;
+            v0 += ic * __ldcg(pc + 3);
+            v1 += ic * __ldcg(pc + 4);
+            v2 += ic * __ldcg(pc + 5);
+        }
+        v0 = warp_sum(v0);
+        v1 = warp_sum(v1);
+        v2 = warp_sum(v2);
+        if (lane == 0) {
+            res[3] = v0;
+            res[4] = v1;
+            res[5] = v2;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        out[k] = (k >= 3 && k < 6 && !coarse) ? 0.0 : res[k];
+    return true;
+}
+
+// Chronopoulos & Gear's CG (one reduction per iteration; Comput. Appl.
+// Math. 25, 1989), preconditioned: with u = M^-1 r and w = A u,
+// gamma = r.u, delta = w.u, beta = gamma / gamma_old,
+// alpha = gamma / (delta - beta gamma / alpha_old), p = u + beta p,
+// s = w + beta s (= A p), x += alpha p, r -= alpha s.  The coarse correction
+// of the next preconditioner application rides on the same reduction
+// (R0 r' = R0 r - alpha (R0 w + beta R0 s_old)), so the polynomial and the
+// product A u exchange their halos through tagged words only: one grid
+// barrier per iteration.  Same arithmetic in exact arithmetic as the
+// standard form; s carries rounding like the A p recurrence of the standard
+// form (damped by beta < 1).
+template <int RPT>
+__device__ bool inner_single(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
+                             const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_z,
+                             float *s_d0, float *s_d1, double itol, int &set, int &it)
+{
+    const bool coarse = a.cheb_local == 3 && a.coarse_inv;
+    float u[RPT], p[RPT], sv[RPT];
+    if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, u, s_d0, s_d1, a.d32_0,
+                                   a.d32_1))
+        return false;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        p[k] = sv[k] = 0.f;
+    double gamma_old = 0.0, alpha_old = 0.0, itol2 = 0.0;
+    for (int i = 0;; ++i) {
+        if (!tagged_exchange<RPT>(t, a, g, s_z, u))
+            return false;
+        DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        DF cs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float w[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            w[k] = 0.f;
+            if (!t.ok[k])
+                continue;
+            float sum = 0.f;
+#pragma unroll 4
+            for (int c = 0; c < t.wd[k]; ++c) {
+                int lc = m.LC[t.le[k] + c * 32];
+                sum += m.VAL[t.le[k] + c * 32] * s_z[lc];
+            }
+            w[k] = sum;
+            df_add_prod(acc[0], rv[k], u[k]);
+            df_add_prod(acc[1], sum, u[k]);
+            df_add_prod(acc[2], rv[k], rv[k]);
+            if (coarse && m.dinv[k] != 0.f) {
+                df_add(cs[0], rv[k]);
+                df_add(cs[1], sum);
+                df_add(cs[2], sv[k]);
+            }
+        }
+        double o[8];
+        if (!grid_sum_single(acc, cs, coarse, set, a, i, gamma_old, alpha_old, o))
+            return false;
+        set ^= 1;
+        const double rr = o[2];
+        if (i == 0)
+            itol2 = itol * itol * rr;
+        if (!(rr > itol2 && rr > 0.0 && it < a.max_iter && !(a.inner_max > 0 && i >= a.inner_max)))
+            break;
+        const double alpha = o[6], beta = o[7];
+        const float a32 = (float)alpha, b32 = (float)beta;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            p[k] = u[k] + b32 * p[k];
+            sv[k] = w[k] + b32 * sv[k];
+            d[k] = d[k] + a32 * p[k];
+            rv[k] = rv[k] - a32 * sv[k];
+        }
+        const double z0 = coarse ? o[3] - alpha * (o[4] + beta * o[5]) : 0.0;
+        if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, u, s_d0, s_d1,
+                                       a.d32_0, a.d32_1, coarse, z0))
+            return false;
+        gamma_old = o[0];
+        alpha_old = alpha;
+        ++it;
+    }
+    return true;
+}
+
 template <int RPT>
 __device__ bool inner_pipelined(const Rows<RPT> &t, const In32<RPT> &m, const PcgArgs &a,
                                 const Seg &g, float (&rv)[RPT], float (&d)[RPT], float *s_m0,
@@ -1908,6 +2077,10 @@ __device__ __forceinline__ void pcg32ir_res(const PcgArgs &a)
     // the merged form needs a grid barrier inside the preconditioner
     const bool merged = a.variant == PIC_PCG_MERGED && a.cheb_degree >= 2 &&
                         (a.cheb_local == 0 || a.cheb_local == 3);
+    // the one-reduction form needs the tagged exchange (its products take no
+    // grid barrier of their own)
+    const bool single = a.variant == PIC_PCG_SINGLE && a.cheb_degree >= 2 &&
+                        (a.cheb_local == 0 || a.cheb_local == 3) && a.dtag[0];
     for (;;) {
         // FP64 residual r = f - M x (own x in s_x; halo of x staged)
         stage_halo(s_x, (const double *)a.x, a, g);
@@ -1960,6 +2133,7 @@ __device__ __forceinline__ void pcg32ir_res(const PcgArgs &a)
             itol = a.inner_rtol;
         const int it0 = it;
         bool good = PIPE     ? inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it)
+                    : single ? inner_single<RPT>(t, m, a, g, rv, d, s_a, s_d0, s_d1, itol, set, it)
                     : merged ? inner_merged<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
                                                  itol, set, it)
                              : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,

@@ -66,7 +66,7 @@ def solve(picfem, mesh, parts, variant, precond, rtol=1e-8):
 
 
 @pytest.mark.parametrize("precond", list(PRECONDS))
-@pytest.mark.parametrize("variant", [K.PCG_STANDARD, K.PCG_MERGED])
+@pytest.mark.parametrize("variant", [K.PCG_STANDARD, K.PCG_MERGED, K.PCG_SINGLE])
 def test_forms_reach_tolerance(picfem, tip_small, oracle_phi, variant, precond):
     phi0_o, phi1_o, parts = oracle_phi
     phi0, phi1, its, rrs, c = solve(picfem, tip_small, parts, variant, precond)
@@ -90,24 +90,29 @@ def test_pipelined_on_uniform_plate(picfem, oracle_mod, plate_small):
     c.close()
 
 
+@pytest.mark.parametrize("variant", [K.PCG_MERGED, K.PCG_SINGLE])
 @pytest.mark.parametrize("precond", ["chebyshev", "chebyshev+coarse"])
-def test_merged_iterations_close_to_standard(picfem, tip_small, oracle_phi, precond):
+def test_merged_iterations_close_to_standard(picfem, tip_small, oracle_phi, precond, variant):
+    """The merged and one-reduction forms take the standard form's iterations."""
     parts = oracle_phi[2]
     _, _, it_s, _, cs = solve(picfem, tip_small, parts, K.PCG_STANDARD, precond, rtol=1e-6)
-    _, _, it_m, _, cm = solve(picfem, tip_small, parts, K.PCG_MERGED, precond, rtol=1e-6)
+    _, _, it_m, _, cm = solve(picfem, tip_small, parts, variant, precond, rtol=1e-6)
     for a, b in zip(it_m, it_s):
         assert abs(a - b) <= 0.05 * b + 2, (it_m, it_s)
     cs.close()
     cm.close()
 
 
-def test_merged_falls_back_to_standard_bit_for_bit(picfem, tip_small, oracle_phi):
+@pytest.mark.parametrize("variant", [K.PCG_MERGED, K.PCG_SINGLE])
+def test_merged_falls_back_to_standard_bit_for_bit(picfem, tip_small, oracle_phi, variant):
+    """Where the merged or one-reduction form does not apply (Jacobi, the
+    block-local polynomial) the standard form runs, bit for bit."""
     parts = oracle_phi[2]
     for precond, local in (("jacobi", None), ("chebyshev", 1)):
         out = []
-        for variant in (K.PCG_STANDARD, K.PCG_MERGED):
+        for variant_k in (K.PCG_STANDARD, variant):
             p = K.params(E0=1e10, w_sp=0.5, capacity=100_000, precision=K.PREC_FP32_IR,
-                         pcg_rtol=1e-8, pcg_variant=variant, **PRECONDS[precond])
+                         pcg_rtol=1e-8, pcg_variant=variant_k, **PRECONDS[precond])
             c = picfem.Context(p).mesh_load(tip_small)
             if local is not None:
                 c.set_tuning(pcg_cheb_local=local)
@@ -223,7 +228,7 @@ def test_tagged_exchange_graph_steps(picfem, tip_small):
             assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("variant", [K.PCG_STANDARD, K.PCG_MERGED])
+@pytest.mark.parametrize("variant", [K.PCG_STANDARD, K.PCG_MERGED, K.PCG_SINGLE])
 def test_fp32_inner_solve_scale_invariant(picfem, tip_small, variant):
     """The FP32 inner solves work on the residual scaled by a power of two, so
     an applied field 2^+-100 times the usual one (right sides far outside the
@@ -240,3 +245,30 @@ def test_fp32_inner_solve_scale_invariant(picfem, tip_small, variant):
     for e in (-100, 100):
         assert np.array_equal(out[e][0], out[0][0]), e
         assert out[e][1] == out[0][1] and out[e][2] == out[0][2], e
+
+
+def test_single_reduction_fused_steps(picfem, tip_small):
+    """Fused FP32_IR steps with the one-reduction form: graph replays equal
+    direct launches bit for bit, and the SPs and potentials stay within the
+    solver tolerance of the standard form's."""
+    base = dict(E0=1e10, w_sp=0.5, capacity=100_000, seed=3, precision=K.PREC_FP32_IR,
+                pcg_rtol=1e-10, pcg_cheb_degree=6)
+    parts = inputs.random_particles(tip_small, 4000, seed=5, v_scale=4e6, v_up=6e6)
+    res = {}
+    for name, kw in (("std", dict(pcg_variant=K.PCG_STANDARD)),
+                     ("single", dict(pcg_variant=K.PCG_SINGLE)),
+                     ("single_direct", dict(pcg_variant=K.PCG_SINGLE, graph=0))):
+        c = picfem.Context(K.params(**base, **kw)).mesh_load(tip_small)
+        c.init_potential()
+        c.set_particles(*parts)
+        st = c.step(5)
+        x, v, cell, pid = c.particles()
+        o = np.argsort(pid)
+        res[name] = (x[o], cell[o], pid[o], c.potential(), [s.pcg_relres for s in st])
+        c.close()
+    assert all(r <= 1e-10 for r in res["single"][4])
+    for k in range(4):
+        assert np.array_equal(res["single"][k], res["single_direct"][k])
+    assert np.array_equal(res["single"][2], res["std"][2])
+    assert np.abs(res["single"][0] - res["std"][0]).max() <= 1e-6 * np.abs(res["std"][0]).max()
+    assert rel(res["single"][3], res["std"][3]) <= 1e-8
