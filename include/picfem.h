@@ -399,6 +399,13 @@ int pic_get_step(pic_ctx ctx, int64_t *step);
 int pic_set_step(pic_ctx ctx, int64_t step);
 /* phi: host or device double [n_nodes]; Dirichlet nodes read/write as 0 */
 int pic_get_potential(pic_ctx ctx, double *phi);
+/* The same copy queued on the context's stream without waiting for it: phi
+ * (host memory should be pinned, else the driver stages it synchronously,
+ * or device) holds the potential once the stream has passed the call --
+ * after pic_sync, or after an event the caller records on the context's
+ * stream following the call.  Lets a caller read step k's result while
+ * step k + 1 runs. */
+int pic_get_potential_async(pic_ctx ctx, double *phi);
 int pic_set_potential(pic_ctx ctx, const double *phi);
 /* E: host or device double [n_tets*3], the field of the current Phi */
 int pic_get_field(pic_ctx ctx, double *E);

@@ -2290,6 +2290,15 @@ extern "C" int pic_get_potential(pic_ctx c, double *phi)
     return PIC_OK;
 }
 
+extern "C" int pic_get_potential_async(pic_ctx c, double *phi)
+{
+    REQUIRE_MESH();
+    if (!phi)
+        return fail(c, PIC_ERR_ARG, "null phi");
+    CK(cudaMemcpyAsync(phi, c->phi, sizeof(double) * c->N, cudaMemcpyDefault, c->s));
+    return PIC_OK;
+}
+
 extern "C" int pic_set_potential(pic_ctx c, const double *phi)
 {
     REQUIRE_MESH();

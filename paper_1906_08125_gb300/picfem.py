@@ -26,7 +26,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_
             "pic_init_potential", "inject", "push_relocate", "deposit", "poisson_solve",
             "pic_step", "pic_adjoint", "pic_set_applied_field", "pic_set_dirichlet",
             "pic_collide", "pic_get_step", "pic_set_step", "pic_get_potential",
-            "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
+            "pic_get_potential_async", "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
             "pic_get_particles", "pic_set_particles", "pic_set_work_function",
             "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync",
             "pic_pcg_solve_static"]
@@ -127,6 +127,7 @@ def load(build_if_missing: bool = True):
         "pic_get_step": [P, C.POINTER(I64)],
         "pic_set_step": [P, I64],
         "pic_get_potential": [P, P],
+        "pic_get_potential_async": [P, P],
         "pic_set_potential": [P, P],
         "pic_get_field": [P, P],
         "pic_get_charge": [P, P],
@@ -329,6 +330,13 @@ class Context:
         if out is None:
             out = np.zeros(self.mesh.n_nodes)
         self._check(self.L.pic_get_potential(self.h, _ptr(out)))
+        return out
+
+    def get_potential_async(self, out):
+        """Queue the copy of the potential into `out` (pinned host memory or a
+        device tensor) on the context's stream; it is there once the stream
+        has passed this call (an event recorded after it, or sync())."""
+        self._check(self.L.pic_get_potential_async(self.h, _ptr(out)))
         return out
 
     def set_potential(self, phi):

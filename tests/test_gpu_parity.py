@@ -332,3 +332,26 @@ def test_profile_and_launch_count(picfem, plate_small):
     n1 = ctx.launch_count()
     ctx.step(2)
     assert ctx.launch_count() - n1 == 2 * 5
+
+
+def test_get_potential_async(picfem, plate_small):
+    """pic_get_potential_async queues the same copy as pic_get_potential on the
+    context's stream: after the stream passes it (an event recorded after the
+    call) pinned host memory and a device tensor hold the potential."""
+    import torch
+    stream = torch.cuda.current_stream()
+    c = picfem.Context(K.params(E0=1e10, w_sp=0.5, capacity=20000), stream=stream).mesh_load(plate_small)
+    c.init_potential()
+    c.step(2)
+    want = c.potential()
+    host = torch.empty(plate_small.n_nodes, dtype=torch.float64).pin_memory()
+    dev = torch.empty(plate_small.n_nodes, dtype=torch.float64, device="cuda")
+    c.get_potential_async(host)
+    c.get_potential_async(dev)
+    ev = torch.cuda.Event()
+    ev.record(stream)
+    ev.synchronize()
+    assert np.array_equal(host.numpy(), want)
+    assert np.array_equal(dev.cpu().numpy(), want)
+    with pytest.raises(picfem.PicError):
+        c._check(c.L.pic_get_potential_async(c.h, None))
