@@ -217,7 +217,7 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  * pcg_cheb_degree, which changes the preconditioner but not the stopping
  * rule, so the potential meets the same tolerance):
  *   particle_blocks_per_sm  blocks of 256 threads per SM of the particle
- *                           kernels (1..64; default 8)
+ *                           kernels (1..64; default 16 for FP32_IR, 8 for FP64)
  *   walk_form               fused step: 0 by precision (FP64 persistent lanes,
  *                           FP32 coherent warps), 1 coherent warps (a warp
  *                           walks 32 consecutive SPs to the end), 2 persistent

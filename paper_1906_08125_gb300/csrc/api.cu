@@ -565,7 +565,9 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
         delete c;
         return fail(nullptr, PIC_ERR_CUDA, "pic_create: device lacks cooperative launch");
     }
-    c->pgrid = c->num_sms * 8;
+    // particle kernels: 16 blocks of 256 per SM for the FP32 walk (more SPs
+    // claimed in flight hides more of its record-fetch latency), 8 for FP64
+    c->pgrid = c->num_sms * (q.precision == PIC_PREC_FP32_IR ? 16 : 8);
     // a Chebyshev-preconditioned solve gets the coarse correction over the
     // solver blocks by default (the plain Jacobi form stays plain)
     c->cheb_local = q.pcg_cheb_degree >= 2 ? 3 : 0;
