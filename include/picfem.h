@@ -314,8 +314,10 @@ int deposit(pic_ctx ctx, int64_t *node_charge_fx);
 
 /*
  * poisson_solve: f = (q w_sp / eps0) W 2^-S + f_Neumann on the free nodes;
- * Jacobi-PCG warm-started from the current Phi (precision per pic_params);
- * updates Phi and E.  phi: DEVICE double [n_nodes], nullable; iters and
+ * preconditioned CG warm-started from the current Phi (precision, inner form
+ * and preconditioner per pic_params and pic_tuning: Jacobi, or a Chebyshev
+ * polynomial in D^-1 M with the two-level coarse correction; FP32_IR runs
+ * FP32 inner solves inside FP64 iterative refinement); updates Phi and E.  phi: DEVICE double [n_nodes], nullable; iters and
  * rel_res: HOST, nullable (non-NULL synchronises).
  */
 int poisson_solve(pic_ctx ctx, double *phi, int32_t *iters, double *rel_res);
