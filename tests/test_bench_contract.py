@@ -1,0 +1,99 @@
+"""The measurement arithmetic of bench.py, on the CPU: the roofline object
+(achieved = algorithmic bytes of the dominant kernel / its event time, frac =
+achieved / the measured peak), the gate on the committed ncu traffic (used
+only with the kernel source it was measured on), the structure of the
+solver's byte model (k SpMVs per iteration at 8 bytes per stored FP32 entry,
+linear in the iterations), and the per-step statistics layout shared with
+the C header."""
+import ctypes
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+INFO = dict(n_free=1000, nnz=14000, n_tets=5000, n_nodes=1100, n_faces=50)
+
+
+def stats(n, iters=10, outer=1):
+    st = np.zeros(n, dtype=bench.STAT_DTYPE)
+    st["pcg_iters"] = iters
+    st["pcg_outer"] = outer
+    st["alive"] = 100
+    st["injected"] = 5
+    st["crossings"] = 1000
+    return st
+
+
+def test_roofline_takes_the_dominant_kernel_and_the_measured_peak(monkeypatch):
+    monkeypatch.setattr(bench, "peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "ncu_traffic", lambda kernel, workload: 12345)
+    st = stats(3)
+    res = dict(info=INFO, stats=st, prof={"pcg": (3, 2.0), "step_fused": (3, 1.0)},
+               prev_alive=np.array([100, 100, 100]), params={"pcg_cheb_degree": 6})
+    roof, k = bench.roofline(res, fp64=False)
+    alg = sum(bench.bytes_pcg(r, INFO, False, 6) for r in st)
+    assert roof["kernel"] == "pcg" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert roof["achieved"] == pytest.approx(alg / 2.0e-3 / 1e9, abs=0.051)   # 0.1 GB/s steps
+    assert roof["peak"] == 6000.0 and roof["peak_source"] == "measured"
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 6000.0, abs=1e-4)
+    assert roof["traffic"] == 12345
+    assert k["pcg"]["share"] == pytest.approx(2.0 / 3.0, abs=1e-4)
+    assert k["pcg"]["alg_bytes_per_launch"] == int(alg / 3)
+    assert k["step_fused"]["launches"] == 3
+
+
+def test_solver_byte_model_structure():
+    row = stats(1)[0]
+
+    def b(it, outer, k, fp64=False):
+        r = row.copy()
+        r["pcg_iters"] = it
+        r["pcg_outer"] = outer
+        return bench.bytes_pcg(r, INFO, fp64, k)
+
+    def per_it(k, fp64=False):
+        return b(11, 1, k, fp64) - b(10, 1, k, fp64)
+
+    assert b(20, 1, 6) - b(10, 1, 6) == 10 * per_it(6)
+    # every extra Chebyshev degree is one more SpMV: the FP32 matrix (value +
+    # column index, 8 bytes per stored entry) and its vector update
+    assert per_it(7) - per_it(6) == 8 * INFO["nnz"] + 20 * INFO["n_free"]
+    assert per_it(1) >= 8 * INFO["nnz"]
+    # FP64 values: 12 bytes per stored entry
+    assert per_it(1, fp64=True) >= 12 * INFO["nnz"] > per_it(1)
+    # each refinement adds an FP64 residual (matrix read once more)
+    assert b(10, 2, 6) - b(10, 1, 6) >= 12 * INFO["nnz"]
+
+
+def test_ncu_traffic_only_with_the_measured_source(monkeypatch):
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
+    e = d["pcg"]
+    monkeypatch.setattr(bench, "source_sha", lambda: e["source_sha"])
+    assert bench.ncu_traffic("pcg", e["workload"]) == e["dram_bytes_per_launch"]
+    assert bench.ncu_traffic("pcg", "another_workload") is None
+    assert bench.ncu_traffic("no_such_kernel", e["workload"]) is None
+    monkeypatch.setattr(bench, "source_sha", lambda: "0" * 16)
+    assert bench.ncu_traffic("pcg", e["workload"]) is None
+
+
+def test_source_sha_is_a_digest_of_the_kernel_sources():
+    a, b = bench.source_sha(), bench.source_sha()
+    assert a == b and len(a) == 16 and int(a, 16) >= 0
+
+
+def test_step_stats_layout_matches_the_binding():
+    from paper_1906_08125_gb300 import picfem
+    assert bench.STAT_DTYPE.itemsize == ctypes.sizeof(picfem.StepStats)
+    assert list(bench.STAT_DTYPE.names) == [f for f, _ in picfem.StepStats._fields_]
+    for f, t in picfem.StepStats._fields_:
+        assert bench.STAT_DTYPE.fields[f][1] == getattr(picfem.StepStats, f).offset, f
+        assert bench.STAT_DTYPE.fields[f][0].itemsize == ctypes.sizeof(t), f
+
+
+def test_pcg_variants_match_the_configs():
+    from paper_1906_08125_gb300 import configs as K
+    assert bench.PCG_VARIANTS == {"standard": K.PCG_STANDARD, "pipelined": K.PCG_PIPELINED,
+                                  "merged": K.PCG_MERGED, "single": K.PCG_SINGLE}
