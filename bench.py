@@ -153,7 +153,7 @@ def bench_population(mesh, n, seed):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch (the byte model is stated in the design doc)
+# algorithmic bytes per launch
 # ---------------------------------------------------------------------------
 def bytes_step_fused(st_prev_alive, st, s, rec):
     n_old = st_prev_alive

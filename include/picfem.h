@@ -253,6 +253,13 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           64-bit words (value | step tag), each block
  *                           waiting only for the values it reads; 0 with a
  *                           grid barrier per step.  Identical results
+ *   wait_limit              polls one device-side wait of the solver (a grid
+ *                           barrier, a tagged halo word) makes before the
+ *                           kernel gives up, records PIC_ERR_TIMEOUT and
+ *                           returns; 0 (default) = 2^25 polls, else 1..2^30.
+ *                           For tests and diagnosis of the failure path: a
+ *                           small limit makes a solve fail with
+ *                           PIC_ERR_TIMEOUT, and the context stays usable
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -265,6 +272,7 @@ typedef struct {
     int32_t pcg_cheb_local;
     int32_t sort_cells;
     int32_t pcg_halo_sync;
+    int32_t wait_limit;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);
@@ -454,15 +462,26 @@ int pic_sync(pic_ctx ctx);
  * that each GPU loading the library holds until the process exits.
  *   n                     rows, 1 <= n <= PIC_STATIC_MAX_ROWS (else PIC_ERR_ARG,
  *                         nothing is launched)
- *   rowptr[n+1], col[nnz] DEVICE int32 CSR pattern (0-based; the diagonal
- *                         must be stored)
+ *   rowptr[n+1], col[nnz] DEVICE int32 CSR pattern, 0-based: rowptr starts
+ *                         at 0, never decreases and ends at nnz (the length
+ *                         of col and val); every column in [0, n); the
+ *                         diagonal must be stored.  A decreasing rowptr or a
+ *                         column outside [0, n) is found by the kernel
+ *                         before any value is read through it and gives
+ *                         PIC_ERR_ARG; a rowptr whose last entry exceeds
+ *                         the arrays' length cannot be detected.
  *   val[nnz], b[n]        DEVICE double
  *   x[n]                  DEVICE double: initial guess in, solution out
  *   rtol, max_iter        stop when ||b - A x||_2 <= rtol ||b||_2 (recursive
- *                         residual), PIC_ERR_NOT_CONVERGED at max_iter
+ *                         residual), PIC_ERR_NOT_CONVERGED at max_iter (iters
+ *                         = max_iter) or on a CG breakdown (p.Ap <= 0, or a
+ *                         non-finite value during the iterations)
  *   iters, rel_res        HOST, nullable
  *   stream                cudaStream_t (NULL = legacy default stream)
- * The call synchronises `stream`.  The first call on a device, with that
+ * A non-finite value in A, b or the initial x gives PIC_ERR_ARG (it reaches
+ * the first pass's sums; x is then left as it was).  Every call copies its
+ * status words to the host and synchronises `stream` before it returns.
+ * The first call on a device, with that
  * device current, looks up the device address of the scratch array and the
  * resident grid size; make that first call before any stream capture.  All
  * calls on a device share the scratch array (each clears the words that must

@@ -126,7 +126,7 @@ struct pic_ctx_s {
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
     int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1,
-        halo_sync = 1;
+        halo_sync = 1, wait_limit = 0;
     int *scnt = nullptr, *soff = nullptr, *srank = nullptr, *sscan = nullptr;   // sort scratch
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
@@ -466,6 +466,7 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
         g.dtag[1] = c->dtag + c->n_pad;
     }
     g.epoch = c->pcg_epoch;
+    g.spin_limit = c->wait_limit > 0 ? (long long)c->wait_limit : PCG_SPIN_LIMIT_DEFAULT;
     g.inner_max = c->p.ir_inner_max_iter;
     g.n_groups = c->plan.n_groups;
     g.grp = c->grp;
@@ -1522,6 +1523,7 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->pcg_cheb_local = c->cheb_local;
     t->sort_cells = c->sort_cells;
     t->pcg_halo_sync = c->halo_sync;
+    t->wait_limit = c->wait_limit;
     return PIC_OK;
 }
 
@@ -1534,6 +1536,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 3 ||
         t->sort_cells < 0 || t->sort_cells > 1 || t->pcg_halo_sync < 0 || t->pcg_halo_sync > 1 ||
+        t->wait_limit < 0 || t->wait_limit > (1 << 30) ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
@@ -1546,6 +1549,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->cheb_local = t->pcg_cheb_local;
     c->sort_cells = t->sort_cells;
     c->halo_sync = t->pcg_halo_sync;
+    c->wait_limit = t->wait_limit;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)

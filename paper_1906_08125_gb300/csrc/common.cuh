@@ -186,6 +186,11 @@ cudaError_t launch_field_unpack(cudaStream_t s, int T, const typename Rec<R>::ve
                                 double *out);
 
 // Poisson solve
+// polls a device-side wait of the solver (grid barrier, tagged halo word)
+// makes before it gives up with PIC_ERR_TIMEOUT, unless pic_tuning.wait_limit
+// sets another limit
+constexpr long long PCG_SPIN_LIMIT_DEFAULT = 1LL << 25;
+
 struct PcgArgs {
     int n, n_pad, n_slices;
     const int *slice_ptr;     // [n_slices+1], element offsets (multiples of 32)
@@ -211,6 +216,7 @@ struct PcgArgs {
     double rtol, inner_rtol;
     int max_iter;
     int precision;
+    long long spin_limit;     // polls of one device-side wait before PIC_ERR_TIMEOUT
     int max_rows;             // resident kernels: see PcgLaunch
     long long max_chunk;
     int variant;              // FP32_IR inner solver (PIC_PCG_*)

@@ -92,7 +92,9 @@ __device__ bool na_grid_sync(Ctrl *c)
             }
         }
         __threadfence();
-        if (*(volatile int *)&c->err == PIC_ERR_TIMEOUT)
+        // any error recorded before the barrier (a timed-out wait, or an
+        // input check of the first pass) ends the solve in every block
+        if (*(volatile int *)&c->err != 0)
             ok = 0;
         ok_s = ok;
     }
@@ -147,12 +149,26 @@ __device__ bool na_grid_sum(const double (&v)[NV], const NaArgs &a, int set, dou
     return true;
 }
 
-__device__ __forceinline__ double na_row_dot(const NaArgs &a, int i, const double *v, bool gather)
+// Row i of A times v for the first pass, which also checks the caller's
+// pattern: a row whose end precedes its start, or a column outside [0, n),
+// records PIC_ERR_ARG and is skipped (nothing outside v is read).  The
+// grid barrier after the first pass ends the solve in every block when
+// an error was recorded, so the later passes only see checked rows.
+__device__ __forceinline__ double na_row_dot_checked(const NaArgs &a, int i, const double *v)
 {
+    const int k0 = a.rowptr[i], k1 = a.rowptr[i + 1];
+    if (k1 < k0 || k0 < 0) {
+        atomicCAS(&a.ctrl->err, 0, PIC_ERR_ARG);
+        return 0.0;
+    }
     double s = 0.0;
-    for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) {
-        int j = a.col[k];
-        s += a.val[k] * (gather ? __ldcg(v + j) : v[j]);
+    for (int k = k0; k < k1; ++k) {
+        const int j = a.col[k];
+        if (j < 0 || j >= a.n) {
+            atomicCAS(&a.ctrl->err, 0, PIC_ERR_ARG);
+            continue;
+        }
+        s += a.val[k] * v[j];
     }
     return s;
 }
@@ -163,6 +179,11 @@ __device__ __forceinline__ double na_diag(const NaArgs &a, int i)
         if (a.col[k] == i)
             return a.val[k];
     return 0.0;
+}
+
+__device__ __forceinline__ bool rowptr_ok(const NaArgs &a, int i)
+{
+    return a.rowptr[i] >= 0 && a.rowptr[i + 1] >= a.rowptr[i];
 }
 
 // Jacobi-PCG on a CSR matrix, thread per row, two grid barriers per
@@ -177,8 +198,8 @@ __global__ void __launch_bounds__(NA_BLOCK) k_pcg_static(NaArgs a)
     int set = 0;
     double acc[3] = {0.0, 0.0, 0.0}, tot[3];
     for (int i = tid; i < a.n; i += nt) {
-        double r = a.b[i] - na_row_dot(a, i, a.x, false);
-        double d = na_diag(a, i);
+        double r = a.b[i] - na_row_dot_checked(a, i, a.x);
+        double d = rowptr_ok(a, i) ? na_diag(a, i) : 0.0;
         double z = d != 0.0 ? r / d : 0.0;
         a.r[i] = r;
         a.z[i] = z;
@@ -192,6 +213,16 @@ __global__ void __launch_bounds__(NA_BLOCK) k_pcg_static(NaArgs a)
     set ^= 1;
     double rz = tot[0], rr = tot[1], bb = tot[2];
     int it = 0, status = 0;
+    // every block holds the same totals, so every block takes the same
+    // branch: a non-finite value in b, x or A reaches these sums
+    if (!isfinite(bb) || !isfinite(rr) || !isfinite(rz)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicCAS(&a.ctrl->err, 0, PIC_ERR_ARG);
+            a.ctrl->iters = 0;
+            a.ctrl->relres = rr / bb;
+        }
+        return;
+    }
     if (bb == 0.0) {
         for (int i = tid; i < a.n; i += nt)
             a.x[i] = 0.0;
@@ -221,6 +252,12 @@ __global__ void __launch_bounds__(NA_BLOCK) k_pcg_static(NaArgs a)
         if (!na_grid_sum<1>(pap, a, set, pt))
             return;
         set ^= 1;
+        // breakdown: A not positive definite along p, or a non-finite value
+        // (the same in every block)
+        if (!(pt[0] > 0.0) || !isfinite(pt[0])) {
+            status = PIC_ERR_NOT_CONVERGED;
+            break;
+        }
         double alpha = rz / pt[0];
         double acc2[2] = {0.0, 0.0}, t2[2];
         for (int i = tid; i < a.n; i += nt) {
@@ -237,6 +274,12 @@ __global__ void __launch_bounds__(NA_BLOCK) k_pcg_static(NaArgs a)
         if (!na_grid_sum<2>(acc2, a, set, t2))
             return;
         set ^= 1;
+        if (!isfinite(t2[0]) || !isfinite(t2[1])) {
+            status = PIC_ERR_NOT_CONVERGED;
+            ++it;
+            rr = t2[1];
+            break;
+        }
         beta = t2[0] / rz;
         rz = t2[0];
         rr = t2[1];
@@ -353,8 +396,15 @@ extern "C" int pic_pcg_solve_static(int32_t n, const int32_t *rowptr, const int3
         *iters = h.iters;
     if (rel_res)
         *rel_res = h.relres;
-    if (h.err)
-        return na_fail(h.err, h.err == PIC_ERR_NOT_CONVERGED ? "reached max_iter"
-                                                              : "device-side wait timed out");
+    if (h.err) {
+        const char *why = h.err == PIC_ERR_NOT_CONVERGED
+                              ? "not converged (max_iter reached, or CG broke down: p.Ap <= 0 "
+                                "or a non-finite value)"
+                          : h.err == PIC_ERR_ARG
+                              ? "bad input (a column outside [0, n), a decreasing rowptr, or a "
+                                "non-finite value in A, b or x)"
+                              : "device-side wait timed out";
+        return na_fail(h.err, why);
+    }
     return PIC_OK;
 }

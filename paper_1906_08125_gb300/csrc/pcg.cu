@@ -36,7 +36,6 @@ namespace pf {
 
 constexpr int PCG_BLOCK = 256;
 constexpr int PCG_WARPS = PCG_BLOCK / 32;
-constexpr long long SPIN_LIMIT = 1LL << 25;
 #define FULL_MASK 0xffffffffu
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
@@ -132,7 +131,7 @@ __device__ bool grid_sync(const PcgArgs &a, Ride r1 = Ride(), Ride r2 = Ride(),
         long long spins = 0;
         while ((int)(ld_acquire_u32(g.ctr) - target) < 0) {
             ++spins;
-            if (spins > SPIN_LIMIT ||
+            if (spins > a.spin_limit ||
                 ((spins & 1023) == 0 && ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)) {
                 atomicCAS(&a.st->err, 0, PIC_ERR_TIMEOUT);
                 ok = 0;
@@ -967,7 +966,7 @@ __device__ bool tagged_exchange(const Rows<RPT> &t, const PcgArgs &a, const Seg 
         long long spins = 0;
         while ((unsigned)(v >> 32) != tag) {
             ++spins;
-            if (spins > SPIN_LIMIT ||
+            if (spins > a.spin_limit ||
                 ((spins & 1023) == 0 && ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)) {
                 bad = 1;
                 break;

@@ -47,7 +47,8 @@ class Tuning(C.Structure):
     _fields_ = [("particle_blocks_per_sm", C.c_int32), ("walk_form", C.c_int32),
                 ("pcg_blocks_per_sm", C.c_int32), ("pcg_cheb_degree", C.c_int32),
                 ("pcg_balance", C.c_int32), ("pcg_cheb_local", C.c_int32),
-                ("sort_cells", C.c_int32), ("pcg_halo_sync", C.c_int32)]
+                ("sort_cells", C.c_int32), ("pcg_halo_sync", C.c_int32),
+                ("wait_limit", C.c_int32)]
 
 
 class StepStats(C.Structure):
