@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke entry and
 by the CPU-baseline leg of the benchmark, never by the CUDA library or its
 Python binding.  ``build()`` compiles the C file with gcc (no fused
-multiply-add) into ``oracle/_build/liboracle.so``.
+multiply-add) into ``oracle/_build/liboracle.so`` and, with OpenMP, into
+``liboracle_omp.so``: the same source with its independent loops run on all
+host cores, bit-identical to the serial build (``Oracle(..., parallel=True)``).
 """
 from __future__ import annotations
 
@@ -16,6 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "picfem_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
+LIB_OMP = os.path.join(HERE, "_build", "liboracle_omp.so")
 
 OK, ERR_ARG, ERR_MESH, ERR_CAPACITY, ERR_WALK_LIMIT, ERR_NOT_CONVERGED = 0, -1, -3, -4, -5, -6
 FN_MURPHY_GOOD, FN_ELEMENTARY = 0, 1
@@ -39,25 +42,26 @@ class Stats(C.Structure):
                 ("collected_charge", C.c_double)]
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, parallel: bool = False) -> str:
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+    out = LIB_OMP if parallel else LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "picfem_oracle.h"))):
-        tmp = LIB + f".{os.getpid()}.tmp"
+        tmp = out + f".{os.getpid()}.tmp"
+        omp = ["-fopenmp"] if parallel else []
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-std=c11", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+                               "-shared", "-std=c11", *omp, "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-_lib = None
+_libs = {False: None, True: None}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
+def lib(parallel: bool = False):
+    if _libs[parallel] is None:
+        _libs[parallel] = C.CDLL(build(parallel=parallel))
+        L = _libs[parallel]
         P = C.c_void_p
         L.or_create.restype = P
         L.or_create.argtypes = [C.POINTER(Params)]
@@ -99,7 +103,15 @@ def lib():
         L.or_locate.argtypes = [P, C.c_int64, P, P, P, P]
         L.or_barycentric.argtypes = [P, C.c_int32, P, P]
         L.or_quad_emission.argtypes = [P, P, P, P]
-    return _lib
+        L.or_quad_emission_field.argtypes = [P, P, P, P, P]
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+    return _libs[parallel]
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP build (n <= 0 leaves them); returns the count."""
+    return lib(True).or_set_threads(int(n))
 
 
 def _p(a):
@@ -136,18 +148,19 @@ def element_stiffness(x4x3) -> np.ndarray:
 
 
 class Oracle:
-    """One oracle PIC context over one mesh."""
+    """One oracle PIC context over one mesh (parallel: the OpenMP build)."""
 
-    def __init__(self, mesh, params: dict):
+    def __init__(self, mesh, params: dict, parallel: bool = False):
         self.mesh = mesh
         self.params = dict(params)
+        self.L = lib(parallel)
         p = Params(**{k: params.get(k, 0) for k, _ in Params._fields_})
         self._keep = p
-        self.h = lib().or_create(C.byref(p))
+        self.h = self.L.or_create(C.byref(p))
         arrs = mesh.arrays()
         self._arrs = arrs
         xyz, tet, nbr, pnbr, dirichlet, fnodes, ftet, wf = arrs
-        st = lib().or_mesh_load(self.h, mesh.n_nodes, _p(xyz), mesh.n_tets, _p(tet), _p(nbr),
+        st = self.L.or_mesh_load(self.h, mesh.n_nodes, _p(xyz), mesh.n_tets, _p(tet), _p(nbr),
                                 _p(pnbr), _p(dirichlet), mesh.n_faces, _p(fnodes), _p(ftet),
                                 _p(wf))
         _check(st, "or_mesh_load")
@@ -155,7 +168,7 @@ class Oracle:
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                lib().or_destroy(self.h)
+                self.L.or_destroy(self.h)
                 self.h = None
         except Exception:
             pass
@@ -163,56 +176,56 @@ class Oracle:
     # derived data ---------------------------------------------------------
     @property
     def n_free(self) -> int:
-        return lib().or_n_free(self.h)
+        return self.L.or_n_free(self.h)
 
     def geometry(self):
         T = self.mesh.n_tets
         jinv, x0, vol = np.zeros((T, 9)), np.zeros((T, 3)), np.zeros(T)
-        lib().or_geometry(self.h, _p(jinv), _p(x0), _p(vol))
+        self.L.or_geometry(self.h, _p(jinv), _p(x0), _p(vol))
         return jinv, x0, vol
 
     def matrix(self):
         n = self.n_free
-        nnz = lib().or_nnz(self.h)
+        nnz = self.L.or_nnz(self.h)
         dof = np.zeros(self.mesh.n_nodes, np.int32)
         rowptr = np.zeros(n + 1, np.int32)
         col = np.zeros(nnz, np.int32)
         val = np.zeros(nnz)
         fN = np.zeros(n)
-        lib().or_matrix(self.h, _p(dof), _p(rowptr), _p(col), _p(val), _p(fN))
+        self.L.or_matrix(self.h, _p(dof), _p(rowptr), _p(col), _p(val), _p(fN))
         return dof, rowptr, col, val, fN
 
     # state ----------------------------------------------------------------
     def init_potential(self):
         it, rr = C.c_int32(0), C.c_double(0)
-        _check(lib().or_init_potential(self.h, C.byref(it), C.byref(rr)), "or_init_potential")
+        _check(self.L.or_init_potential(self.h, C.byref(it), C.byref(rr)), "or_init_potential")
         return it.value, rr.value
 
     def potential(self) -> np.ndarray:
         phi = np.zeros(self.mesh.n_nodes)
-        lib().or_get_potential(self.h, _p(phi))
+        self.L.or_get_potential(self.h, _p(phi))
         return phi
 
     def set_potential(self, phi):
         phi = np.ascontiguousarray(phi, np.float64)
-        lib().or_set_potential(self.h, _p(phi))
+        self.L.or_set_potential(self.h, _p(phi))
 
     def set_dirichlet(self, g):
         """Prescribed potential on the Dirichlet nodes (values elsewhere ignored)."""
         g = np.ascontiguousarray(g, np.float64)
-        lib().or_set_dirichlet(self.h, _p(g))
+        self.L.or_set_dirichlet(self.h, _p(g))
 
     def field(self) -> np.ndarray:
         E = np.zeros((self.mesh.n_tets, 3))
-        lib().or_get_field(self.h, _p(E))
+        self.L.or_get_field(self.h, _p(E))
         return E
 
     def particles(self):
-        n = lib().or_num_particles(self.h)
+        n = self.L.or_num_particles(self.h)
         r, v = np.zeros((n, 3)), np.zeros((n, 3))
         cell, pid = np.zeros(n, np.int32), np.zeros(n, np.int64)
         if n:
-            lib().or_get_particles(self.h, _p(r), _p(v), _p(cell), _p(pid))
+            self.L.or_get_particles(self.h, _p(r), _p(v), _p(cell), _p(pid))
         return r, v, cell, pid
 
     def set_particles(self, r, v, cell, pid):
@@ -220,53 +233,53 @@ class Oracle:
         v = np.ascontiguousarray(v, np.float64)
         cell = np.ascontiguousarray(cell, np.int32)
         pid = np.ascontiguousarray(pid, np.int64)
-        _check(lib().or_set_particles(self.h, len(cell), _p(r), _p(v), _p(cell), _p(pid)),
+        _check(self.L.or_set_particles(self.h, len(cell), _p(r), _p(v), _p(cell), _p(pid)),
                "or_set_particles")
 
     def charge(self) -> np.ndarray:
         W = np.zeros(self.mesh.n_nodes, np.int64)
-        lib().or_get_charge(self.h, _p(W))
+        self.L.or_get_charge(self.h, _p(W))
         return W
 
     @property
     def step_index(self) -> int:
-        return lib().or_step_index(self.h)
+        return self.L.or_step_index(self.h)
 
     @step_index.setter
     def step_index(self, k):
-        lib().or_set_step_index(self.h, int(k))
+        self.L.or_set_step_index(self.h, int(k))
 
     def set_work_function(self, wf):
         wf = np.ascontiguousarray(wf, np.float64)
-        lib().or_set_work_function(self.h, _p(wf))
+        self.L.or_set_work_function(self.h, _p(wf))
 
     # the steps --------------------------------------------------------------
     def inject(self, step) -> int:
         n = C.c_int64(0)
-        _check(lib().or_inject(self.h, int(step), C.byref(n)), "or_inject")
+        _check(self.L.or_inject(self.h, int(step), C.byref(n)), "or_inject")
         return n.value
 
     def push_relocate(self, step) -> Stats:
         st = Stats()
-        _check(lib().or_push_relocate(self.h, int(step), C.byref(st)), "or_push_relocate")
+        _check(self.L.or_push_relocate(self.h, int(step), C.byref(st)), "or_push_relocate")
         return st
 
     def collide(self, step):
         """Binary collisions of the SPs in flight (App. F) for step `step`."""
-        lib().or_collide(self.h, int(step))
+        self.L.or_collide(self.h, int(step))
 
     def deposit(self) -> np.ndarray:
-        _check(lib().or_deposit(self.h), "or_deposit")
+        _check(self.L.or_deposit(self.h), "or_deposit")
         return self.charge()
 
     def poisson_solve(self):
         it, rr = C.c_int32(0), C.c_double(0)
-        _check(lib().or_poisson_solve(self.h, C.byref(it), C.byref(rr)), "or_poisson_solve")
+        _check(self.L.or_poisson_solve(self.h, C.byref(it), C.byref(rr)), "or_poisson_solve")
         return it.value, rr.value
 
     def step(self, n=1):
         stats = (Stats * max(1, n))()
-        _check(lib().or_step(self.h, int(n), stats), "or_step")
+        _check(self.L.or_step(self.h, int(n), stats), "or_step")
         return list(stats)[:n]
 
     def locate(self, r, cell):
@@ -274,17 +287,23 @@ class Oracle:
         cell = np.array(cell, np.int32, copy=True).reshape(-1)
         fate = np.zeros(len(cell), np.int32)
         wl = np.zeros(len(cell), np.int32)
-        _check(lib().or_locate(self.h, len(cell), _p(r), _p(cell), _p(fate), _p(wl)), "or_locate")
+        _check(self.L.or_locate(self.h, len(cell), _p(r), _p(cell), _p(fate), _p(wl)), "or_locate")
         return r, cell, fate, wl
 
     def barycentric(self, t, r):
         r = np.ascontiguousarray(r, np.float64)
         lam = np.zeros(4)
-        lib().or_barycentric(self.h, int(t), _p(r), _p(lam))
+        self.L.or_barycentric(self.h, int(t), _p(r), _p(lam))
         return lam
 
-    def quad_emission(self):
+    def quad_emission(self, field=None):
+        """Per quadrangle: F, J_FN and n_sp (eq. nsp) of the oracle's current
+        field, or of `field` [n_tets, 3] when given."""
         nq = 3 * self.mesh.n_faces
         F, J, n = np.zeros(nq), np.zeros(nq), np.zeros(nq)
-        lib().or_quad_emission(self.h, _p(F), _p(J), _p(n))
+        if field is None:
+            self.L.or_quad_emission(self.h, _p(F), _p(J), _p(n))
+        else:
+            E = np.ascontiguousarray(field, np.float64).reshape(self.mesh.n_tets, 3)
+            self.L.or_quad_emission_field(self.h, _p(E), _p(F), _p(J), _p(n))
         return F, J, n

@@ -25,6 +25,14 @@
  *
  * Parity unpinned: the absolute current on tip geometries (GETELEC is not
  * available and the paper's figures are missing).
+ *
+ * Threads: built with -fopenmp, the loops whose iterations are independent
+ * (tetrahedra of the field, rows of the SpMV and of the vector updates, SPs
+ * of the push and walk, quadrangles of the injection, SPs of the deposit
+ * with atomic int64 adds) run in parallel; every floating-point operation
+ * and its order are the same as in the serial build (dot products stay one
+ * sequential sum, compaction and the injection slots keep the serial
+ * order), so the two builds give bit-identical results.
  */
 #include "picfem_oracle.h"
 
@@ -32,6 +40,9 @@
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 struct or_ctx {
     or_params p;
@@ -562,7 +573,8 @@ void or_matrix(const or_ctx *c, int32_t *dof_of_node, int32_t *rowptr,
 /* ------------------------------------------------------------------ */
 static void compute_field(or_ctx *c)
 {
-    for (size_t t = 0; t < (size_t)c->n_tets; ++t) {
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < (int64_t)c->n_tets; ++t) {
         double g[4][3];
         tet_gradients(c->jinv + 9 * t, g);
         const int32_t *v = c->tet + 4 * t;
@@ -670,6 +682,7 @@ static double vdot(const double *a, const double *b, int32_t n)
 }
 static void spmv(const or_ctx *c, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < c->n_free; ++i) {
         double s = 0.0;
         for (int32_t k = c->rowptr[i]; k < c->rowptr[i + 1]; ++k)
@@ -686,6 +699,7 @@ static int pcg(or_ctx *c, const double *f, double *x, int32_t *iters,
     double *r = malloc(sz), *z = malloc(sz), *p = malloc(sz), *Ap = malloc(sz);
     int status = OR_OK;
     spmv(c, x, Ap);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         r[i] = f[i] - Ap[i];
         z[i] = r[i] / c->diag[i];
@@ -709,6 +723,7 @@ static int pcg(or_ctx *c, const double *f, double *x, int32_t *iters,
         }
         spmv(c, p, Ap);
         double alpha = rz / vdot(p, Ap, n);
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; ++i) {
             x[i] = x[i] + alpha * p[i];
             r[i] = r[i] - alpha * Ap[i];
@@ -718,6 +733,7 @@ static int pcg(or_ctx *c, const double *f, double *x, int32_t *iters,
         rr = vdot(r, r, n);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (int32_t i = 0; i < n; ++i)
             p[i] = z[i] + beta * p[i];
         ++it;
@@ -741,6 +757,7 @@ int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres)
     double *f = malloc(sizeof(double) * ((size_t)n + 1));
     double *x = malloc(sizeof(double) * ((size_t)n + 1));
     double coef = (c->p.q * c->p.w_sp) / c->p.eps0;
+#pragma omp parallel for schedule(static)
     for (int32_t node = 0; node < c->n_nodes; ++node) {
         int32_t d = c->dof[node];
         if (d < 0)
@@ -771,10 +788,16 @@ int or_init_potential(or_ctx *c, int32_t *iters, double *relres)
 /* injection (Sec. II.B.3 eqs. nsp, rnd_nsp, sp_velocity,                */
 /* sp_displacement; App. E eq. rnd_point)                                */
 /* ------------------------------------------------------------------ */
-void or_quad_emission(const or_ctx *c, double *Fout, double *Jout, double *nout)
+/* the emission of every quadrangle (F, J_FN and n_sp of eq. nsp) from the
+ * per-tetrahedron field E3 [n_tets*3]: the context's own field, or any
+ * other field of the same mesh (e.g. one read from another code, to
+ * evaluate where its rounding decisions of eq. rnd_nsp may differ) */
+void or_quad_emission_field(const or_ctx *c, const double *E3, double *Fout, double *Jout,
+                            double *nout)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t f = 0; f < c->n_faces; ++f) {
-        const double *E = c->E + 3 * (size_t)c->face_tet[f];
+        const double *E = E3 + 3 * (size_t)c->face_tet[f];
         double F = -dot3(E, c->fnhat + 3 * (size_t)f);
         if (!(F > 0.0))
             F = 0.0;
@@ -787,6 +810,11 @@ void or_quad_emission(const or_ctx *c, double *Fout, double *Jout, double *nout)
             if (nout) nout[3 * (size_t)f + k] = nsp;
         }
     }
+}
+
+void or_quad_emission(const or_ctx *c, double *Fout, double *Jout, double *nout)
+{
+    or_quad_emission_field(c, c->E, Fout, Jout, nout);
 }
 
 #define OR_ID_QUAD_SHIFT 18
@@ -821,7 +849,13 @@ int or_inject(or_ctx *c, int64_t step, int64_t *n_injected)
     double qmdt = c->p.q_over_m * c->p.dt;
     double dt = c->p.dt;
     int status = OR_OK;
-    for (int64_t q = 0; q < nq && status == OR_OK; ++q) {
+    /* slot of the first SP of each quadrangle: quadrangles in order, then j */
+    int64_t *slot = malloc(sizeof(int64_t) * (size_t)(nq + 1));
+    slot[0] = c->np;
+    for (int64_t q = 0; q < nq; ++q)
+        slot[q + 1] = slot[q] + cnt[q];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < nq; ++q) {
         if (cnt[q] == 0)
             continue;
         int32_t f = (int32_t)(q / 3);
@@ -847,13 +881,14 @@ int or_inject(or_ctx *c, int64_t step, int64_t *n_injected)
                 ok = l_v >= l_next && l_v >= l_prev;
             }
             if (!ok) {
+#pragma omp atomic write
                 status = OR_ERR_ARG;
                 break;
             }
             double R3 = or_uniform(c->p.seed, (uint64_t)step, (uint64_t)q, (uint64_t)j, 255);
             double s = qmdt * (0.5 + R3);
             double tR = dt * R3;
-            size_t k = (size_t)c->np;
+            size_t k = (size_t)(slot[q] + j);
             for (int i = 0; i < 3; ++i) {
                 double pnt = (V[i] + R1 * (m1[i] - V[i])) + R2 * (m2[i] - V[i]);
                 double v0 = s * E[i];
@@ -862,12 +897,15 @@ int or_inject(or_ctx *c, int64_t step, int64_t *n_injected)
             }
             c->cell[k] = c->face_tet[f];
             c->id[k] = (step << OR_ID_STEP_SHIFT) | (q << OR_ID_QUAD_SHIFT) | j;
-            c->np++;
-            c->n_fresh++;
         }
+    }
+    if (status == OR_OK) {
+        c->np += total;
+        c->n_fresh += total;
     }
     if (n_injected)
         *n_injected = total;
+    free(slot);
     free(nsp);
     free(cnt);
     return status;
@@ -1047,9 +1085,14 @@ int or_deposit(or_ctx *c)
         int64_t w2 = llrint(ldexp(lam[2], S));
         int64_t w3 = ((one - w0) - w1) - w2;
         const int32_t *v = c->tet + 4 * (size_t)t;
+        /* int64 sums: the same totals in any order */
+#pragma omp atomic
         c->W[v[0]] += w0;
+#pragma omp atomic
         c->W[v[1]] += w1;
+#pragma omp atomic
         c->W[v[2]] += w2;
+#pragma omp atomic
         c->W[v[3]] += w3;
     }
     return OR_OK;
@@ -1185,6 +1228,20 @@ void or_collide(or_ctx *c, int64_t step)
         g0 = g1;
     }
     free(rec);
+}
+
+/* threads of the parallel loops (an OpenMP build only); returns the number
+ * in use, 1 in a serial build */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* one PIC step in the order of Sec. II.B: E_k (already held), kick,

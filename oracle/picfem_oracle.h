@@ -131,6 +131,12 @@ void or_barycentric(const or_ctx *c, int32_t t, const double *r, double *lam4);
 
 /* per-quadrangle emission numbers of the current field (for the pins) */
 void or_quad_emission(const or_ctx *c, double *F, double *J, double *n_sp);
+/* threads of the parallel loops of an OpenMP build (n <= 0: unchanged);
+ * returns the number in use (1 in a serial build) */
+int or_set_threads(int n);
+/* the same numbers from a given per-tetrahedron field E3 [n_tets*3] */
+void or_quad_emission_field(const or_ctx *c, const double *E3, double *F, double *J,
+                            double *n_sp);
 
 #ifdef __cplusplus
 }

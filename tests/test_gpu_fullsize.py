@@ -4,6 +4,8 @@ fused pic_step), against the FP64 oracle on sampled outputs: a seeded
 population of 2e5 SPs (the oracle handles it in seconds) stepped once from
 identical state, and the potentials of the charge-free and space-charge
 solves.  Also the FP64 split path at full size, bit for bit."""
+import os
+
 import numpy as np
 import pytest
 
@@ -119,6 +121,46 @@ def test_one_bench_step_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
     W = ctx.charge()
     assert int(W.sum()) == len(g[3]) * 2 ** 32
     assert rel(ctx.potential(), o2.potential()) <= 1e-6
+
+
+FREE_STEPS = int(os.environ.get("PIC_PARITY_TIP_STEPS", "20"))
+
+
+def test_free_running_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
+    """The benchmark's configuration (FP32 push, FP32 Chebyshev-PCG inside
+    FP64 refinement to the benchmark's 1e-6, fused pic_step) against the FP64
+    oracle (rtol 1e-10), both running free from identical state (the oracle's
+    tight potential and the seeded 2e5-SP sample) for FREE_STEPS steps
+    (PIC_PARITY_TIP_STEPS; 20 by default): the potential within 1e-6 every
+    step, every SP within 1e-5 of the box height of the oracle's at every
+    step unless tests/freerun_check.py explains it (a cell flip at a face
+    while the positions still agreed, an injection count on the other side
+    of a rounding threshold, an exit one step apart near Gamma_1/Gamma_3)."""
+    from freerun_check import FreeRunCheck
+    mesh, p = tip1m
+    orc0, phi0, parts = oracle_state
+    phi_start = orc0.potential()
+    orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-10,
+                                       pcg_max_iter=50000))
+    orc.set_potential(phi_start)
+    orc.set_particles(*parts)
+    ctx = picfem.Context(p).mesh_load(mesh)
+    ctx.set_potential(phi_start)
+    ctx.set_particles(*parts)
+    chk = FreeRunCheck(mesh, orc, p["seed"])
+    worst = 0.0
+    for _ in range(FREE_STEPS):
+        k = orc.step_index
+        assert ctx.step_index == k
+        E_g, E_o = ctx.field(), orc.field()
+        ctx.step(1)
+        orc.step(1)
+        chk.step(k, ctx.particles(), orc.particles(), E_g, E_o)
+        worst = max(worst, rel(ctx.potential(), orc.potential()))
+    s = chk.summary()
+    print(f"tip_1m FP32+IR free-running {FREE_STEPS} steps:", s, "potential", worst)
+    assert worst <= 1e-6
+    assert not chk.failures, s
 
 
 def test_fp64_split_step_bit_exact_full_size(picfem, oracle_mod, tip1m, oracle_state):
