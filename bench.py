@@ -7,7 +7,10 @@ the C ABI with host buffers, and the CPU oracle as a reported baseline.
 
 One step = one full PIC cycle (injection, push, walk, deposit, Poisson solve).
 Every timed step is preceded by an L2 flush (a 256 MB write, outside the
-step's events) and bracketed by CUDA events on the library's stream.
+step's events) and bracketed by CUDA events on the library's stream; the
+steps replay their captured CUDA graphs as in production (no per-kernel
+events).  The per-kernel split and the roofline come from a second pass of
+the same length right after it with the library's per-kernel events on.
 Several GPUs run independent replicas (the cycle does not shard; the
 ensemble of runs does), each seeded by its rank.
 """
@@ -35,7 +38,8 @@ PCG_VARIANTS = {"standard": 0, "pipelined": 1, "merged": 2, "single": 3}
 STAT_DTYPE = np.dtype([("injected", "<i8"), ("collected", "<i8"), ("absorbed", "<i8"),
                        ("wrapped", "<i8"), ("crossings", "<i8"), ("alive", "<i8"),
                        ("max_walk", "<i4"), ("pcg_iters", "<i4"), ("pcg_relres", "<f8"),
-                       ("collected_charge", "<f8"), ("pcg_outer", "<i4"), ("reserved", "<i4")])
+                       ("collected_charge", "<f8"), ("pcg_outer", "<i4"), ("reserved", "<i4"),
+                       ("walk_warp_iters", "<i8")])
 
 
 def parse():
@@ -51,10 +55,13 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=10,
+                    help="oracle steps timed for the CPU baseline (one thread and all cores)")
     ap.add_argument("--ensemble", type=int, default=64, help="replicas of the batched ensemble")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--adjoint-steps", type=int, default=20, help="0 skips the adjoint timing")
+    ap.add_argument("--adjoint-steps", type=int, default=200, help="0 skips the adjoint timing")
+    ap.add_argument("--adjoint-ckpt", type=int, default=20)
+    ap.add_argument("--large-steps", type=int, default=20, help="timed steps of the 8M-tet tip")
     ap.add_argument("--no-diode", action="store_true", help="skip the planar-diode I-V sweep")
     ap.add_argument("--no-large", action="store_true", help="skip the 8M-tet tip")
     return ap.parse_args()
@@ -181,6 +188,21 @@ def bytes_pcg(st, info, fp64, cheb):
     return it * per_it + (outer + 1) * (12 * nnz + 24 * n) + outer * 76 * n + 28 * n + 20 * n
 
 
+def bytes_pcg_min(st, info, fp64):
+    """Algorithmic bytes of one solve with one SpMV per CG iteration (the
+    preconditioner's own products not counted): per iteration the stored
+    matrix (s-byte value + 4-byte column per entry), the row pointers and ten
+    vector sweeps of 8 bytes, I * (nnz (s + 4) + 4 (n + 1) + 80 n); the FP32
+    form adds per FP64 refinement one FP64 residual product, 12 nnz + 24 n."""
+    n, nnz = info["n_free"], info["nnz"]
+    it, outer = int(st["pcg_iters"]), int(st["pcg_outer"])
+    s = 8 if fp64 else 4
+    total = it * (nnz * (s + 4) + 4 * (n + 1) + 80 * n)
+    if not fp64:
+        total += outer * (12 * nnz + 24 * n)
+    return total
+
+
 def bytes_field(info, s, rec):
     return info["n_tets"] * (rec + 16 + 4 * s) + 8 * info["n_nodes"]
 
@@ -207,18 +229,32 @@ def aggregate_replicas(total_ms, pushes, world, device):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True):
+FORMS = {
+    # the benchmark's form: FP32 push, FP32 Chebyshev-PCG (+ coarse correction)
+    # inside FP64 refinement
+    "fp32_ir": {},
+    # the plain FP64 form: FP64 throughout, Jacobi-PCG
+    "fp64": dict(precision=0, pcg_rtol=1e-6, pcg_cheb_degree=0),
+    # FP64 throughout with the FP32 form's preconditioner (Chebyshev(6) and
+    # the coarse correction over the solver blocks): separates precision
+    # from preconditioning
+    "fp64_twolevel": dict(precision=0, pcg_rtol=1e-6, pcg_cheb_degree=6),
+}
+
+
+def run_gpu(args, rank, world, form, timed_steps, warmup, prof_steps=None):
+    """Warm-up, then `timed_steps` steps as production runs them (CUDA graph
+    replays, no per-kernel events; L2 flushed before each step outside its
+    events), then `prof_steps` more steps with the library's per-kernel
+    events on for the kernel split."""
     import torch
 
     from paper_1906_08125_gb300 import configs as K
     from paper_1906_08125_gb300 import picfem
 
-    prec = K.PREC_FP32_IR if precision == "fp32_ir" else K.PREC_FP64
-    mesh, p, _ = K.workload(args.workload, precision=prec, seed=rank)
-    if prec == K.PREC_FP64:
-        # the plain FP64 form: FP64 throughout, Jacobi-PCG
-        p = dict(p, pcg_rtol=1e-6, pcg_cheb_degree=0)
-    else:
+    mesh, p, _ = K.workload(args.workload, seed=rank)
+    p = dict(p, **FORMS[form])
+    if p["precision"] == K.PREC_FP32_IR:
         p = dict(p, pcg_variant=PCG_VARIANTS[args.pcg_variant])
     target = K.WORKLOADS[args.workload]["target_sp"]
     stream = torch.cuda.current_stream()
@@ -230,65 +266,100 @@ def run_gpu(args, rank, world, precision, timed_steps, warmup, with_profile=True
     ctx.deposit()
     ctx.poisson_solve()          # space-charge potential of the starting population
     dev = torch.cuda.current_device()
+    ctx.profile(False)
     for _ in range(warmup):
         ctx.step(1, stats=False)
     ctx.sync()
-    n0 = ctx.num_particles()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    dstats = torch.zeros(timed_steps * STAT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(timed_steps)]
+    L = ctx.L
+
+    def timed(n, events):
+        n0 = ctx.num_particles()
+        dstats = torch.zeros(n * STAT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        base = dstats.data_ptr()
+        for k in range(n):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            rc = L.pic_step(ctx.h, 1, picfem.C.cast(
+                picfem.C.c_void_p(base + k * STAT_DTYPE.itemsize),
+                picfem.C.POINTER(picfem.StepStats)))
+            ev[k][1].record(stream)
+            if rc != 0:
+                ctx._check(rc)
+        torch.cuda.synchronize()
+        ctx.sync()
+        st = np.frombuffer(dstats.cpu().numpy().tobytes(), dtype=STAT_DTYPE)
+        prev = np.concatenate([[n0], st["alive"][:-1]])
+        return [a.elapsed_time(b) for a, b in ev], st, prev, n0
+
     clocks = ClockSampler(dev)
     clocks.start()
     time.sleep(0.6)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    L = ctx.L
     launches0 = ctx.launch_count()
-    if with_profile:
-        ctx.profile(True)
-    base = dstats.data_ptr()
-    for k in range(timed_steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        rc = L.pic_step(ctx.h, 1, picfem.C.cast(picfem.C.c_void_p(base + k * STAT_DTYPE.itemsize),
-                                                picfem.C.POINTER(picfem.StepStats)))
-        ev[k][1].record(stream)
-        if rc != 0:
-            ctx._check(rc)
-    torch.cuda.synchronize()
-    ctx.sync()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms, st, prev, n0 = timed(timed_steps, True)
     launches = ctx.launch_count() - launches0
-    prof = ctx.profile_read() if with_profile else {}
+    graph = ctx.info()["graph"]
     clk = clocks.stop()
-    st = np.frombuffer(dstats.cpu().numpy().tobytes(), dtype=STAT_DTYPE)
-    prev = np.concatenate([[n0], st["alive"][:-1]])
     total_ms, pushes = aggregate_replicas(float(sum(step_ms)), int((prev + st["injected"]).sum()),
                                           world, dev)
+    prof, pst, pprev = {}, None, None
+    if prof_steps:
+        ctx.profile(True)
+        pms, pst, pprev, _ = timed(prof_steps, False)
+        prof = ctx.profile_read()
+        ctx.profile(False)
     res = dict(ctx=ctx, mesh=mesh, params=p, info=info, step_ms=step_ms, total_ms=total_ms,
                stats=st, prev_alive=prev, pushes=pushes, launches=launches, prof=prof,
-               clocks=clk, n0=n0)
+               prof_stats=pst, prof_prev_alive=pprev, clocks=clk, n0=n0, graph=graph)
     return res
 
 
+def ncu_onchip(kernel, workload):
+    """Shared-memory bytes per launch (and the DRAM share of peak) from the
+    committed single-kernel ncu summary, if it was taken on the current
+    kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_onchip.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != source_sha() or e.get("workload") != workload:
+        return None
+    return e
+
+
+SMEM_BYTES_PER_CLK_PER_SM = 128      # one shared-memory wavefront per clock and SM
+
+
 def roofline(res, fp64):
-    info, st, prof = res["info"], res["stats"], res["prof"]
+    """Roofline of the dominant kernel from the profiled pass: algorithmic
+    bytes per launch / its mean CUDA-event time against the measured HBM copy
+    peak.  For the solver the bytes count one SpMV per CG iteration
+    (bytes_pcg_min); the bytes with every SpMV of the Chebyshev
+    preconditioner (bytes_pcg) are reported beside it."""
+    info, prof = res["info"], res["prof"]
+    st, prev = res.get("prof_stats"), res.get("prof_prev_alive")
+    if st is None:
+        st, prev = res["stats"], res["prev_alive"]
     s = 8 if fp64 else 4
     rec = 128 if fp64 else 64
+    cheb = res["params"].get("pcg_cheb_degree", 0)
     alg = {
-        "step_fused": sum(bytes_step_fused(int(pa), row, s, rec)
-                          for pa, row in zip(res["prev_alive"], st)),
-        "pcg": sum(bytes_pcg(row, info, fp64, res["params"].get("pcg_cheb_degree", 0))
-                   for row in st),
+        "step_fused": sum(bytes_step_fused(int(pa), row, s, rec) for pa, row in zip(prev, st)),
+        "pcg": sum(bytes_pcg_min(row, info, fp64) for row in st),
         "field": len(st) * bytes_field(info, s, rec),
         "inject_count": len(st) * bytes_inject_count(info, s),
     }
+    alg_precond = sum(bytes_pcg(row, info, fp64, cheb) for row in st)
     peak, kind = peaks()
-    kernels = {}
-    for name, (n, ms) in prof.items():
-        kernels[name] = {"launches": int(n), "ms": ms}
+    kernels = {name: {"launches": int(n), "ms": ms} for name, (n, ms) in prof.items()}
     total = sum(k["ms"] for k in kernels.values()) or 1.0
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     out_k = {}
@@ -297,12 +368,32 @@ def roofline(res, fp64):
         out_k[name] = {"launches": k["launches"], "ms_total": round(k["ms"], 4),
                        "share": round(k["ms"] / total, 4),
                        "alg_bytes_per_launch": int(alg[name] / k["launches"]) if name in alg else None,
-                       "achieved_gbs": round(gbs, 1) if gbs else None}
-    a = out_k[dom]["achieved_gbs"]
-    traffic = ncu_traffic(dom, WORKLOAD)
+                       "alg_gbs": round(gbs, 1) if gbs else None}
+    if "step_fused" in out_k:
+        out_k["step_fused"]["note"] = ("bytes count one walk-record fetch per face crossing; "
+                                       "neighbouring SPs share records in L1/L2, so this is "
+                                       "not DRAM traffic")
+    a = out_k[dom]["alg_gbs"]
     roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": peak, "unit": "GB/s",
-            "frac": round(a / peak, 4) if a else None, "traffic": traffic,
+            "frac": round(a / peak, 4) if a else None, "traffic": ncu_traffic(dom, WORKLOAD),
             "peak_source": kind}
+    if dom == "pcg":
+        ms = kernels["pcg"]["ms"]
+        roof["bytes_model"] = ("one SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n), "
+                               "s = value bytes; FP32 form + refinements x (12 nnz + 24 n)")
+        roof["alg_frac_incl_precond"] = round(alg_precond / (ms * 1e-3) / 1e9 / peak, 4)
+        oc = ncu_onchip("pcg", WORKLOAD)
+        if oc:
+            mhz = (res.get("clocks") or {}).get("sm_mhz") or oc.get("sm_mhz")
+            sms = oc.get("sms", 152)
+            speak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+            sach = oc["smem_bytes_per_launch"] / (ms / kernels["pcg"]["launches"] * 1e-3) / 1e9
+            roof["onchip"] = {"bound": "smem", "achieved": round(sach, 1),
+                              "peak": round(speak, 1), "unit": "GB/s",
+                              "frac": round(sach / speak, 4),
+                              "peak_basis": f"{sms} SMs x 128 B/clk at {mhz:.0f} MHz"}
+            roof["limiter"] = oc.get("limiter")
+            roof["dram_pct_of_peak_ncu"] = oc.get("dram_pct_of_peak")
     return roof, out_k
 
 
@@ -327,13 +418,16 @@ def ensemble_inputs(n_rep):
     return b, (cat[0], cat[1], cat[2].astype(np.int32), cat[3])
 
 
-def bytes_batch_pcg(ri, fp64, cheb, outer):
-    """bytes_pcg summed over the replicas of a batch, each with its own
-    iteration count (the last solve's), stored entries and free DOFs."""
+def bytes_batch_pcg(ri, fp64, cheb, outer, minimal=True):
+    """The solver's bytes summed over the replicas of a batch, each with its
+    own iteration count (the last solve's), stored entries and free DOFs:
+    bytes_pcg_min (one SpMV per iteration), or bytes_pcg with every SpMV of
+    the preconditioner."""
     total = 0
     for it, nnz, n in zip(ri["pcg_iters"], ri["stored"], ri["free_dofs"]):
-        total += bytes_pcg({"pcg_iters": int(it), "pcg_outer": outer},
-                           {"n_free": int(n), "nnz": int(nnz)}, fp64, cheb)
+        row = {"pcg_iters": int(it), "pcg_outer": outer}
+        inf = {"n_free": int(n), "nnz": int(nnz)}
+        total += bytes_pcg_min(row, inf, fp64) if minimal else bytes_pcg(row, inf, fp64, cheb)
     return total
 
 
@@ -346,7 +440,9 @@ def run_ensemble(n_rep, steps, warmup):
     b, cat = ensemble_inputs(n_rep)
     peak, kind = peaks()
     forms = {"fp32_ir": dict(precision=K.PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
-             "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0)}
+             "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0),
+             "fp64_twolevel": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=6)}
+    sequential_forms = ("fp32_ir", "fp64")
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {"replicas": n_rep, "tets": int(b.mesh.n_tets), "nodes": int(b.mesh.n_nodes),
            "emitting_faces": int(b.mesh.n_faces), "sp_start": int(len(cat[3])),
@@ -385,9 +481,11 @@ def run_ensemble(n_rep, steps, warmup):
         c.profile(False)
         pcg_ms = prof["pcg"][1] / prof["pcg"][0]
         cheb = c.tuning()["pcg_cheb_degree"]
-        alg = bytes_batch_pcg(ri, form["precision"] == K.PREC_FP64, cheb,
-                              int(np.median([s.pcg_outer for s in st])))
+        outer = int(np.median([s.pcg_outer for s in st]))
+        is64 = form["precision"] == K.PREC_FP64
+        alg = bytes_batch_pcg(ri, is64, cheb, outer)
         gbs = alg / (pcg_ms * 1e-3) / 1e9
+        gbs_pre = bytes_batch_pcg(ri, is64, cheb, outer, minimal=False) / (pcg_ms * 1e-3) / 1e9
         entry.update({"ms_per_step": round(ms, 3),
                       "replica_cycles_per_s": round(n_rep * 1e3 / ms, 1),
                       "sp_in_flight": int(st[-1].alive),
@@ -399,13 +497,15 @@ def run_ensemble(n_rep, steps, warmup):
                                              int(ri["pcg_iters"].max())],
                       "roofline_pcg": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
                                        "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                       "alg_frac_incl_precond": round(gbs_pre / peak, 4),
                                        "peak_source": kind}})
         out["batched"][name] = entry
         c.close()
     # the same replicas one context at a time, from the FP32 batch's state
     phi, parts, k = state
     rid = np.searchsorted(b.tet_off, parts[2], side="right") - 1
-    for name, form in forms.items():
+    for name in sequential_forms:
+        form = forms[name]
         tot = 0.0
         for r, m in enumerate(b.members):
             p = K.params(w_sp=ENSEMBLE_WSP, capacity=2_000_000, E0=float(b.E0[r]), seed=r, **form)
@@ -500,16 +600,19 @@ def run_large(workload, steps, warmup):
     pcg_ms = prof["pcg"][1] / prof["pcg"][0]
     row = {"pcg_iters": int(np.median([s.pcg_iters for s in st])),
            "pcg_outer": int(np.median([s.pcg_outer for s in st]))}
-    alg = bytes_pcg(row, info, False, p["pcg_cheb_degree"])
+    alg = bytes_pcg_min(row, info, False)
     peak, kind = peaks()
     gbs = alg / (pcg_ms * 1e-3) / 1e9
+    gbs_pre = bytes_pcg(row, info, False, p["pcg_cheb_degree"]) / (pcg_ms * 1e-3) / 1e9
     return {"workload": workload, "tets": info["n_tets"], "free_dofs": info["n_free"],
             "nnz": info["nnz"], "resident_solver": bool(info["pcg_resident"]),
             "sp_in_flight": int(st[-1].alive), "steps": steps, "warmup": warmup,
             "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 2), "unit": METRIC,
             "pcg_ms_per_step": round(pcg_ms, 3), "pcg_iters": row["pcg_iters"],
             "roofline_pcg": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
-                             "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": kind},
+                             "unit": "GB/s", "frac": round(gbs / peak, 4),
+                             "alg_frac_incl_precond": round(gbs_pre / peak, 4),
+                             "traffic": ncu_traffic("pcg", workload), "peak_source": kind},
             "setup_s": round(setup_s, 1)}
 
 
@@ -566,13 +669,40 @@ def run_e2e(res, steps):
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def run_oracle(workload, steps, seed=0):
+def host_cpu():
+    """The host's logical CPUs and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def run_oracle(workload, steps, seed=0, parallel=False):
+    """The FP64 oracle on the host: `steps` full PIC steps of the workload from
+    the benchmark's seeded starting population (deposited and solved first,
+    untimed).  parallel: the OpenMP build on every host core (bit-identical
+    results); else the serial build on one core."""
     from oracle import oracle as O
     from paper_1906_08125_gb300 import configs as K
     mesh, p, _ = K.workload(workload)
     target = K.WORKLOADS[workload]["target_sp"]
     p = dict(p, precision=K.PREC_FP64)
-    orc = O.Oracle(mesh, p)
+    cores = O.set_threads(os.cpu_count()) if parallel else 1
+    orc = O.Oracle(mesh, p, parallel=parallel)
     orc.init_potential()
     r, v, cell, pid = bench_population(mesh, target, seed=1000 + seed)
     orc.set_particles(r, v, cell, pid)
@@ -581,28 +711,41 @@ def run_oracle(workload, steps, seed=0):
     t0 = time.perf_counter()
     orc.step(steps)
     dt = time.perf_counter() - t0
-    return {"value": round(steps / dt, 5), "unit": "PIC cycles/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{steps} full PIC steps of the {workload} workload (FP64 oracle, one "
-                       f"thread), from the seeded synthetic population of {target} SPs that "
-                       f"the GPU arm starts from (deposited and solved first); mesh build and the "
-                       f"initial solves untimed"),
-            "seconds": round(dt, 2)}
+    how = (f"OpenMP build, {cores} threads" if parallel else "serial build, one thread")
+    return {"value": round(steps / dt, 5), "unit": "PIC cycles/s", "cores": cores,
+            "kind": "oracle",
+            "sample": (f"{steps} full PIC steps of the {workload} workload (FP64 oracle, {how}), "
+                       f"from the seeded synthetic population of {target} SPs that the GPU arm "
+                       f"starts from (deposited and solved first); mesh build and the initial "
+                       f"solves untimed"),
+            "seconds": round(dt, 2), "host": host_cpu()}
 
 
 def reference_arm(args, rank, world):
+    """The reference arm: the oracle on all host cores (rank 0 only)."""
     if rank != 0:
         return
-    steps = max(1, min(args.steps, args.cpu_steps))
-    cb = run_oracle(args.workload, steps)
+    steps = max(1, min(args.steps, 30))
+    cb = run_oracle(args.workload, steps, parallel=True)
     line = {"metric": METRIC, "value": cb["value"], "unit": cb["unit"], "n_gpus": args.gpus,
             "steps": steps, "warmup": 0, "ms_per_step": round(1e3 / cb["value"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "ref": "CPU oracle (plain FP64 C)"},
+            "config": {"workload": args.workload, "ref": "CPU oracle (plain FP64 C, OpenMP)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def arm_summary(r, world):
+    """Throughput of a comparison arm from its timed (production) steps."""
+    st = r["stats"]
+    return {"value": round(world * len(r["step_ms"]) / (r["total_ms"] * 1e-3), 3),
+            "unit": METRIC, "ms_per_step": round(r["total_ms"] / len(r["step_ms"]), 3),
+            "pushes_per_s": round(r["pushes"] / (r["total_ms"] * 1e-3), 1),
+            "pcg_iters_mean": round(float(st["pcg_iters"].mean()), 1),
+            "steps": len(r["step_ms"])}
 
 
 def main():
@@ -619,9 +762,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     fp64 = args.precision == "fp64"
-    res = run_gpu(args, rank, world, args.precision, args.steps, max(3, args.warmup))
-    roof, kernels = roofline(res, fp64)
     K = args.steps
+    res = run_gpu(args, rank, world, args.precision, K, max(3, args.warmup),
+                  prof_steps=max(5, min(K, 20)))
+    roof, kernels = roofline(res, fp64)
     value = world * K / (res["total_ms"] * 1e-3)
     push_rate = res["pushes"] / (res["total_ms"] * 1e-3)
     e2e = run_e2e(res, args.e2e_steps)
@@ -632,35 +776,46 @@ def main():
            "sp_in_flight_mean": int(st["alive"].mean()), "target_sp": int(res["n0"]),
            "dt_fs": 4.0, "precision": args.precision, "pcg_rtol": res["params"]["pcg_rtol"],
            "pcg_variant": args.pcg_variant if args.precision == "fp32_ir" else "standard",
-           "l2": "flushed before every timed step (256 MB write)", "parallelism":
-           f"replicas x{world}"}
+           "l2": "flushed before every timed step (256 MB write)",
+           "timed_path": ("CUDA graph replays, no per-kernel events" if res["graph"] == 1
+                          else "direct launches"),
+           "kernel_split": f"a second pass of {len(res['prof_stats'])} steps with per-kernel "
+                           f"CUDA events, right after the timed steps",
+           "parallelism": f"replicas x{world}"}
+    cross = float(st["crossings"].sum())
     extra = {"pushes_per_s": round(push_rate, 1),
              "pcg_iters_mean": round(float(st["pcg_iters"].mean()), 1),
              "pcg_outer_mean": round(float(st["pcg_outer"].mean()), 2),
-             "crossings_per_sp": round(float(st["crossings"].sum()) / max(1, res["pushes"]), 1),
+             "crossings_per_sp": round(cross / max(1, res["pushes"]), 1),
+             "walk_lane_slots_per_crossing": round(32.0 * float(st["walk_warp_iters"].sum())
+                                                   / max(1.0, cross), 3),
              "kernels": kernels}
+    pcg_ms_step = kernels.get("pcg", {}).get("ms_total", 0.0) / max(1, len(res["prof_stats"]))
+    extra["pcg_ms_per_step"] = round(pcg_ms_step, 4)
     launches, clocks = res["launches"], res["clocks"]
     res["ctx"].close()
     del res
-    fp64_cmp = None
+    compare = {}
     if not args.no_fp64_compare and not fp64:
-        r64 = run_gpu(args, rank, world, "fp64", max(5, K // 3), max(3, args.warmup))
-        fp64_cmp = {"value": round(world * len(r64["step_ms"]) / (r64["total_ms"] * 1e-3), 3),
-                    "unit": METRIC,
-                    "ms_per_step": round(r64["total_ms"] / len(r64["step_ms"]), 3),
-                    "pushes_per_s": round(r64["pushes"] / (r64["total_ms"] * 1e-3), 1),
-                    "pcg_iters_mean": round(float(r64["stats"]["pcg_iters"].mean()), 1)}
-        r64["ctx"].close()
-        del r64
+        for form in ("fp64", "fp64_twolevel"):
+            r = run_gpu(args, rank, world, form, max(5, K // 3), max(3, args.warmup),
+                        prof_steps=5)
+            compare[form] = arm_summary(r, world)
+            compare[form]["pcg_ms_per_step"] = round(r["prof"]["pcg"][1] / r["prof"]["pcg"][0], 4)
+            r["ctx"].close()
+            del r
+        for form, c in compare.items():
+            c["fp32_ir_speedup"] = round(value / world / c["value"], 3)
+            c["fp32_ir_solver_speedup"] = round(c["pcg_ms_per_step"] / max(pcg_ms_step, 1e-9), 3)
     ens = None
     if rank == 0 and world == 1 and not args.no_ensemble:
         ens = run_ensemble(args.ensemble, steps=10, warmup=10)
     adj = None
     if rank == 0 and world == 1 and args.adjoint_steps > 0:
-        adj = run_adjoint_bench(args.workload, args.adjoint_steps, 10)
+        adj = run_adjoint_bench(args.workload, args.adjoint_steps, args.adjoint_ckpt)
     large = None
     if rank == 0 and world == 1 and not args.no_large:
-        large = run_large("tip_8m", steps=5, warmup=5)
+        large = run_large("tip_8m", steps=args.large_steps, warmup=5)
     diode = None
     if rank == 0 and world == 1 and not args.no_diode:
         from paper_1906_08125_gb300 import diode as D
@@ -672,6 +827,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_oracle(args.workload, args.cpu_steps)
+        cpu["all_cores"] = run_oracle(args.workload, args.cpu_steps, parallel=True)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "PIC cycles/s",
                 "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
@@ -679,7 +835,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if not fp64 else "f64", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64_cmp,
+                "gpu_launches": launches, "clocks": clocks,
+                "fp64_plain": compare.get("fp64"), "fp64_twolevel": compare.get("fp64_twolevel"),
                 "ensemble": ens, "adjoint": adj, "diode_iv": diode, "tip_8m": large, **extra}
         print(json.dumps(line), flush=True)
     if world > 1:

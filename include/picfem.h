@@ -133,6 +133,11 @@ typedef struct {
     double collected_charge;  /* q * w_sp * collected [C]                      */
     int32_t pcg_outer;        /* FP32_IR refinements (FP64: 0)                 */
     int32_t reserved;
+    int64_t walk_warp_iters;  /* walk iterations summed over warps: a warp of
+                                 the coherent form spends its longest walk on
+                                 each group of 32 SPs, one of the persistent
+                                 form its loop iterations; 32 x this / crossings
+                                 is the lane slots per useful walk step      */
 } pic_step_stats;
 
 typedef struct {
@@ -239,9 +244,19 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           R0^T A0^-1 R0 r over the blocks (R0 sums a block's
  *                           rows, A0 = R0 M R0^T; one grid barrier); 3 is the
  *                           whole-matrix polynomial plus that coarse
- *                           correction (the default when pcg_cheb_degree >= 2;
- *                           otherwise 0).  All are SPD; the stopping rule is
- *                           unchanged
+ *                           correction; 4 a three-level multigrid V-cycle:
+ *                           aggregates of the matrix rows by three passes of
+ *                           pairwise matching within each solver block (level
+ *                           1), four more on level 1 (level 2, solved with a
+ *                           dense inverse), Galerkin coarse matrices,
+ *                           Chebyshev smoothing of degree 3 before and after
+ *                           the coarse correction on the fine level and on
+ *                           level 1 (built at mesh_load for the resident
+ *                           solver; PIC_ERR_ARG where it was not built).  The
+ *                           default is 4 where the hierarchy exists and
+ *                           pcg_cheb_degree >= 2, else 3 when pcg_cheb_degree
+ *                           >= 2, otherwise 0.  All are SPD; the stopping rule
+ *                           is unchanged
  *   sort_cells              pic_step: 1 (default) orders the surviving SPs by
  *                           cell after every step (a counting sort; the
  *                           neighbouring SPs' walks then share walk records in

@@ -29,6 +29,7 @@ UNITS = {
     "noalloc.cu": [],
     "adjoint.cu": [],
     "collide.cu": ["--fmad=false"],
+    "mg.cu": [],
 }
 
 

@@ -56,15 +56,16 @@ WORKLOADS = {
                    params=dict(dt=4e-15, E0=1e10, w_sp=7.2e-4, capacity=3_000_000,
                                precision=PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
                    steps=500, target_sp=1_000_000),
-    # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, 6.4M tets with
+    # large tip: r = 5 nm, h = 90 nm in a 120x120x400 nm box, 7.92M tets with
     # this grading, 8 GV/m, work function 4.5 +/- 0.1 eV per face, 1e7 SPs,
     # 200 steps.  w_sp: a 200-step run of the CUDA path at w_sp = 7.2e-4 from an
     # empty start settles at 5.0e6 SPs in flight within 25 steps; rescaled to
-    # 1e7 (the oracle is too slow for this mesh)
+    # 1e7 (the oracle is too slow for this mesh).  The SPs in flight follow the
+    # emitted current, which depends on the tip surface, not on its faceting
     "tip_8m": dict(mesh=lambda: inputs.tip_mesh(radius=5e-9, height=90e-9, width=120e-9,
                                                  box_height=400e-9, h_fine=0.5e-9,
                                                  lateral_growth=1.12, h_lat_max=3e-9,
-                                                 h_shank=1.0e-9, h_top_max=4e-9,
+                                                 h_shank=0.75e-9, h_top_max=3.2e-9,
                                                  vertical_growth=1.1,
                                                  work_function_spread=0.1, seed=0),
                    params=dict(dt=4e-15, E0=8e9, w_sp=3.6e-4, capacity=30_000_000,

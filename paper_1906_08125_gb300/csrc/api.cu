@@ -98,6 +98,19 @@ struct pic_ctx_s {
     const long long *inv_off = nullptr;
     const float *agg_inv = nullptr;
     double *slice_r = nullptr, *agg_r = nullptr, *agg_z = nullptr;
+    // multigrid hierarchy of the resident solver (mg.cu; n1 == 0: none)
+    struct {
+        int n1 = 0, n2 = 0, max_l1_local = 0, max_l1_own = 0, max_l2_own = 0;
+        double lmax1 = 2.0;
+        int *agg0 = nullptr, *l1_off = nullptr, *l2_off = nullptr, *m0_ptr = nullptr,
+            *m0_idx = nullptr, *a1_ptr = nullptr, *a1_col = nullptr, *h1_ptr = nullptr,
+            *h1_idx = nullptr, *agg1 = nullptr, *m1_ptr = nullptr, *m1_idx = nullptr;
+        float *a1_val32 = nullptr, *dinv1_32 = nullptr, *a2inv = nullptr, *r2f = nullptr;
+        double *a1_val64 = nullptr, *dinv1_64 = nullptr, *r2d = nullptr;
+        float *g1f[2] = {nullptr, nullptr};
+        double *g1d[2] = {nullptr, nullptr};
+        unsigned long long *dtag1 = nullptr;
+    } mg;
     // replicas of a batch (1 for a single mesh)
     int n_rep = 1, n_rows = 0;
     int *tet_rep = nullptr, *face_rep = nullptr, *rep_face_off = nullptr;
@@ -439,7 +452,9 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.max_local = c->plan.max_local;
     g.cheb_degree = c->p.pcg_cheb_degree;
     g.cheb_b = c->cheb_b;
-    g.cheb_a = c->p.pcg_cheb_degree >= 2 ? c->cheb_b / c->p.pcg_cheb_ratio : 0.0;
+    g.cheb_a = (c->p.pcg_cheb_degree >= 2 || (c->cheb_local == 4 && c->mg.n1 > 0))
+                   ? c->cheb_b / c->p.pcg_cheb_ratio
+                   : 0.0;
     {
         // Chebyshev iteration on [a, b] (Saad, Alg. 12.1): theta, delta, sigma and
         // the recurrence rho_j = 1 / (2 sigma - rho_{j-1}), rho_0 = 1 / sigma
@@ -479,6 +494,55 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.rhs = nullptr;
     g.fD = c->fD;
     g.cheb_local = c->cheb_local;
+    if (c->mg.n1 > 0 && c->cheb_local == 4) {
+        g.mg_n1 = c->mg.n1;
+        g.mg_n2 = c->mg.n2;
+        g.mg_deg0 = MG_DEGREE0;
+        g.mg_deg1 = MG_DEGREE1;
+        g.mg_max_l1_local = c->mg.max_l1_local;
+        g.mg_max_l1_own = c->mg.max_l1_own;
+        g.mg_max_l2_own = c->mg.max_l2_own;
+        g.mg_smem_off = c->plan.mg_off;
+        g.mg_agg0 = c->mg.agg0;
+        g.mg_l1_off = c->mg.l1_off;
+        g.mg_l2_off = c->mg.l2_off;
+        g.mg_m0_ptr = c->mg.m0_ptr;
+        g.mg_m0_idx = c->mg.m0_idx;
+        g.mg_a1_ptr = c->mg.a1_ptr;
+        g.mg_a1_col = c->mg.a1_col;
+        g.mg_a1_val32 = c->mg.a1_val32;
+        g.mg_a1_val64 = c->mg.a1_val64;
+        g.mg_dinv1_32 = c->mg.dinv1_32;
+        g.mg_dinv1_64 = c->mg.dinv1_64;
+        g.mg_h1_ptr = c->mg.h1_ptr;
+        g.mg_h1_idx = c->mg.h1_idx;
+        g.mg_agg1 = c->mg.agg1;
+        g.mg_m1_ptr = c->mg.m1_ptr;
+        g.mg_m1_idx = c->mg.m1_idx;
+        g.mg_a2inv = c->mg.a2inv;
+        g.mg_r2f = c->mg.r2f;
+        g.mg_r2d = c->mg.r2d;
+        g.mg_dtag1 = (!fp64(c) && c->halo_sync == 1) ? c->mg.dtag1 : nullptr;
+        for (int k = 0; k < 2; ++k) {
+            g.mg_g1f[k] = c->mg.g1f[k];
+            g.mg_g1d[k] = c->mg.g1d[k];
+        }
+        // level-1 Chebyshev coefficients on [lmax1 / ratio, lmax1]
+        const double b1 = c->mg.lmax1, a1 = b1 / c->p.pcg_cheb_ratio;
+        const double theta = 0.5 * (b1 + a1), delta = 0.5 * (b1 - a1);
+        const double sigma = theta / delta;
+        double rho = 1.0 / sigma;
+        g.mg_inv_theta = 1.0 / theta;
+        g.mg_inv_thetaf = (float)g.mg_inv_theta;
+        for (int j = 0; j < 32; ++j) {
+            const double rho_new = 1.0 / (2.0 * sigma - rho);
+            g.mg_c1[j] = rho_new * rho;
+            g.mg_c2[j] = 2.0 * rho_new / delta;
+            g.mg_c1f[j] = (float)g.mg_c1[j];
+            g.mg_c2f[j] = (float)g.mg_c2[j];
+            rho = rho_new;
+        }
+    }
     g.coarse_inv = c->coarse_inv;
     g.coarse_r = c->coarse_r;
     g.agg_inv = c->cheb_local == 3 ? c->agg_inv : nullptr;
@@ -643,6 +707,52 @@ static bool spd_inverse(const std::vector<double> &A, int n, float *inv)
             inv[(size_t)i * n + c0] = (float)col[i];
     }
     return true;
+}
+
+// copy of a host vector into new device memory of element type T
+template <typename T, typename U>
+static int upload_vec(pic_ctx c, T **dst, const std::vector<U> &v)
+{
+    CK(dalloc(c, dst, v.size() + 1));
+    if (!v.empty()) {
+        std::vector<T> tmp(v.begin(), v.end());
+        CK(cudaMemcpy(*dst, tmp.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    }
+    return PIC_OK;
+}
+
+// the multigrid hierarchy on the device (tables, level-1 matrix in FP32 and
+// FP64, the level-2 inverse, exchange buffers)
+static int upload_mg(pic_ctx c, const MgHost &m)
+{
+    auto &d = c->mg;
+    int rc = 0;
+    if ((rc = upload_vec(c, &d.agg0, m.agg0)) || (rc = upload_vec(c, &d.l1_off, m.l1_off)) ||
+        (rc = upload_vec(c, &d.l2_off, m.l2_off)) || (rc = upload_vec(c, &d.m0_ptr, m.m0_ptr)) ||
+        (rc = upload_vec(c, &d.m0_idx, m.m0_idx)) || (rc = upload_vec(c, &d.a1_ptr, m.a1_ptr)) ||
+        (rc = upload_vec(c, &d.a1_col, m.a1_col)) || (rc = upload_vec(c, &d.h1_ptr, m.h1_ptr)) ||
+        (rc = upload_vec(c, &d.h1_idx, m.h1_idx)) || (rc = upload_vec(c, &d.agg1, m.agg1)) ||
+        (rc = upload_vec(c, &d.m1_ptr, m.m1_ptr)) || (rc = upload_vec(c, &d.m1_idx, m.m1_idx)) ||
+        (rc = upload_vec(c, &d.a1_val32, m.a1_val)) || (rc = upload_vec(c, &d.a1_val64, m.a1_val)) ||
+        (rc = upload_vec(c, &d.dinv1_32, m.dinv1)) || (rc = upload_vec(c, &d.dinv1_64, m.dinv1)) ||
+        (rc = upload_vec(c, &d.a2inv, m.a2inv)))
+        return rc;
+    CK(dalloc(c, &d.r2f, (size_t)m.n2));
+    CK(dalloc(c, &d.r2d, (size_t)m.n2));
+    for (int k = 0; k < 2; ++k) {
+        CK(dalloc(c, &d.g1f[k], (size_t)m.n1));
+        CK(dalloc(c, &d.g1d[k], (size_t)m.n1));
+    }
+    CK(dalloc(c, &d.dtag1, 2 * (size_t)m.n1));
+    // all-ones tags: no epoch (< 255) produces them
+    CK(cudaMemset(d.dtag1, 0xFF, sizeof(unsigned long long) * 2 * (size_t)m.n1));
+    d.n1 = m.n1;
+    d.n2 = m.n2;
+    d.max_l1_local = m.max_l1_local;
+    d.max_l1_own = m.max_l1_own;
+    d.max_l2_own = m.max_l2_own;
+    d.lmax1 = m.lmax1;
+    return PIC_OK;
 }
 
 // scratch of the binary collisions: per-cell counts, offsets and fill
@@ -1355,6 +1465,25 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
                 CK(dalloc(c, &c->coarse_r, (size_t)2 * G));   // sums of r, of A p
             }
         }
+        // multigrid hierarchy of the resident solver (pcg_cheb_local = 4)
+        c->mg = {};
+        if (c->plan.resident) {
+            MgHost mh;
+            bool ok = mg_build(sptr.data(), scol.data(), hv.data(), hd.data(), n_slices,
+                               c->plan.grid, MG_PASSES0, MG_PASSES1, MG_MAX_COARSE, &mh);
+            if (ok)
+                CK(pcg_plan_mg(&c->plan, c->p.precision, c->p.pcg_variant,
+                               mg_smem_bytes(mh, fp64(c) ? 8 : 4), &ok));
+            if (ok) {
+                int rc = upload_mg(c, mh);
+                if (rc)
+                    return rc;
+                // the V-cycle replaces the two-level Chebyshev preconditioner
+                // as the default of the polynomial-preconditioned solvers
+                if (c->cheb_local == 3)
+                    c->cheb_local = 4;
+            }
+        }
         // general kernels (batches, large systems): aggregates of
         // PCG_AGG_SLICES slices within each group, A0 of each group inverted
         c->agg_inv = nullptr;
@@ -1534,7 +1663,8 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     if (t->particle_blocks_per_sm < 1 || t->particle_blocks_per_sm > 64 || t->walk_form < 0 ||
         t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
-        t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 3 ||
+        t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 4 ||
+        (t->pcg_cheb_local == 4 && c->mg.n1 == 0) ||
         t->sort_cells < 0 || t->sort_cells > 1 || t->pcg_halo_sync < 0 || t->pcg_halo_sync > 1 ||
         t->wait_limit < 0 || t->wait_limit > (1 << 30) ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))

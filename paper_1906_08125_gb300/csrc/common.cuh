@@ -100,6 +100,14 @@ struct RunConst {
 // Device-side bookkeeping of one context.
 // slices per aggregate of the general solver's coarse correction
 constexpr int PCG_AGG_SLICES = 32;
+// multigrid hierarchy of the resident solver: pairwise-matching passes for
+// level 1 and level 2, the most level-2 rows (dense inverse), and the
+// Chebyshev smoothing degrees of the fine level and of level 1
+constexpr int MG_PASSES0 = 3;
+constexpr int MG_PASSES1 = 4;
+constexpr int MG_MAX_COARSE = 2048;
+constexpr int MG_DEGREE0 = 3;
+constexpr int MG_DEGREE1 = 3;
 
 // Step bookkeeping kept on the device, so that a whole step can be captured
 // in a CUDA graph and replayed: the index of the step being run (key of the
@@ -260,7 +268,59 @@ struct PcgArgs {
     double *slice_r, *agg_r, *agg_z;   // [n_slices], [n_agg], [n_agg]
     const double *rhs;        // null: f from W and the Neumann load; else f[row] = rhs[row]
     const double *fD;         // load of the prescribed Dirichlet values (rows)
+    // Multigrid V-cycle of the resident kernels (cheb_local == 4, mg_n1 > 0):
+    // level 1 aggregates the fine rows, level 2 the level-1 rows, every
+    // aggregate inside one block; Chebyshev smoothing of degree mg_deg0 on the
+    // fine level (the fine coefficients above) and mg_deg1 on level 1; level 2
+    // solved with a dense inverse.  Block b owns level-1 rows
+    // [mg_l1_off[b], mg_l1_off[b+1]) and level-2 rows [mg_l2_off[b], ..+1]).
+    int mg_n1, mg_n2, mg_deg0, mg_deg1;
+    int mg_max_l1_local, mg_max_l1_own, mg_max_l2_own;
+    size_t mg_smem_off;       // byte offset of the V-cycle's arrays in dynamic shared memory
+    const int *mg_agg0;       // [n_pad] fine row -> block-local level-1 row, -1 on padding
+    const int *mg_l1_off, *mg_l2_off;  // [G+1]
+    const int *mg_m0_ptr, *mg_m0_idx;  // [n1+1]: fine rows (block-local) of each level-1 row
+    const int *mg_a1_ptr, *mg_a1_col;  // level-1 matrix: CSR rows, block-local columns
+    const float *mg_a1_val32;
+    const double *mg_a1_val64;
+    const float *mg_dinv1_32;
+    const double *mg_dinv1_64;
+    const int *mg_h1_ptr, *mg_h1_idx;  // [G+1] / global level-1 rows of each block's halo
+    const int *mg_agg1;       // [n1] level-1 row -> block-local level-2 row
+    const int *mg_m1_ptr, *mg_m1_idx;  // [n2+1]: level-1 rows (block-local) of each level-2 row
+    const float *mg_a2inv;    // [n2*n2] inverse of the level-2 matrix, row-major
+    float *mg_r2f;            // [n2] level-2 right-hand side (FP32 kernels)
+    double *mg_r2d;           // [n2] (FP64 kernels)
+    unsigned long long *mg_dtag1;  // [2*n1] tagged level-1 exchange words
+    float *mg_g1f[2];         // [n1] level-1 exchange through a grid barrier (FP32)
+    double *mg_g1d[2];        // (FP64)
+    double mg_c1[32], mg_c2[32], mg_inv_theta;   // level-1 Chebyshev coefficients
+    float mg_c1f[32], mg_c2f[32], mg_inv_thetaf;
 };
+// Host-side product of mg_build: the multigrid hierarchy of the resident
+// solver (see mg.cu), with the layout of the PcgArgs fields above.
+struct MgHost {
+    int n1 = 0, n2 = 0;
+    std::vector<int> agg0, l1_off, l2_off, m0_ptr, m0_idx, a1_ptr, a1_col, h1_ptr, h1_idx;
+    std::vector<int> agg1, m1_ptr, m1_idx;
+    std::vector<double> a1_val, dinv1;
+    std::vector<float> a2inv;
+    double lmax1 = 2.0;
+    int max_l1_local = 0, max_l1_own = 0, max_l2_own = 0;
+};
+// Build the hierarchy from the fine matrix in sliced ELLPACK (host copies of
+// slice_ptr, columns, FP64 values and 1/diagonal, 0 on padding rows) split
+// over G blocks as the resident kernels split it: passes0 matching passes
+// for level 1, passes1 (more while it has over max_coarse rows) for level 2.
+// false when the hierarchy cannot be built (the caller keeps the other
+// preconditioners).
+bool mg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
+              int n_slices, int G, int passes0, int passes1, int max_coarse, MgHost *out);
+// dynamic shared memory of the V-cycle's arrays (bytes, elements of `elem` bytes)
+inline size_t mg_smem_bytes(const MgHost &m, size_t elem)
+{
+    return elem * ((size_t)m.max_l1_local + 4 * (size_t)m.max_l1_own + (size_t)m.max_l2_own) + 16;
+}
 struct PcgLaunch {
     int grid, block;
     int resident;          // 1: rows owned in registers, own segments in shared memory
@@ -272,6 +332,7 @@ struct PcgLaunch {
     int max_local;         // resident: most own rows + halo columns of one block
     int halo_symmetric;    // resident: block b reads block o's rows iff o reads b's
     int n_groups;          // general: independent systems (0: one system, whole grid)
+    size_t mg_off;         // resident with a multigrid hierarchy: where its shared arrays start
 };
 // Host-side tables: local column indices and halos of the resident kernels;
 // group tables of the general kernels when several systems are solved side
@@ -293,6 +354,10 @@ cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slice
 // the most blocks a batch solve can use (its partial-sum buffer is sized for it)
 int pcg_max_group_blocks(int precision, int num_sms);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
+// Grow a resident plan's dynamic shared memory by the multigrid arrays
+// (`extra` bytes); *ok = false (plan unchanged) when the block would no
+// longer fit on an SM.
+cudaError_t pcg_plan_mg(PcgLaunch *plan, int precision, int variant, size_t extra, bool *ok);
 
 // ---------------------------------------------------------------------------
 // adjoint (pic_adjoint)

@@ -292,8 +292,10 @@ __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool
             atomicAdd((unsigned long long *)&stats->crossings, (unsigned long long)sw);
         if (sr)
             atomicAdd((unsigned long long *)&stats->wrapped, (unsigned long long)sr);
-        if (mx)
+        if (mx) {
             atomicMax(&stats->max_walk, mx);
+            atomicAdd((unsigned long long *)&stats->walk_warp_iters, (unsigned long long)mx);
+        }
     }
 }
 
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(256) k_step_fused_persistent(
     R r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, lam[4] = {0, 0, 0, 0};
     int t = 0, entered = -1, steps = 0, wraps = 0;
     long long id = 0;
-    unsigned long long n_cross = 0;
+    unsigned long long n_cross = 0, n_iter = 0;
     unsigned n_col = 0, n_abs = 0, n_wrap = 0;
     int n_max = 0;
     for (;;) {
@@ -726,6 +728,7 @@ __global__ void __launch_bounds__(256) k_step_fused_persistent(
         if (!__any_sync(FULL_MASK, active))
             break;
         int fate = WALK_CONTINUE;
+        ++n_iter;
         if (active)
             fate = walk_step<R>(m, c.walk_max, r, t, entered, lam, steps, wraps);
         bool finished = active && fate != WALK_CONTINUE;
@@ -766,6 +769,8 @@ __global__ void __launch_bounds__(256) k_step_fused_persistent(
                 atomicAdd((unsigned long long *)&stats->wrapped, (unsigned long long)wr);
             if (mx)
                 atomicMax(&stats->max_walk, mx);
+            if (n_iter)
+                atomicAdd((unsigned long long *)&stats->walk_warp_iters, n_iter);
         }
     }
 }

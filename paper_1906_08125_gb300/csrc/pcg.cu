@@ -29,6 +29,8 @@
 // Every wait (grid barrier, tagged word) has an iteration limit: a block
 // that waits too long records PIC_ERR_TIMEOUT and the whole kernel returns.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -881,6 +883,7 @@ template <int RPT> struct Rows {
     int row[RPT], o[RPT], le[RPT], ge[RPT], wd[RPT];
     bool ok[RPT];
     mutable unsigned pub;   // tagged exchanges so far in this launch
+    mutable unsigned pub1;  // tagged exchanges of the multigrid level 1 so far
     unsigned epoch;         // this launch's epoch, < 255
 };
 
@@ -889,6 +892,7 @@ __device__ __forceinline__ void init_rows(Rows<RPT> &t, const PcgArgs &a, const 
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     t.pub = 0u;
+    t.pub1 = 0u;
     t.epoch = a.epoch ? (unsigned)ld_volatile_i32((const int *)a.epoch) : 0u;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -1059,12 +1063,365 @@ __device__ __forceinline__ void ride_gather(const PcgArgs &a, int set)
         ride_part()[RW] = v;
 }
 
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle preconditioner (cheb_local == 4; hierarchy of mg.cu).
+//
+//   z  = S0 r                       Chebyshev smoothing of degree k0 from zero
+//   r1 = P0^T (r - A z)             restriction: sums over the aggregates
+//   e1 = V1 r1                      the same cycle on level 1 (degree k1),
+//                                   with level 2 solved exactly: e2 = A2^-1 r2
+//   z += P0 e1                      prolongation (piecewise constant)
+//   z += S0 (r - A z)               smoothing of degree k0 from z
+//
+// S0 = p(D^-1 A) D^-1 is symmetric and the same on both sides, so the cycle is
+// a fixed symmetric positive definite operator and CG stays CG.  Aggregates
+// never cross blocks: restriction and prolongation are block-local; the
+// smoothing steps exchange halo values as the Chebyshev preconditioner does
+// (tagged words in FP32, grid barriers in FP64); the level-2 right-hand side
+// crosses one grid barrier, after which every block applies its own rows of
+// A2^-1.  Exchanges of the fine level: 2 k0; of level 1: 2 k1.
+// ---------------------------------------------------------------------------
+template <typename T> struct MgSm {
+    T *v;          // [own | halo] level-1 vector of the current exchange
+    T *r, *e, *rc, *d, *e2;
+    int L0, own1, h0, nh, Q0, own2;
+};
+
+template <typename T> __device__ __forceinline__ const T *mg_a1_val(const PcgArgs &a);
+template <> __device__ __forceinline__ const float *mg_a1_val<float>(const PcgArgs &a)
+{
+    return a.mg_a1_val32;
+}
+template <> __device__ __forceinline__ const double *mg_a1_val<double>(const PcgArgs &a)
+{
+    return a.mg_a1_val64;
+}
+template <typename T> __device__ __forceinline__ const T *mg_dinv1(const PcgArgs &a);
+template <> __device__ __forceinline__ const float *mg_dinv1<float>(const PcgArgs &a)
+{
+    return a.mg_dinv1_32;
+}
+template <> __device__ __forceinline__ const double *mg_dinv1<double>(const PcgArgs &a)
+{
+    return a.mg_dinv1_64;
+}
+
+// Level-1 halo exchange of src (own rows) into m.v [own | halo].  FP32 with
+// tagged words: the level's own count of exchanges and buffers (the halo
+// relation of the symmetric level-1 matrix is symmetric, checked on the
+// host), so the double-buffer argument of the fine exchange holds per level;
+// otherwise through a grid barrier and two alternating global buffers.
+template <typename T>
+__device__ bool mg_exchange1(const PcgArgs &a, const MgSm<T> &m, const T *src, unsigned &pub1,
+                             unsigned epoch)
+{
+    __syncthreads();
+    const unsigned par = pub1 & 1u;
+    if constexpr (sizeof(T) == 4) {
+        if (a.mg_dtag1) {
+            const unsigned tag = (epoch << 24) | (pub1 & 0xFFFFFFu);
+            unsigned long long *buf = a.mg_dtag1 + (size_t)par * a.mg_n1;
+            ++pub1;
+            for (int l = threadIdx.x; l < m.own1; l += blockDim.x) {
+                const float v = (float)src[l];
+                m.v[l] = v;
+                st_relaxed_u64(buf + m.L0 + l, (unsigned long long)__float_as_uint(v) |
+                                                    ((unsigned long long)tag << 32));
+            }
+            int bad = 0;
+            for (int i = threadIdx.x; i < m.nh && !bad; i += blockDim.x) {
+                const unsigned long long *q = buf + a.mg_h1_idx[m.h0 + i];
+                unsigned long long v = ld_relaxed_u64(q);
+                long long spins = 0;
+                while ((unsigned)(v >> 32) != tag) {
+                    ++spins;
+                    if (spins > a.spin_limit ||
+                        ((spins & 1023) == 0 && ld_volatile_i32(&a.st->err) == PIC_ERR_TIMEOUT)) {
+                        bad = 1;
+                        break;
+                    }
+                    v = ld_relaxed_u64(q);
+                }
+                m.v[m.own1 + i] = __uint_as_float((unsigned)v);
+            }
+            if (bad)
+                atomicCAS(&a.st->err, 0, PIC_ERR_TIMEOUT);
+            return __syncthreads_or(bad) == 0;
+        }
+    }
+    ++pub1;
+    T *gbuf;
+    if constexpr (sizeof(T) == 4)
+        gbuf = a.mg_g1f[par];
+    else
+        gbuf = a.mg_g1d[par];
+    for (int l = threadIdx.x; l < m.own1; l += blockDim.x) {
+        const T v = src[l];
+        m.v[l] = v;
+        gbuf[m.L0 + l] = v;
+    }
+    if (!grid_sync(a))
+        return false;
+    for (int i = threadIdx.x; i < m.nh; i += blockDim.x)
+        m.v[m.own1 + i] = __ldcg(gbuf + a.mg_h1_idx[m.h0 + i]);
+    __syncthreads();
+    return true;
+}
+
+// (A1 m.v) of the block's level-1 row l
+template <typename T>
+__device__ __forceinline__ T mg_a1_row(const PcgArgs &a, const MgSm<T> &m, int l)
+{
+    const T *val = mg_a1_val<T>(a);
+    const int k1 = __ldg(a.mg_a1_ptr + m.L0 + l + 1);
+    T s = (T)0;
+    for (int k = __ldg(a.mg_a1_ptr + m.L0 + l); k < k1; ++k)
+        s += __ldg(val + k) * m.v[__ldg(a.mg_a1_col + k)];
+    return s;
+}
+
+// Chebyshev smoothing on level 1 (degree mg_deg1), from zero (m.e = 0) or
+// from the current m.e: m.e += p(D1^-1 A1) D1^-1 (m.r - A1 m.e)
+template <typename T>
+__device__ bool mg_smooth1(const PcgArgs &a, const MgSm<T> &m, bool from_zero, unsigned &pub1,
+                           unsigned epoch)
+{
+    const T *dinv1 = mg_dinv1<T>(a);
+    const T it1 = cheb_coef<T>(a.mg_inv_theta, a.mg_inv_thetaf);
+    if (!from_zero && !mg_exchange1<T>(a, m, m.e, pub1, epoch))
+        return false;
+    for (int l = threadIdx.x; l < m.own1; l += blockDim.x) {
+        const T rc = from_zero ? m.r[l] : m.r[l] - mg_a1_row<T>(a, m, l);
+        const T d = __ldg(dinv1 + m.L0 + l) * rc * it1;
+        m.rc[l] = rc;
+        m.d[l] = d;
+        m.e[l] = from_zero ? d : m.e[l] + d;
+    }
+    for (int j = 1; j < a.mg_deg1; ++j) {
+        if (!mg_exchange1<T>(a, m, m.d, pub1, epoch))
+            return false;
+        const T c1 = cheb_coef<T>(a.mg_c1[j - 1], a.mg_c1f[j - 1]);
+        const T c2 = cheb_coef<T>(a.mg_c2[j - 1], a.mg_c2f[j - 1]);
+        for (int l = threadIdx.x; l < m.own1; l += blockDim.x) {
+            const T rc = m.rc[l] - mg_a1_row<T>(a, m, l);
+            const T d = c1 * m.d[l] + c2 * (__ldg(dinv1 + m.L0 + l) * rc);
+            m.rc[l] = rc;
+            m.d[l] = d;
+            m.e[l] = m.e[l] + d;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// The level-1 cycle on m.r into m.e (level 2 exact)
+template <typename T>
+__device__ bool mg_level1(const PcgArgs &a, const MgSm<T> &m, unsigned &pub1, unsigned epoch)
+{
+    if (!mg_smooth1<T>(a, m, true, pub1, epoch))
+        return false;
+    // residual r - A1 e = rc - A1 d_last
+    if (!mg_exchange1<T>(a, m, m.d, pub1, epoch))
+        return false;
+    for (int l = threadIdx.x; l < m.own1; l += blockDim.x)
+        m.rc[l] = m.rc[l] - mg_a1_row<T>(a, m, l);
+    __syncthreads();
+    // restriction to the block's level-2 rows, published for every block
+    T *r2;
+    if constexpr (sizeof(T) == 4)
+        r2 = a.mg_r2f;
+    else
+        r2 = a.mg_r2d;
+    for (int q = threadIdx.x; q < m.own2; q += blockDim.x) {
+        T s = (T)0;
+        const int k1 = __ldg(a.mg_m1_ptr + m.Q0 + q + 1);
+        for (int k = __ldg(a.mg_m1_ptr + m.Q0 + q); k < k1; ++k)
+            s += m.rc[__ldg(a.mg_m1_idx + k)];
+        r2[m.Q0 + q] = s;
+    }
+    if (!grid_sync(a))
+        return false;
+    // the block's rows of e2 = A2^-1 r2, one warp per row
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int n2 = a.mg_n2;
+        for (int q = w; q < m.own2; q += nw) {
+            const float *row = a.mg_a2inv + (size_t)(m.Q0 + q) * n2;
+            T s = (T)0;
+            for (int c = lane; c < n2; c += 32)
+                s += (T)__ldg(row + c) * __ldcg(r2 + c);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                s += __shfl_xor_sync(FULL_MASK, s, o);
+            if (lane == 0)
+                m.e2[q] = s;
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < m.own1; l += blockDim.x)
+        m.e[l] = m.e[l] + m.e2[__ldg(a.mg_agg1 + m.L0 + l)];
+    __syncthreads();
+    return mg_smooth1<T>(a, m, false, pub1, epoch);
+}
+
+// fine-level halo exchange of d into s_d (tagged words in FP32 when
+// available, otherwise own values to g_d, a grid barrier and the halo staged)
 template <int RPT, typename T>
+__device__ bool fine_exchange(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, T *s_d, T *g_d,
+                              const T (&d)[RPT])
+{
+    if (sizeof(T) == 4 && a.dtag[0])
+        return tagged_exchange_t<RPT, T>(t, a, g, s_d, d);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        s_d[t.o[k]] = d[k];
+        g_d[t.row[k]] = d[k];
+    }
+    if (!grid_sync(a))
+        return false;
+    stage_halo(s_d, (const T *)g_d, a, g);
+    __syncthreads();
+    return true;
+}
+
+template <int RPT, typename T>
+__device__ __forceinline__ T fine_row(const Rows<RPT> &t, int k, const int *LC, const T *VAL,
+                                      const T *s_v)
+{
+    T s = 0;
+#pragma unroll 4
+    for (int c = 0; c < t.wd[k]; ++c) {
+        int lc = LC[t.le[k] + c * 32];
+        s += VAL[t.le[k] + c * 32] * s_v[lc];
+    }
+    return s;
+}
+
+template <int RPT, typename T>
+__device__ bool mg_vcycle(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
+                          const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT], T (&z)[RPT],
+                          T *s_d0, T *s_d1, T *g_d0, T *g_d1)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    MgSm<T> m;
+    {
+        T *base = (T *)(smem + a.mg_smem_off);
+        m.v = base;
+        m.r = m.v + a.mg_max_l1_local;
+        m.e = m.r + a.mg_max_l1_own;
+        m.rc = m.e + a.mg_max_l1_own;
+        m.d = m.rc + a.mg_max_l1_own;
+        m.e2 = m.d + a.mg_max_l1_own;
+        const int b = blockIdx.x;
+        m.L0 = __ldg(a.mg_l1_off + b);
+        m.own1 = __ldg(a.mg_l1_off + b + 1) - m.L0;
+        m.h0 = __ldg(a.mg_h1_ptr + b);
+        m.nh = __ldg(a.mg_h1_ptr + b + 1) - m.h0;
+        m.Q0 = __ldg(a.mg_l2_off + b);
+        m.own2 = __ldg(a.mg_l2_off + b + 1) - m.Q0;
+    }
+    const T it0 = cheb_coef<T>(a.cheb_inv_theta, a.cheb_inv_thetaf);
+    T rc[RPT], d[RPT];
+    int par = 0;
+    // pre-smoothing from zero
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        rc[k] = r[k];
+        d[k] = dinv[k] * rc[k] * it0;
+        z[k] = d[k];
+    }
+    for (int j = 1; j < a.mg_deg0; ++j) {
+        T *sd = par ? s_d1 : s_d0;
+        T *gd = par ? g_d1 : g_d0;
+        par ^= 1;
+        if (!fine_exchange<RPT, T>(t, a, g, sd, gd, d))
+            return false;
+        cheb_update<RPT, T>(t, a, LC, VAL, dinv, sd, j, rc, d);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            z[k] = z[k] + d[k];
+    }
+    // the residual r - A z = rc - A d_last
+    {
+        T *sd = par ? s_d1 : s_d0;
+        T *gd = par ? g_d1 : g_d0;
+        par ^= 1;
+        if (!fine_exchange<RPT, T>(t, a, g, sd, gd, d))
+            return false;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (t.ok[k])
+                rc[k] = rc[k] - fine_row<RPT, T>(t, k, LC, VAL, sd);
+    }
+    // restriction: the residual of the own rows in the other buffer, summed
+    // over each aggregate in a fixed order
+    T *st = par ? s_d1 : s_d0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+        if (t.ok[k])
+            st[t.o[k]] = rc[k];
+    __syncthreads();
+    for (int l = threadIdx.x; l < m.own1; l += blockDim.x) {
+        T s = (T)0;
+        const int k1 = __ldg(a.mg_m0_ptr + m.L0 + l + 1);
+        for (int k = __ldg(a.mg_m0_ptr + m.L0 + l); k < k1; ++k)
+            s += st[__ldg(a.mg_m0_idx + k)];
+        m.r[l] = s;
+    }
+    __syncthreads();
+    if (!mg_level1<T>(a, m, t.pub1, t.epoch))
+        return false;
+    // prolongation
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        if (!t.ok[k])
+            continue;
+        const int l = __ldg(a.mg_agg0 + t.row[k]);
+        if (l >= 0)
+            z[k] = z[k] + m.e[l];
+    }
+    // post-smoothing from z
+    {
+        T *sd = par ? s_d1 : s_d0;
+        T *gd = par ? g_d1 : g_d0;
+        par ^= 1;
+        if (!fine_exchange<RPT, T>(t, a, g, sd, gd, z))
+            return false;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (!t.ok[k])
+                continue;
+            rc[k] = r[k] - fine_row<RPT, T>(t, k, LC, VAL, sd);
+            d[k] = dinv[k] * rc[k] * it0;
+            z[k] = z[k] + d[k];
+        }
+    }
+    for (int j = 1; j < a.mg_deg0; ++j) {
+        T *sd = par ? s_d1 : s_d0;
+        T *gd = par ? g_d1 : g_d0;
+        par ^= 1;
+        if (!fine_exchange<RPT, T>(t, a, g, sd, gd, d))
+            return false;
+        cheb_update<RPT, T>(t, a, LC, VAL, dinv, sd, j, rc, d);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            z[k] = z[k] + d[k];
+    }
+    return true;
+}
+
+template <int RPT, typename T, bool MG = false>
 __device__ bool apply_precond(const Rows<RPT> &t, const PcgArgs &a, const Seg &g, const int *LC,
                               const T *VAL, const T (&dinv)[RPT], const T (&r)[RPT],
                               T (&z)[RPT], T *s_d0, T *s_d1, T *g_d0, T *g_d1,
                               bool have_z0 = false, double z0_given = 0.0)
 {
+    if constexpr (MG && RPT <= 4) {
+        if (a.cheb_local == 4 && a.mg_n1 > 0)
+            return mg_vcycle<RPT, T>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, g_d0, g_d1);
+    }
     if (a.cheb_degree < 2) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
@@ -1314,7 +1671,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
         acc[2] += f[k] * f[k];
     }
     __syncthreads();
-    if (!apply_precond<RPT, double>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
+    if (!apply_precond<RPT, double, true>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
         return;
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -1385,7 +1742,7 @@ __global__ void __launch_bounds__(RB, 1) k_pcg64_res(PcgArgs a)
             x[k] = x[k] + alpha * p[k];
             r[k] = r[k] - alpha * ap[k];
         }
-        if (!apply_precond<RPT, double>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
+        if (!apply_precond<RPT, double, true>(t, a, g, LC, VAL, dinv, r, z, s_d0, s_d1, a.d0, a.d1))
             return;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
@@ -1509,7 +1866,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
     float z[RPT], p[RPT], ap[RPT];
     DF acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
     double tot[2];
-    if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1, a.d32_0,
+    if (!apply_precond<RPT, float, true>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1, a.d32_0,
                                    a.d32_1))
         return false;
 #pragma unroll
@@ -1582,7 +1939,7 @@ __device__ bool inner_standard(const Rows<RPT> &t, const In32<RPT> &m, const Pcg
             d[k] = d[k] + a32 * p[k];
             rv[k] = rv[k] - a32 * ap[k];
         }
-        if (!apply_precond<RPT, float>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1,
+        if (!apply_precond<RPT, float, true>(t, a, g, m.LC, m.VAL, m.dinv, rv, z, s_d0, s_d1,
                                        a.d32_0, a.d32_1, coarse_ride, z0))
             return false;
 #pragma unroll
@@ -2131,12 +2488,15 @@ __device__ __forceinline__ void pcg32ir_res(const PcgArgs &a)
         if (itol < a.inner_rtol)
             itol = a.inner_rtol;
         const int it0 = it;
-        bool good = PIPE     ? inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it)
-                    : single ? inner_single<RPT>(t, m, a, g, rv, d, s_a, s_d0, s_d1, itol, set, it)
-                    : merged ? inner_merged<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
-                                                 itol, set, it)
-                             : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
-                                                   itol, set, it);
+        bool good;
+        if constexpr (PIPE)
+            good = inner_pipelined<RPT>(t, m, a, g, rv, d, s_a, s_b, set, it);
+        else
+            good = single ? inner_single<RPT>(t, m, a, g, rv, d, s_a, s_d0, s_d1, itol, set, it)
+                   : merged ? inner_merged<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
+                                                itol, set, it)
+                            : inner_standard<RPT>(t, m, a, g, rv, d, s_a, s_b, s_c, s_d0, s_d1,
+                                                  itol, set, it);
         if (!good)
             return;
         if (it == it0) {   // no inner iteration: no progress possible
@@ -2197,6 +2557,24 @@ const void *pick_resident(int precision, int variant, int rpt, bool sm)
 }
 
 constexpr size_t SMEM_LIMIT = 200 * 1024;   // + static reduction buffers
+
+// The dynamic shared memory a kernel may take is a property of the function,
+// shared by every context: only ever raise it, so that a plan made for a
+// smaller system never breaks the launch of a larger one.
+static cudaError_t raise_smem_attr(const void *fn, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<const void *, size_t> set;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[fn];
+    if (bytes <= cur)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess)
+        cur = bytes;
+    return e;
+}
 
 // Row ownership, local column indices and halos of the resident kernels.
 static void build_halo(const int *slice_ptr, const int *col, int n_slices, int G, PcgHalo *h,
@@ -2343,8 +2721,7 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
         size_t bytes = (sm ? mat : 0) + vec;
         if (bytes <= SMEM_LIMIT) {
             const void *fn = pick_resident(precision, variant, rpt, sm);
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
+            cudaError_t e = raise_smem_attr(fn, bytes);
             int per_sm = 0;
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RB, bytes);
@@ -2382,6 +2759,36 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
     if (plan->grid > max_blocks)
         plan->grid = max_blocks;
     plan->block = PCG_BLOCK;
+    return cudaSuccess;
+}
+
+// dynamic shared memory a resident block may take with the multigrid arrays
+// (the static reduction buffers come on top; 227 KB per block in all)
+constexpr size_t SMEM_LIMIT_MG = 212 * 1024;
+
+cudaError_t pcg_plan_mg(PcgLaunch *plan, int precision, int variant, size_t extra, bool *ok)
+{
+    *ok = false;
+    if (!plan->resident || plan->rpt > 4)     // the V-cycle is compiled for up to 4 rows a thread
+        return cudaSuccess;
+    const size_t off = (plan->smem_bytes + 15) & ~(size_t)15;
+    const size_t bytes = off + extra;
+    if (bytes > SMEM_LIMIT_MG)
+        return cudaSuccess;
+    const void *fn = pick_resident(precision, variant, plan->rpt, plan->smem_matrix != 0);
+    cudaError_t e = raise_smem_attr(fn, bytes);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RB, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    if (per_sm < 1)
+        return cudaSuccess;
+    plan->mg_off = off;
+    plan->smem_bytes = bytes;
+    *ok = true;
     return cudaSuccess;
 }
 

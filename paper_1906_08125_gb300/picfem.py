@@ -56,7 +56,7 @@ class StepStats(C.Structure):
                 ("wrapped", C.c_int64), ("crossings", C.c_int64), ("alive", C.c_int64),
                 ("max_walk", C.c_int32), ("pcg_iters", C.c_int32), ("pcg_relres", C.c_double),
                 ("collected_charge", C.c_double), ("pcg_outer", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("walk_warp_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

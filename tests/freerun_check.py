@@ -129,6 +129,10 @@ class FreeRunCheck:
         self.checked = 0
         self.divergence_gap = []       # |r_G - r_O| at each explained cell divergence
         self.divergence_excess = []    # distance of each position from the other cell
+        # the first step after which the runs hold different SPs (an
+        # injection rounding flip or an exit one step apart): from then on
+        # the space charge of the two runs differs by whole SPs
+        self.first_event = None
 
     # geometry ----------------------------------------------------------------
     def lam(self, cell, r):
@@ -188,7 +192,10 @@ class FreeRunCheck:
         new_div = clean & ~same
         if new_div.any():
             d2 = np.linalg.norm(r_g[new_div] - r_o[new_div], axis=1)
-            e1 = self.excess(co[b][new_div], r_g[new_div])
+            # each position against the other run's cell, on the periodic
+            # image nearest that run's own position
+            r_g_at_o = self.nearest_image(r_g[new_div], ro[b][new_div])
+            e1 = self.excess(co[b][new_div], r_g_at_o)
             e2 = self.excess(cg[a][new_div], r_o[new_div])
             ok = (gap[new_div] <= self.tol) & (e1 <= d2 + self.eps) & (e2 <= d2 + self.eps)
             ids = common[new_div]
@@ -221,9 +228,18 @@ class FreeRunCheck:
                 j = nb & np.int64((1 << ID_QUAD_SHIFT) - 1)
                 R0 = np.array([O.uniform(self.seed, k, int(qq), 0, 0) for qq in q])
                 ok = injection_flip_explained(n_g[q], n_o[q], R0, j)
-                self._fail(k, f"injected in run {side} only, not a rounding flip", nb[~ok])
                 for x in nb[ok]:
                     self.flipped[int(x)] = k
+                # injected in both, but left the other run within its first
+                # step (an exit one step apart, below)
+                rest = nb[~ok]
+                if len(rest):
+                    pos = r_side[np.searchsorted(id_side, rest)]
+                    near = self.boundary_distance(pos) <= self.tol + self.eps
+                    self._fail(k, f"injected in run {side} only, not a rounding flip",
+                               rest[~near])
+                    for x in rest[near]:
+                        self.exited[int(x)] = k
             old = ids[~born]
             if len(old):
                 was_common = np.isin(old, self.prev_common, assume_unique=True)
@@ -237,6 +253,8 @@ class FreeRunCheck:
                     for x in old[near]:
                         self.exited[int(x)] = k
         self.prev_common = common
+        if self.first_event is None and (len(only_g) or len(only_o)):
+            self.first_event = k
 
     def summary(self):
         return {"steps": self.steps, "sp_steps_checked": self.checked,
@@ -244,4 +262,5 @@ class FreeRunCheck:
                 "exit_timing": len(self.exited), "max_err_clean_rel": self.max_err_clean / self.L[2],
                 "max_gap_at_divergence_rel": (max(self.divergence_gap) / self.L[2]
                                               if self.divergence_gap else 0.0),
+                "first_event_step": self.first_event,
                 "failures": self.failures[:10]}

@@ -34,15 +34,30 @@ def test_roofline_takes_the_dominant_kernel_and_the_measured_peak(monkeypatch):
     res = dict(info=INFO, stats=st, prof={"pcg": (3, 2.0), "step_fused": (3, 1.0)},
                prev_alive=np.array([100, 100, 100]), params={"pcg_cheb_degree": 6})
     roof, k = bench.roofline(res, fp64=False)
-    alg = sum(bench.bytes_pcg(r, INFO, False, 6) for r in st)
+    alg = sum(bench.bytes_pcg_min(r, INFO, False) for r in st)
+    alg_pre = sum(bench.bytes_pcg(r, INFO, False, 6) for r in st)
     assert roof["kernel"] == "pcg" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
     assert roof["achieved"] == pytest.approx(alg / 2.0e-3 / 1e9, abs=0.051)   # 0.1 GB/s steps
     assert roof["peak"] == 6000.0 and roof["peak_source"] == "measured"
     assert roof["frac"] == pytest.approx(roof["achieved"] / 6000.0, abs=1e-4)
+    assert roof["alg_frac_incl_precond"] == pytest.approx(alg_pre / 2.0e-3 / 1e9 / 6000.0,
+                                                          abs=1e-4)
     assert roof["traffic"] == 12345
     assert k["pcg"]["share"] == pytest.approx(2.0 / 3.0, abs=1e-4)
     assert k["pcg"]["alg_bytes_per_launch"] == int(alg / 3)
     assert k["step_fused"]["launches"] == 3
+
+
+def test_minimal_solver_bytes_follow_the_scope_table():
+    """One SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n) with s
+    the value bytes, plus, in the FP32 form, 12 nnz + 24 n per refinement."""
+    row = stats(1, iters=93, outer=2)[0]
+    n, nnz = INFO["n_free"], INFO["nnz"]
+    assert bench.bytes_pcg_min(row, INFO, True) == 93 * (nnz * 12 + 4 * (n + 1) + 80 * n)
+    assert bench.bytes_pcg_min(row, INFO, False) == (93 * (nnz * 8 + 4 * (n + 1) + 80 * n)
+                                                     + 2 * (12 * nnz + 24 * n))
+    # never more than the count with every preconditioner SpMV
+    assert bench.bytes_pcg_min(row, INFO, False) <= bench.bytes_pcg(row, INFO, False, 6)
 
 
 def test_solver_byte_model_structure():

@@ -39,7 +39,7 @@ def oracle_state(oracle_mod, tip1m):
     sample population deposited and its potential solved tightly."""
     mesh, p = tip1m
     orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-11,
-                                       pcg_max_iter=50000))
+                                       pcg_max_iter=50000), parallel=True)
     orc.init_potential()
     phi0 = orc.potential()
     parts = inputs.random_particles(mesh, N_SAMPLE, seed=77, v_scale=3e6, v_up=1.5e7)
@@ -96,7 +96,7 @@ def test_one_bench_step_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
     orc, phi0, parts = oracle_state
     phi_start = orc.potential()
     o2 = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-11,
-                                      pcg_max_iter=50000))
+                                      pcg_max_iter=50000), parallel=True)
     o2.set_potential(phi_start)
     o2.set_particles(*parts)
     o2.step_index = 5
@@ -123,44 +123,109 @@ def test_one_bench_step_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
     assert rel(ctx.potential(), o2.potential()) <= 1e-6
 
 
-FREE_STEPS = int(os.environ.get("PIC_PARITY_TIP_STEPS", "20"))
+TF_STEPS = int(os.environ.get("PIC_PARITY_TIP_STEPS", "20"))
 
 
-def test_free_running_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
+def test_teacher_forced_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
     """The benchmark's configuration (FP32 push, FP32 Chebyshev-PCG inside
     FP64 refinement to the benchmark's 1e-6, fused pic_step) against the FP64
-    oracle (rtol 1e-10), both running free from identical state (the oracle's
-    tight potential and the seeded 2e5-SP sample) for FREE_STEPS steps
-    (PIC_PARITY_TIP_STEPS; 20 by default): the potential within 1e-6 every
-    step, every SP within 1e-5 of the box height of the oracle's at every
-    step unless tests/freerun_check.py explains it (a cell flip at a face
-    while the positions still agreed, an injection count on the other side
-    of a rounding threshold, an exit one step apart near Gamma_1/Gamma_3)."""
+    oracle (rtol 1e-10) over TF_STEPS steps (PIC_PARITY_TIP_STEPS; 20 by
+    default) of the evolving sample population, each step started from the
+    oracle's state: every SP within 1e-5 of the box height, every differing
+    cell, injection count and exit explained by tests/freerun_check.py, the
+    new potential within 1e-6, and exact charge conservation."""
     from freerun_check import FreeRunCheck
     mesh, p = tip1m
     orc0, phi0, parts = oracle_state
-    phi_start = orc0.potential()
     orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-10,
-                                       pcg_max_iter=50000))
-    orc.set_potential(phi_start)
+                                       pcg_max_iter=50000), parallel=True)
+    orc.set_potential(orc0.potential())
     orc.set_particles(*parts)
     ctx = picfem.Context(p).mesh_load(mesh)
-    ctx.set_potential(phi_start)
-    ctx.set_particles(*parts)
-    chk = FreeRunCheck(mesh, orc, p["seed"])
-    worst = 0.0
-    for _ in range(FREE_STEPS):
+    worst, flips, div, checked = 0.0, 0, 0, 0
+    for _ in range(TF_STEPS):
         k = orc.step_index
-        assert ctx.step_index == k
+        ctx.set_potential(orc.potential())
+        ctx.set_particles(*orc.particles())
+        ctx.step_index = k
         E_g, E_o = ctx.field(), orc.field()
         ctx.step(1)
         orc.step(1)
-        chk.step(k, ctx.particles(), orc.particles(), E_g, E_o)
+        chk = FreeRunCheck(mesh, orc, p["seed"])
+        g = ctx.particles()
+        chk.step(k, g, orc.particles(), E_g, E_o)
+        assert not chk.failures, (k, chk.summary())
+        s = chk.summary()
+        flips += s["injection_flips"]
+        div += s["cell_divergences"]
+        checked += s["sp_steps_checked"]
+        assert int(ctx.charge().sum()) == len(g[3]) * 2 ** 32
         worst = max(worst, rel(ctx.potential(), orc.potential()))
-    s = chk.summary()
-    print(f"tip_1m FP32+IR free-running {FREE_STEPS} steps:", s, "potential", worst)
+    print(f"tip_1m FP32+IR teacher-forced {TF_STEPS} steps: {checked} SP-steps, "
+          f"{div} face flips, {flips} injection flips, potential {worst:.2e}")
     assert worst <= 1e-6
-    assert not chk.failures, s
+
+
+SENS_STEPS = int(os.environ.get("PIC_SENS_TIP_STEPS", "8"))
+
+
+def test_free_running_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
+    """Free-running from identical state.  Until the first step in which the
+    runs hold different SPs (an injection count on the other side of a
+    rounding threshold, or an exit one step apart), every SP within 1e-5 of
+    the box height and every difference explained by tests/freerun_check.py.
+    After it the space charges differ by whole SPs, and SPs near the apex
+    cross the box in a step or two, so any two correct runs part ways: the
+    benchmark's form (rtol 1e-6) against the oracle (rtol 1e-10) is held to
+    the spread of the oracle itself when its state is rounded to FP32 after
+    every step and it solves to the benchmark's 1e-6 -- at every step at
+    most ten times the fraction of SPs beyond 1e-5 of the box height (plus
+    1e-3) and ten times the 99.9th percentile of the distance (plus 1e-5)."""
+    from freerun_check import FreeRunCheck
+    mesh, p = tip1m
+    orc0, phi0, parts = oracle_state
+    L = mesh.box_hi - mesh.box_lo
+
+    def start(rtol):
+        o = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=rtol,
+                                         pcg_max_iter=50000), parallel=True)
+        o.set_potential(orc0.potential())
+        o.set_particles(*parts)
+        return o
+
+    ref, r32 = start(1e-10), start(1e-6)
+    ctx = picfem.Context(p).mesh_load(mesh)
+    ctx.set_potential(orc0.potential())
+    ctx.set_particles(*parts)
+    chk = FreeRunCheck(mesh, ref, p["seed"])
+
+    def spread(x, y):
+        common, ix, iy = np.intersect1d(x[3], y[3], return_indices=True)
+        d = x[0][ix] - y[0][iy]
+        d[:, :2] -= L[:2] * np.round(d[:, :2] / L[:2])
+        e = np.abs(d).max(axis=1) / L[2]
+        return float(np.mean(e > 1e-5)), float(np.quantile(e, 0.999))
+
+    rows = []
+    for _ in range(SENS_STEPS):
+        k = ref.step_index
+        E_g, E_o = ctx.field(), ref.field()
+        ctx.step(1)
+        ref.step(1)
+        r32.step(1)
+        r, v, c, i = r32.particles()
+        r32.set_particles(r.astype(np.float32).astype(np.float64),
+                          v.astype(np.float32).astype(np.float64), c, i)
+        g, o = ctx.particles(), ref.particles()
+        if chk.first_event is None:
+            chk.step(k, g, o, E_g, E_o)
+            assert not chk.failures, (k, chk.summary())
+        rows.append((k,) + spread(g, o) + spread(r32.particles(), o))
+    print(f"tip_1m FP32+IR free-running: strict until step {chk.first_event}",
+          chk.summary(), "spread (step, GPU frac, GPU q999, oracle-FP32 frac, q999):", rows)
+    for k, gf, gq, of, oq in rows:
+        assert gf <= 10 * of + 1e-3, rows
+        assert gq <= 10 * oq + 1e-5, rows
 
 
 def test_fp64_split_step_bit_exact_full_size(picfem, oracle_mod, tip1m, oracle_state):
@@ -169,7 +234,7 @@ def test_fp64_split_step_bit_exact_full_size(picfem, oracle_mod, tip1m, oracle_s
     mesh, p = tip1m
     orc, phi0, parts = oracle_state
     pp = dict(p, precision=K.PREC_FP64, pcg_cheb_degree=0)
-    o2 = oracle_mod.Oracle(mesh, pp)
+    o2 = oracle_mod.Oracle(mesh, pp, parallel=True)
     o2.set_potential(orc.potential())
     o2.set_particles(*parts)
     ctx = picfem.Context(pp).mesh_load(mesh)

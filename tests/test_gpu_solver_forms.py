@@ -1,8 +1,10 @@
 """The inner FP32 solver forms of the FP32_IR Poisson solve (PIC_PCG_*)
 against the oracle's tight FP64 solve: standard and merged (p.Ap summed on
 the Chebyshev polynomial's first grid barrier, one barrier fewer per
-iteration) with Jacobi, the whole-matrix Chebyshev polynomial and the
-polynomial with the coarse correction; pipelined (Jacobi only) on the
+iteration) with Jacobi, the whole-matrix Chebyshev polynomial, the
+polynomial with the coarse correction and the multigrid V-cycle (where the
+merged form does not apply it runs the standard one); the V-cycle in FP64;
+pipelined (Jacobi only) on the
 uniform plate, since its FP32 recurrences stagnate on the graded tip.  Every
 form reaches the requested tolerance; the merged form takes the iterations
 of the standard one, and where it does not apply (Jacobi, block-local
@@ -47,15 +49,17 @@ def oracle_phi(oracle_mod, tip_small):
 
 PRECONDS = {"jacobi": dict(pcg_cheb_degree=0),
             "chebyshev": dict(pcg_cheb_degree=6),
-            "chebyshev+coarse": dict(pcg_cheb_degree=6)}
+            "chebyshev+coarse": dict(pcg_cheb_degree=6),
+            "multigrid": dict(pcg_cheb_degree=6)}
+LOCAL = {"chebyshev": 0, "chebyshev+coarse": 3, "multigrid": 4}
 
 
 def solve(picfem, mesh, parts, variant, precond, rtol=1e-8):
     p = K.params(E0=1e10, w_sp=0.5, capacity=100_000, precision=K.PREC_FP32_IR,
                  pcg_rtol=rtol, pcg_variant=variant, **PRECONDS[precond])
     c = picfem.Context(p).mesh_load(mesh)
-    if precond == "chebyshev":
-        c.set_tuning(pcg_cheb_local=0)      # the polynomial alone
+    if precond in LOCAL:
+        c.set_tuning(pcg_cheb_local=LOCAL[precond])
     assert c.info()["pcg_resident"] == 1
     it0, rr0 = c.init_potential()
     phi0 = c.potential()
@@ -156,7 +160,7 @@ def test_merged_fused_steps_match_standard(picfem, tip_small):
 
 
 @pytest.mark.parametrize("variant", [K.PCG_STANDARD, K.PCG_MERGED])
-@pytest.mark.parametrize("local", [0, 3])
+@pytest.mark.parametrize("local", [0, 3, 4])
 def test_tagged_exchange_equals_grid_barrier(picfem, tip_small, oracle_phi, variant, local):
     """The Chebyshev steps' neighbour exchange through tagged words
     (pcg_halo_sync = 1) moves the same values in the same order as the grid
@@ -272,3 +276,31 @@ def test_single_reduction_fused_steps(picfem, tip_small):
     assert np.array_equal(res["single"][2], res["std"][2])
     assert np.abs(res["single"][0] - res["std"][0]).max() <= 1e-6 * np.abs(res["std"][0]).max()
     assert rel(res["single"][3], res["std"][3]) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [K.PREC_FP64, K.PREC_FP32_IR])
+def test_multigrid_against_the_oracle(picfem, tip_small, oracle_phi, precision):
+    """The multigrid V-cycle (pcg_cheb_local = 4, the default where the
+    hierarchy is built) in both precisions: the oracle's potentials to the
+    requested tolerance, in fewer CG iterations than the two-level
+    Chebyshev form, and the same result whether its exchanges go through
+    tagged words or grid barriers."""
+    phi0_o, phi1_o, parts = oracle_phi
+    rtol = 1e-11 if precision == K.PREC_FP64 else 1e-8
+    its = {}
+    for local in (3, 4):
+        p = K.params(E0=1e10, w_sp=0.5, capacity=100_000, precision=precision, pcg_rtol=rtol,
+                     pcg_cheb_degree=6)
+        c = picfem.Context(p).mesh_load(tip_small)
+        assert c.tuning()["pcg_cheb_local"] == 4           # the default
+        c.set_tuning(pcg_cheb_local=local)
+        it0, rr0 = c.init_potential()
+        assert rel(c.potential(), phi0_o) <= (1e-9 if precision == K.PREC_FP64 else 1e-7)
+        c.set_particles(*parts)
+        c.deposit()
+        it1, rr1 = c.poisson_solve()
+        assert max(rr0, rr1) <= rtol
+        assert rel(c.potential(), phi1_o) <= (1e-9 if precision == K.PREC_FP64 else 1e-7)
+        its[local] = it0 + it1
+        c.close()
+    assert its[4] < its[3], its
