@@ -162,14 +162,30 @@ def bench_population(mesh, n, seed):
 # ---------------------------------------------------------------------------
 # algorithmic bytes per launch
 # ---------------------------------------------------------------------------
-def bytes_step_fused(st_prev_alive, st, s, rec):
+def bytes_step_fused(st_prev_alive, st, s, info):
+    """Algorithmic bytes of one fused particle step: the SoA state of the SPs
+    read and written, N (6s + 4 + 8) each way; per face crossing of the walk
+    the neighbour table and J^-1 of the next tetrahedron, 16 + 12 s; per
+    occupied tetrahedron its record and field, 16 + 4*8 + 12 s (the occupied
+    tetrahedra bounded by min(T, N)); the node charge written, 2 * 8 per
+    node; 64 bytes per emitted SP."""
     n_old = st_prev_alive
     n_new = int(st["injected"])
-    alive = int(st["alive"])
     X = int(st["crossings"])
-    state = 6 * s + 12
-    return (n_old * state + alive * state + (n_old + n_new + X) * rec + n_old * 4 * s
-            + alive * 16 + n_new * 64)
+    n = n_old + n_new
+    t_occ = min(info["n_tets"], n)
+    return (n * 2 * (6 * s + 4 + 8) + X * (16 + 12 * s) + t_occ * (16 + 4 * 8 + 12 * s)
+            + 2 * info["n_nodes"] * 8 + 64 * n_new)
+
+
+def bytes_step_fused_compulsory(st_prev_alive, st, s, info, rec):
+    """DRAM bytes one fused particle step cannot avoid: the SoA state read
+    and written once, each walk record and field of the tetrahedra touched
+    (at most all of them) once, the node charge written once."""
+    n = st_prev_alive + int(st["injected"])
+    alive = int(st["alive"])
+    touched = min(info["n_tets"], n + int(st["crossings"]))
+    return n * (6 * s + 12) + alive * (6 * s + 12) + touched * (rec + 4 * s) + 8 * info["n_nodes"]
 
 
 def bytes_pcg(st, info, fp64, cheb):
@@ -352,7 +368,7 @@ def roofline(res, fp64):
     rec = 128 if fp64 else 64
     cheb = res["params"].get("pcg_cheb_degree", 0)
     alg = {
-        "step_fused": sum(bytes_step_fused(int(pa), row, s, rec) for pa, row in zip(prev, st)),
+        "step_fused": sum(bytes_step_fused(int(pa), row, s, info) for pa, row in zip(prev, st)),
         "pcg": sum(bytes_pcg_min(row, info, fp64) for row in st),
         "field": len(st) * bytes_field(info, s, rec),
         "inject_count": len(st) * bytes_inject_count(info, s),
@@ -377,6 +393,18 @@ def roofline(res, fp64):
     roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": peak, "unit": "GB/s",
             "frac": round(a / peak, 4) if a else None, "traffic": ncu_traffic(dom, WORKLOAD),
             "peak_source": kind}
+    if dom == "step_fused":
+        ms = kernels["step_fused"]["ms"]
+        comp = sum(bytes_step_fused_compulsory(int(pa), row, s, info, rec)
+                   for pa, row in zip(prev, st))
+        roof["bytes_model"] = ("N 2 (6s + 12) + X (16 + 12 s) + T_occ (48 + 12 s) + 16 N_nodes "
+                               "+ 64 per new SP, X = face crossings (counted)")
+        roof["limiter"] = ("latency of the dependent walk-record fetches (one per face "
+                           "crossing, served from L1/L2 for neighbouring SPs)")
+        roof["compulsory"] = {"bytes_per_launch": int(comp / kernels["step_fused"]["launches"]),
+                              "achieved": round(comp / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                              "frac": round(comp / (ms * 1e-3) / 1e9 / peak, 4),
+                              "model": "each SP state and each touched record once"}
     if dom == "pcg":
         ms = kernels["pcg"]["ms"]
         roof["bytes_model"] = ("one SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n), "
@@ -439,9 +467,10 @@ def run_ensemble(n_rep, steps, warmup):
     P.load()
     b, cat = ensemble_inputs(n_rep)
     peak, kind = peaks()
+    # (the batched FP64 solve is Jacobi-PCG: the general FP64 kernels take no
+    # polynomial preconditioner)
     forms = {"fp32_ir": dict(precision=K.PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
-             "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0),
-             "fp64_twolevel": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=6)}
+             "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0)}
     sequential_forms = ("fp32_ir", "fp64")
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {"replicas": n_rep, "tets": int(b.mesh.n_tets), "nodes": int(b.mesh.n_nodes),

@@ -227,7 +227,11 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           FP32 coherent warps), 1 coherent warps (a warp
  *                           walks 32 consecutive SPs to the end), 2 persistent
  *                           lanes (a lane takes the next SP from its warp's
- *                           queue); the SP results are identical
+ *                           queue), 3 rounds (a warp walks a contiguous range
+ *                           of the SPs, shared out evenly over the warps, in
+ *                           rounds of at most 16 face crossings, lanes that
+ *                           finished taking the range's next SPs after each
+ *                           round); the SP results are identical
  *   pcg_blocks_per_sm       batch solve (mesh_load_batch): at most this many
  *                           blocks per SM (0 = as many as fit; 0..64); the
  *                           one-system solver ignores it

@@ -1019,6 +1019,10 @@ int or_push_relocate(or_ctx *c, int64_t step, or_stats *st)
     int64_t collected = 0, absorbed = 0, wraps = 0, crossings = 0;
     int32_t max_walk = 0;
     int64_t out = 0;
+    int status = OR_OK;
+    /* every SP on its own (kick, drift, walk), in place ... */
+    int8_t *fate = malloc((size_t)c->np + 1);
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : wraps, crossings) reduction(max : max_walk)
     for (int64_t k = 0; k < c->np; ++k) {
         double *r = c->r + 3 * k, *v = c->v + 3 * k;
         if (k < n_old) {
@@ -1028,32 +1032,48 @@ int or_push_relocate(or_ctx *c, int64_t step, or_stats *st)
         }
         for (int i = 0; i < 3; ++i)
             r[i] = r[i] + dt * v[i];
-        int fate = 0;
+        int fa = 0;
         int32_t len = 0;
         int32_t t = c->cell[k];
-        int s = walk(c, r, &t, &fate, &len, &wraps);
-        if (s != OR_OK)
-            return s;
+        int64_t w = 0;
+        int s = walk(c, r, &t, &fa, &len, &w);
+        if (s != OR_OK) {
+#pragma omp atomic write
+            status = s;
+            fa = FATE_ALIVE;
+        }
+        wraps += w;
         crossings += len;
         if (len > max_walk)
             max_walk = len;
-        if (fate == FATE_COLLECTED) {
+        c->cell[k] = t;
+        fate[k] = (int8_t)fa;
+    }
+    if (status != OR_OK) {
+        free(fate);
+        return status;
+    }
+    /* ... then the survivors kept in order */
+    for (int64_t k = 0; k < c->np; ++k) {
+        if (fate[k] == FATE_COLLECTED) {
             ++collected;
             continue;
         }
-        if (fate == FATE_ABSORBED) {
+        if (fate[k] == FATE_ABSORBED) {
             ++absorbed;
             continue;
         }
-        /* keep, in order */
-        for (int i = 0; i < 3; ++i) {
-            c->r[3 * out + i] = r[i];
-            c->v[3 * out + i] = v[i];
+        if (out != k) {
+            for (int i = 0; i < 3; ++i) {
+                c->r[3 * out + i] = c->r[3 * k + i];
+                c->v[3 * out + i] = c->v[3 * k + i];
+            }
+            c->cell[out] = c->cell[k];
+            c->id[out] = c->id[k];
         }
-        c->cell[out] = t;
-        c->id[out] = c->id[k];
         ++out;
     }
+    free(fate);
     c->np = out;
     c->n_fresh = 0;
     if (st) {
@@ -1076,6 +1096,7 @@ int or_deposit(or_ctx *c)
     int S = c->p.quant_bits;
     int64_t one = (int64_t)1 << S;
     memset(c->W, 0, sizeof(int64_t) * (size_t)c->n_nodes);
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < c->np; ++k) {
         double lam[4];
         int32_t t = c->cell[k];

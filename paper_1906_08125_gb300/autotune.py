@@ -24,7 +24,7 @@ import numpy as np
 
 SPACE = {
     "particle_blocks_per_sm": (2, 4, 8, 16),
-    "walk_form": (1, 2),
+    "walk_form": (1, 2, 3),
     "pcg_blocks_per_sm": (0, 1, 2, 4),
     "pcg_cheb_degree": (0, 4, 6, 8),
     "pcg_balance": (0, 1),

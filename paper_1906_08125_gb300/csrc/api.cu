@@ -1661,7 +1661,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     if (!c || !t)
         return fail(c, PIC_ERR_ARG, "null argument");
     if (t->particle_blocks_per_sm < 1 || t->particle_blocks_per_sm > 64 || t->walk_form < 0 ||
-        t->walk_form > 2 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
+        t->walk_form > 3 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 4 ||
         (t->pcg_cheb_local == 4 && c->mg.n1 == 0) ||

@@ -176,8 +176,8 @@ template <typename R>
 cudaError_t launch_deposit(cudaStream_t s, int grid, MeshView<R> m, RunConst c,
                            Particles<R> A, int a, DevState *st, unsigned long long *W);
 // walk_form: WALK_FORM_AUTO (persistent lanes for FP64, coherent warps for
-// FP32), WALK_FORM_COHERENT or WALK_FORM_PERSISTENT
-enum { WALK_FORM_AUTO = 0, WALK_FORM_COHERENT = 1, WALK_FORM_PERSISTENT = 2 };
+// FP32), WALK_FORM_COHERENT, WALK_FORM_PERSISTENT or WALK_FORM_ROUNDS
+enum { WALK_FORM_AUTO = 0, WALK_FORM_COHERENT = 1, WALK_FORM_PERSISTENT = 2, WALK_FORM_ROUNDS = 3 };
 template <typename R>
 cudaError_t launch_step_fused(cudaStream_t s, int grid, int walk_form, MeshView<R> m, RunConst c,
                               const long long *step, int nq, const long long *qoff, Particles<R> A,

@@ -274,7 +274,7 @@ __device__ __forceinline__ long long append(bool alive, const R r[3], const R v[
 }
 
 __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool act,
-                                            pic_step_stats *stats)
+                                            pic_step_stats *stats, bool warp_iters = true)
 {
     if (!stats)
         return;
@@ -294,7 +294,8 @@ __device__ __forceinline__ void count_fates(int fate, int steps, int wraps, bool
             atomicAdd((unsigned long long *)&stats->wrapped, (unsigned long long)sr);
         if (mx) {
             atomicMax(&stats->max_walk, mx);
-            atomicAdd((unsigned long long *)&stats->walk_warp_iters, (unsigned long long)mx);
+            if (warp_iters)
+                atomicAdd((unsigned long long *)&stats->walk_warp_iters, (unsigned long long)mx);
         }
     }
 }
@@ -775,6 +776,83 @@ __global__ void __launch_bounds__(256) k_step_fused_persistent(
     }
 }
 
+// Rounds form: each warp owns a contiguous range of the buffer -- the SPs
+// shared out evenly over the warps of the launch, in multiples of 32 -- and
+// walks them in rounds of at most ROUND_STEPS face crossings; after every
+// round the lanes whose SP has finished start the next SPs of the range, in
+// order.  A lane then idles at most one round behind the warp's slowest walk
+// instead of the whole walk, the per-crossing loop stays the tight loop of
+// the coherent form (no warp vote per crossing), and the SPs in flight in a
+// warp stay neighbours in the buffer (ordered by cell), so they keep sharing
+// walk records in L1.
+constexpr int ROUND_STEPS = 16;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_step_fused_rounds(
+    MeshView<R> m, RunConst c, const long long *stepp, int nq, const long long *__restrict__ qoff,
+    Particles<R> A, Particles<R> B, int a, DevState *st, unsigned long long *W,
+    pic_step_stats *stats)
+{
+    const long long step = *stepp;
+    const long long n_old = (long long)st->cnt[a];
+    const long long n = n_old + st->n_new;
+    unsigned long long *cntB = &st->cnt[1 - a];
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long chunk = 32 * ((n + 32 * nwarps - 1) / (32 * nwarps));
+    unsigned long long n_iter = 0;
+    for (long long c0 = wid * chunk; c0 < n; c0 += nwarps * chunk) {
+        const long long c1 = c0 + chunk < n ? c0 + chunk : n;
+        long long next = c0;   // warp-uniform: the next SP of the range to start
+        bool active = false;
+        R r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, lam[4] = {0, 0, 0, 0};
+        int t = 0, entered = -1, steps = 0, wraps = 0;
+        long long id = 0;
+        for (;;) {
+            const unsigned idle = __ballot_sync(FULL_MASK, !active);
+            const long long avail = c1 - next;
+            const int take = avail < (long long)__popc(idle) ? (int)avail : __popc(idle);
+            if (!active) {
+                const int rank = __popc(idle & lower);
+                if (rank < take) {
+                    start_sp<R>(m, c, step, nq, qoff, A, n_old, next + rank, st, r, v, t, id);
+                    entered = -1;
+                    steps = 0;
+                    wraps = 0;
+                    active = true;
+                }
+            }
+            next += take;
+            if (!__any_sync(FULL_MASK, active))
+                break;
+            int fate = WALK_CONTINUE;
+            const int s0 = steps;
+            if (active) {
+                for (int k = 0; k < ROUND_STEPS; ++k) {
+                    fate = walk_step<R>(m, c.walk_max, r, t, entered, lam, steps, wraps);
+                    if (fate != WALK_CONTINUE)
+                        break;
+                }
+            }
+            n_iter += __reduce_max_sync(FULL_MASK, active ? (unsigned)(steps - s0) : 0u);
+            const bool finished = active && fate != WALK_CONTINUE;
+            if (finished && fate == FATE_LIMIT)
+                set_err(&st->err, PIC_ERR_WALK_LIMIT);
+            const bool keep = finished && fate == FATE_ALIVE;
+            if (keep)
+                deposit_one<R>(m.tet, t, lam, c.scale, W);
+            append<R>(keep, r, v, t, id, B, cntB);
+            count_fates(finished ? fate : FATE_ALIVE, steps, wraps, finished, stats, false);
+            if (finished)
+                active = false;
+        }
+    }
+    if (stats && lane == 0 && n_iter)
+        atomicAdd((unsigned long long *)&stats->walk_warp_iters, n_iter);
+}
+
 // ---------------------------------------------------------------------------
 // state conversion between the SoA store and interleaved FP64 arrays
 // ---------------------------------------------------------------------------
@@ -901,7 +979,9 @@ cudaError_t launch_step_fused(cudaStream_t s, int grid, int walk_form, MeshView<
 {
     const bool persistent = walk_form == WALK_FORM_AUTO ? sizeof(R) == 8
                                                          : walk_form == WALK_FORM_PERSISTENT;
-    if (persistent)
+    if (walk_form == WALK_FORM_ROUNDS)
+        k_step_fused_rounds<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
+    else if (persistent)
         k_step_fused_persistent<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);
     else
         k_step_fused<R><<<grid, 256, 0, s>>>(m, c, step, nq, qoff, A, B, a, st, W, stats);

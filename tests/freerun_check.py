@@ -21,6 +21,11 @@ places, and only there (Sec. II.B):
 * exits: an SP within the position tolerance of Gamma_1 or Gamma_3 may leave
   one step earlier in one run; the survivor must lie within the tolerance
   of such a face.
+* the periodic sides: an SP on (within rounding of) Gamma_2 may be wrapped
+  in one run and not in the other; its positions then agree on the nearest
+  periodic image, but it sits at the opposite side of the box, where its
+  charge goes to other nodes (the field mesh is not periodic: zero-Neumann
+  sides), so the potentials of the two runs differ near both sides.
 
 Everything else is held to the bar: an SP whose cells have agreed at every
 step must have its position within the tolerance (1e-5 of the box height)
@@ -130,9 +135,11 @@ class FreeRunCheck:
         self.divergence_gap = []       # |r_G - r_O| at each explained cell divergence
         self.divergence_excess = []    # distance of each position from the other cell
         # the first step after which the runs hold different SPs (an
-        # injection rounding flip or an exit one step apart): from then on
-        # the space charge of the two runs differs by whole SPs
+        # injection rounding flip or an exit one step apart) or an SP on
+        # different periodic images: from then on the space charge of the
+        # two runs differs by whole SPs
         self.first_event = None
+        self.image_flips = {}          # id -> step its runs took different images
 
     # geometry ----------------------------------------------------------------
     def lam(self, cell, r):
@@ -182,6 +189,12 @@ class FreeRunCheck:
         common, a, b = np.intersect1d(ig, io, assume_unique=True, return_indices=True)
         self.checked += len(common)
         r_g, r_o = rg[a], self.nearest_image(ro[b], rg[a])
+        img = np.any(r_o != ro[b], axis=1)
+        new_img = img & ~np.isin(common, self._ids(self.image_flips))
+        for x in common[new_img]:
+            self.image_flips[int(x)] = k
+        if new_img.any() and self.first_event is None:
+            self.first_event = k
         gap = np.abs(r_g - r_o).max(axis=1)
         clean = ~np.isin(common, self._ids(self.diverged))
         same = cg[a] == co[b]
@@ -263,4 +276,5 @@ class FreeRunCheck:
                 "max_gap_at_divergence_rel": (max(self.divergence_gap) / self.L[2]
                                               if self.divergence_gap else 0.0),
                 "first_event_step": self.first_event,
+                "image_flips": len(self.image_flips),
                 "failures": self.failures[:10]}

@@ -137,3 +137,34 @@ def test_point_triangle_distance():
     want = [0.5, 1.0, np.sqrt(2.0), 1.0]
     got = point_triangle_distance(pts, np.repeat(a, 4, 0), np.repeat(b, 4, 0), np.repeat(c, 4, 0))
     assert np.allclose(got, want)
+
+
+def test_sp_on_the_periodic_side_with_two_images_is_explained(oracle_mod, plate_small):
+    """One SP exactly on Gamma_2: one run holds it at x = x_lo, the other at
+    x = x_hi (wrapped).  Positions agree on the nearest image, the step is a
+    charge event (the charge lands on the nodes of opposite sides), and
+    nothing is reported as unexplained."""
+    mesh = plate_small
+    p = K.params(E0=1e9, w_sp=1e-6, pcg_rtol=1e-12, capacity=10_000)
+    a, b = (oracle_mod.Oracle(mesh, p) for _ in range(2))
+    for o in (a, b):
+        o.init_potential()
+        o.set_work_function(np.full(mesh.n_faces, 1000.0))     # no emission
+    lo, hi = mesh.box_lo, mesh.box_hi
+    ra = np.array([[lo[0], 0.37 * (lo[1] + hi[1]), 0.5 * hi[2]]])
+    rb = ra.copy()
+    rb[0, 0] = hi[0]
+    ca = a.locate(ra + [[1e-12, 0, 0]], np.array([0], np.int32))[1]
+    cb = b.locate(rb - [[1e-12, 0, 0]], np.array([0], np.int32))[1]
+    pid = np.array([1 << 62], np.int64)
+    v = np.array([[0.0, 1e5, 0.0]])
+    a.set_particles(ra, v, ca, pid)
+    b.set_particles(rb, v, cb, pid)
+    chk = FreeRunCheck(mesh, b, p["seed"], fp32_positions=False)
+    E = a.field()
+    chk.step(-1, a.particles(), b.particles(), E, E)
+    _run(chk, a, b, 2)
+    s = chk.summary()
+    assert not chk.failures, chk.failures
+    assert s["image_flips"] == 1 and s["first_event_step"] == -1
+    assert not np.array_equal(a.charge(), b.charge())   # the charge sits on other nodes

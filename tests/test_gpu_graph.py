@@ -83,7 +83,8 @@ def test_tuning_knobs_keep_results(picfem, tip_small, plate_small):
     parts = inputs.random_particles(tip_small, 4000, seed=5, v_scale=4e6, v_up=6e6)
     runs = []
     for knobs in ({}, dict(particle_blocks_per_sm=2, walk_form=2),
-                  dict(particle_blocks_per_sm=16, walk_form=1)):
+                  dict(particle_blocks_per_sm=16, walk_form=1),
+                  dict(particle_blocks_per_sm=8, walk_form=3)):
         c = picfem.Context(K.params(**base)).mesh_load(tip_small)
         c.set_tuning(**knobs)
         c.init_potential()
