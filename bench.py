@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=200, help="0 skips the adjoint timing")
     ap.add_argument("--adjoint-ckpt", type=int, default=20)
     ap.add_argument("--large-steps", type=int, default=20, help="timed steps of the 8M-tet tip")
+    ap.add_argument("--target-sp", type=int, default=0,
+                    help="starting SPs of the main arm (0: the workload's own count)")
     ap.add_argument("--no-diode", action="store_true", help="skip the planar-diode I-V sweep")
     ap.add_argument("--no-large", action="store_true", help="skip the 8M-tet tip")
     return ap.parse_args()
@@ -272,7 +274,7 @@ def run_gpu(args, rank, world, form, timed_steps, warmup, prof_steps=None):
     p = dict(p, **FORMS[form])
     if p["precision"] == K.PREC_FP32_IR:
         p = dict(p, pcg_variant=PCG_VARIANTS[args.pcg_variant])
-    target = K.WORKLOADS[args.workload]["target_sp"]
+    target = args.target_sp or K.WORKLOADS[args.workload]["target_sp"]
     stream = torch.cuda.current_stream()
     ctx = picfem.Context(p, stream=stream).mesh_load(mesh)
     info = ctx.info()
@@ -492,7 +494,7 @@ def run_ensemble(n_rep, steps, warmup):
             state = (c.potential(), c.particles(), c.step_index)
             knobs, _, trials = autotune.tune(
                 c, steps=3, warmup=1, use_cache=False,
-                space={"particle_blocks_per_sm": (8, 16), "pcg_cheb_degree": (4, 6)})
+                space={"particle_blocks_per_sm": (8, 16, 24), "pcg_cheb_degree": (4, 6)})
             entry["tuning"] = knobs
             entry["tuning_trials"] = len(trials)
             c.step(2, stats=False)                  # balance on the tuned solves

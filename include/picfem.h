@@ -222,7 +222,7 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  * pcg_cheb_degree, which changes the preconditioner but not the stopping
  * rule, so the potential meets the same tolerance):
  *   particle_blocks_per_sm  blocks of 256 threads per SM of the particle
- *                           kernels (1..64; default 16 for FP32_IR, 8 for FP64)
+ *                           kernels (1..64; default 24 for FP32_IR, 8 for FP64)
  *   walk_form               fused step: 0 by precision (FP64 persistent lanes,
  *                           FP32 coherent warps), 1 coherent warps (a warp
  *                           walks 32 consecutive SPs to the end), 2 persistent
@@ -279,6 +279,11 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           For tests and diagnosis of the failure path: a
  *                           small limit makes a solve fail with
  *                           PIC_ERR_TIMEOUT, and the context stays usable
+ *   pcg_mg_degree0/1        multigrid V-cycle (pcg_cheb_local = 4): degree of
+ *                           the Chebyshev smoothing on the fine level / on
+ *                           level 1, before and after the coarse correction
+ *                           (1..8; default 3 and 3).  Changes the
+ *                           preconditioner, not the stopping rule
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */
@@ -292,6 +297,8 @@ typedef struct {
     int32_t sort_cells;
     int32_t pcg_halo_sync;
     int32_t wait_limit;
+    int32_t pcg_mg_degree0;
+    int32_t pcg_mg_degree1;
 } pic_tuning;
 int pic_get_tuning(pic_ctx ctx, pic_tuning *t);
 int pic_set_tuning(pic_ctx ctx, const pic_tuning *t);

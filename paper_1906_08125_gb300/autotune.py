@@ -23,7 +23,7 @@ import time
 import numpy as np
 
 SPACE = {
-    "particle_blocks_per_sm": (2, 4, 8, 16),
+    "particle_blocks_per_sm": (4, 8, 16, 24, 32),
     "walk_form": (1, 2, 3),
     "pcg_blocks_per_sm": (0, 1, 2, 4),
     "pcg_cheb_degree": (0, 4, 6, 8),

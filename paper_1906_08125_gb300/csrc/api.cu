@@ -139,7 +139,7 @@ struct pic_ctx_s {
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
     int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1,
-        halo_sync = 1, wait_limit = 0;
+        halo_sync = 1, wait_limit = 0, mg_deg0 = MG_DEGREE0, mg_deg1 = MG_DEGREE1;
     int *scnt = nullptr, *soff = nullptr, *srank = nullptr, *sscan = nullptr;   // sort scratch
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
@@ -497,8 +497,8 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     if (c->mg.n1 > 0 && c->cheb_local == 4) {
         g.mg_n1 = c->mg.n1;
         g.mg_n2 = c->mg.n2;
-        g.mg_deg0 = MG_DEGREE0;
-        g.mg_deg1 = MG_DEGREE1;
+        g.mg_deg0 = c->mg_deg0;
+        g.mg_deg1 = c->mg_deg1;
         g.mg_max_l1_local = c->mg.max_l1_local;
         g.mg_max_l1_own = c->mg.max_l1_own;
         g.mg_max_l2_own = c->mg.max_l2_own;
@@ -632,7 +632,7 @@ extern "C" int pic_create(pic_ctx *out, const pic_params *p, void *stream)
     }
     // particle kernels: 16 blocks of 256 per SM for the FP32 walk (more SPs
     // claimed in flight hides more of its record-fetch latency), 8 for FP64
-    c->pgrid = c->num_sms * (q.precision == PIC_PREC_FP32_IR ? 16 : 8);
+    c->pgrid = c->num_sms * (q.precision == PIC_PREC_FP32_IR ? 24 : 8);
     // a Chebyshev-preconditioned solve gets the coarse correction over the
     // solver blocks by default (the plain Jacobi form stays plain)
     c->cheb_local = q.pcg_cheb_degree >= 2 ? 3 : 0;
@@ -1653,6 +1653,8 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->sort_cells = c->sort_cells;
     t->pcg_halo_sync = c->halo_sync;
     t->wait_limit = c->wait_limit;
+    t->pcg_mg_degree0 = c->mg_deg0;
+    t->pcg_mg_degree1 = c->mg_deg1;
     return PIC_OK;
 }
 
@@ -1666,7 +1668,8 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 4 ||
         (t->pcg_cheb_local == 4 && c->mg.n1 == 0) ||
         t->sort_cells < 0 || t->sort_cells > 1 || t->pcg_halo_sync < 0 || t->pcg_halo_sync > 1 ||
-        t->wait_limit < 0 || t->wait_limit > (1 << 30) ||
+        t->wait_limit < 0 || t->wait_limit > (1 << 30) || t->pcg_mg_degree0 < 0 ||
+        t->pcg_mg_degree0 > 8 || t->pcg_mg_degree1 < 0 || t->pcg_mg_degree1 > 8 ||
         (t->pcg_cheb_degree >= 2 && !(c->p.pcg_cheb_ratio > 1.0)))
         return fail(c, PIC_ERR_ARG, "pic_set_tuning: value out of range");
     CK(cudaSetDevice(c->dev));
@@ -1680,6 +1683,8 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->sort_cells = t->sort_cells;
     c->halo_sync = t->pcg_halo_sync;
     c->wait_limit = t->wait_limit;
+    c->mg_deg0 = t->pcg_mg_degree0 > 0 ? t->pcg_mg_degree0 : MG_DEGREE0;
+    c->mg_deg1 = t->pcg_mg_degree1 > 0 ? t->pcg_mg_degree1 : MG_DEGREE1;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)

@@ -48,7 +48,8 @@ class Tuning(C.Structure):
                 ("pcg_blocks_per_sm", C.c_int32), ("pcg_cheb_degree", C.c_int32),
                 ("pcg_balance", C.c_int32), ("pcg_cheb_local", C.c_int32),
                 ("sort_cells", C.c_int32), ("pcg_halo_sync", C.c_int32),
-                ("wait_limit", C.c_int32)]
+                ("wait_limit", C.c_int32), ("pcg_mg_degree0", C.c_int32),
+                ("pcg_mg_degree1", C.c_int32)]
 
 
 class StepStats(C.Structure):

@@ -98,6 +98,8 @@ def test_adjoint_fp32ir_close_to_fp64(picfem, oracle_grad):
     (Qo, gE0o, gwfo), tape = oracle_grad
     c, (Q, gE0, gwf) = gpu_adjoint(picfem, ckpt=4, precision=K.PREC_FP32_IR, pcg_rtol=1e-8,
                                    pcg_cheb_degree=4)
+    print("FP32_IR adjoint against FP64: Q", Q / tape.Q_recorded - 1, "dQ/dE0",
+          gE0[0] / gE0o - 1, "dQ/dphi", rel(gwf, gwfo))
     assert abs(Q - tape.Q_recorded) <= 2 * abs(tape.Q_recorded) / 100
     assert gE0[0] == pytest.approx(gE0o, rel=2e-2)
     assert rel(gwf, gwfo) <= 5e-2

@@ -250,3 +250,48 @@ def test_fp64_split_step_bit_exact_full_size(picfem, oracle_mod, tip1m, oracle_s
         assert np.array_equal(a, b)
     ctx.deposit()
     assert np.array_equal(ctx.charge(), o2.deposit())
+
+
+def test_one_step_large_tip_fp32ir(picfem, oracle_mod):
+    """The large tip (7.9M tets, 1.35M free DOFs: the general solver kernels)
+    in its benchmark configuration: one fused FP32+IR step of a seeded 2e5-SP
+    sample from identical state (the GPU's FP64 solve at rtol 1e-12 as the
+    common starting potential) against the OpenMP oracle (rtol 1e-10): every
+    SP within 1e-5 of the box height, every differing cell, injection count,
+    exit and periodic image explained, exact charge conservation, and the new
+    potential within 1e-6 unless the step had a charge event."""
+    from freerun_check import FreeRunCheck
+    mesh, p, _ = K.workload("tip_8m")
+    parts = inputs.random_particles(mesh, N_SAMPLE, seed=88, v_scale=3e6, v_up=1.5e7)
+    ref = picfem.Context(dict(p, precision=K.PREC_FP64, pcg_rtol=1e-12, pcg_cheb_degree=0,
+                              pcg_max_iter=200_000)).mesh_load(mesh)
+    assert ref.info()["pcg_resident"] == 0 and ref.info()["n_tets"] >= 7_500_000
+    ref.init_potential()
+    ref.set_particles(*parts)
+    ref.deposit()
+    ref.poisson_solve()
+    phi = ref.potential()
+    ref.close()
+    orc = oracle_mod.Oracle(mesh, dict(p, precision=K.PREC_FP64, pcg_rtol=1e-10,
+                                       pcg_max_iter=200_000), parallel=True)
+    orc.set_potential(phi)
+    orc.set_particles(*parts)
+    orc.step_index = 3
+    ctx = picfem.Context(p).mesh_load(mesh)
+    ctx.set_potential(phi)
+    ctx.set_particles(*parts)
+    ctx.step_index = 3
+    E_g, E_o = ctx.field(), orc.field()
+    ctx.step(1)
+    orc.step(1)
+    chk = FreeRunCheck(mesh, orc, p["seed"])
+    g = ctx.particles()
+    chk.step(3, g, orc.particles(), E_g, E_o)
+    s = chk.summary()
+    print("tip_8m FP32+IR one step:", s, "potential", rel(ctx.potential(), orc.potential()))
+    assert not chk.failures, s
+    assert s["sp_steps_checked"] > 0.9 * N_SAMPLE
+    assert int(ctx.charge().sum()) == len(g[3]) * 2 ** 32
+    if s["first_event_step"] is None:
+        assert rel(ctx.potential(), orc.potential()) <= 1e-6
+    ctx.close()

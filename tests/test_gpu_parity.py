@@ -276,13 +276,15 @@ def test_teacher_forced_plate_96k_fp32ir(picfem, oracle_mod):
 
 def test_free_running_plate_fp32ir(picfem, oracle_mod):
     """The same, both sides free-running for 100 steps: until the first step
-    in which the runs hold different SPs (an injection count on the other
-    side of a rounding threshold), every SP within 1e-5 of the box height and
-    every difference explained, the potential within 1e-6.  From then on the
-    two space charges differ by a whole SP (its potential near the cathode is
-    ~1e-5 of the applied one), which moves every trajectory by more than the
-    tolerance until that SP has left the gap; at the end of the 100 steps at
-    most 5 % of the SPs may still lie beyond 1e-5 of the box height."""
+    in which the runs deposit different charge (an SP more or fewer from an
+    injection count on the other side of a rounding threshold, an exit one
+    step apart, or an SP on the periodic side held in different images),
+    every SP within 1e-5 of the box height and every difference explained,
+    the potential within 1e-6.  From then on the two space charges differ by
+    a whole SP (its potential near it is ~1e-5 of the applied one), which
+    moves every trajectory by more than the tolerance until that SP has left
+    the gap; at the end of the 100 steps at most 5 % of the SPs may still lie
+    beyond 1e-5 of the box height."""
     from freerun_check import FreeRunCheck
     mesh, p, steps = K.workload("plate_96k", pcg_rtol=1e-10)
     pg = dict(p, precision=K.PREC_FP32_IR, pcg_rtol=1e-8, pcg_cheb_degree=6)
@@ -304,7 +306,8 @@ def test_free_running_plate_fp32ir(picfem, oracle_mod):
         if chk.first_event is None:
             chk.step(k, g, o, E_g, E_o)
             assert not chk.failures, (k, chk.summary())
-            worst = max(worst, rel(ctx.potential(), orc.potential()))
+            if chk.first_event is None:
+                worst = max(worst, rel(ctx.potential(), orc.potential()))
         spread.append(_spread(g, o, L))
     s = chk.summary()
     print("plate_96k FP32+IR free-running:", s, "potential", worst, "spread", spread[-1],
