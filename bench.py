@@ -191,11 +191,13 @@ def bytes_step_fused_compulsory(st_prev_alive, st, s, info, rec):
 
 
 def bytes_pcg(st, info, fp64, cheb):
-    """Algorithmic bytes of one solve: every SpMV reads the stored matrix
-    (values + column indices) and the vector it multiplies once; the vector
-    updates read and write each vector they touch once.  A CG iteration with
-    a Chebyshev preconditioner of degree k runs k SpMVs (k - 1 in the
-    preconditioner, one for the search direction)."""
+    """Algorithmic bytes of one solve counting every SpMV of the
+    preconditioner: every SpMV reads the stored matrix (values + column
+    indices) and the vector it multiplies once; the vector updates read and
+    write each vector they touch once.  A CG iteration with a Chebyshev
+    preconditioner of degree k runs k SpMVs (k - 1 in the preconditioner, one
+    for the search direction); the caller passes k = 2 k0 + 1 for the V-cycle
+    with fine-level smoothing degree k0."""
     n, nnz = info["n_free"], info["nnz"]
     it, outer = int(st["pcg_iters"]), int(st["pcg_outer"])
     k = max(1, cheb)
@@ -331,7 +333,8 @@ def run_gpu(args, rank, world, form, timed_steps, warmup, prof_steps=None):
         pms, pst, pprev, _ = timed(prof_steps, False)
         prof = ctx.profile_read()
         ctx.profile(False)
-    res = dict(ctx=ctx, mesh=mesh, params=p, info=info, step_ms=step_ms, total_ms=total_ms,
+    res = dict(ctx=ctx, mesh=mesh, params=p, info=info, tuning=ctx.tuning(), step_ms=step_ms,
+               total_ms=total_ms,
                stats=st, prev_alive=prev, pushes=pushes, launches=launches, prof=prof,
                prof_stats=pst, prof_prev_alive=pprev, clocks=clk, n0=n0, graph=graph)
     return res
@@ -369,6 +372,12 @@ def roofline(res, fp64):
     s = 8 if fp64 else 4
     rec = 128 if fp64 else 64
     cheb = res["params"].get("pcg_cheb_degree", 0)
+    tun = res.get("tuning") or {}
+    if tun.get("pcg_cheb_local") == 4:
+        # the V-cycle: 2 k0 fine-level products per application (smoothing
+        # before and after, the residual between) plus the CG's own; the
+        # coarse levels' products are under 15 % of a fine one and not counted
+        cheb = 2 * tun.get("pcg_mg_degree0", 3) + 1
     alg = {
         "step_fused": sum(bytes_step_fused(int(pa), row, s, info) for pa, row in zip(prev, st)),
         "pcg": sum(bytes_pcg_min(row, info, fp64) for row in st),
@@ -391,39 +400,46 @@ def roofline(res, fp64):
         out_k["step_fused"]["note"] = ("bytes count one walk-record fetch per face crossing; "
                                        "neighbouring SPs share records in L1/L2, so this is "
                                        "not DRAM traffic")
-    a = out_k[dom]["alg_gbs"]
-    roof = {"bound": "hbm", "kernel": dom, "achieved": a, "peak": peak, "unit": "GB/s",
-            "frac": round(a / peak, 4) if a else None, "traffic": ncu_traffic(dom, WORKLOAD),
-            "peak_source": kind}
-    if dom == "step_fused":
-        ms = kernels["step_fused"]["ms"]
-        comp = sum(bytes_step_fused_compulsory(int(pa), row, s, info, rec)
-                   for pa, row in zip(prev, st))
-        roof["bytes_model"] = ("N 2 (6s + 12) + X (16 + 12 s) + T_occ (48 + 12 s) + 16 N_nodes "
-                               "+ 64 per new SP, X = face crossings (counted)")
-        roof["limiter"] = ("latency of the dependent walk-record fetches (one per face "
-                           "crossing, served from L1/L2 for neighbouring SPs)")
-        roof["compulsory"] = {"bytes_per_launch": int(comp / kernels["step_fused"]["launches"]),
-                              "achieved": round(comp / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
-                              "frac": round(comp / (ms * 1e-3) / 1e9 / peak, 4),
-                              "model": "each SP state and each touched record once"}
-    if dom == "pcg":
-        ms = kernels["pcg"]["ms"]
-        roof["bytes_model"] = ("one SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n), "
-                               "s = value bytes; FP32 form + refinements x (12 nnz + 24 n)")
-        roof["alg_frac_incl_precond"] = round(alg_precond / (ms * 1e-3) / 1e9 / peak, 4)
-        oc = ncu_onchip("pcg", WORKLOAD)
-        if oc:
-            mhz = (res.get("clocks") or {}).get("sm_mhz") or oc.get("sm_mhz")
-            sms = oc.get("sms", 152)
-            speak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9
-            sach = oc["smem_bytes_per_launch"] / (ms / kernels["pcg"]["launches"] * 1e-3) / 1e9
-            roof["onchip"] = {"bound": "smem", "achieved": round(sach, 1),
-                              "peak": round(speak, 1), "unit": "GB/s",
-                              "frac": round(sach / speak, 4),
-                              "peak_basis": f"{sms} SMs x 128 B/clk at {mhz:.0f} MHz"}
-            roof["limiter"] = oc.get("limiter")
-            roof["dram_pct_of_peak_ncu"] = oc.get("dram_pct_of_peak")
+    def kernel_roof(name):
+        ms = kernels[name]["ms"]
+        a = out_k[name]["alg_gbs"]
+        r = {"bound": "hbm", "kernel": name, "achieved": a, "peak": peak, "unit": "GB/s",
+             "frac": round(a / peak, 4) if a else None, "traffic": ncu_traffic(name, WORKLOAD),
+             "peak_source": kind}
+        if name == "step_fused":
+            comp = sum(bytes_step_fused_compulsory(int(pa), row, s, info, rec)
+                       for pa, row in zip(prev, st))
+            r["bytes_model"] = ("N 2 (6s + 12) + X (16 + 12 s) + T_occ (48 + 12 s) + 16 N_nodes "
+                                "+ 64 per new SP, X = face crossings (counted)")
+            r["limiter"] = ("latency of the dependent walk-record fetches (one per face "
+                            "crossing, served from L1/L2 for neighbouring SPs)")
+            r["compulsory"] = {"bytes_per_launch": int(comp / kernels[name]["launches"]),
+                               "achieved": round(comp / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                               "frac": round(comp / (ms * 1e-3) / 1e9 / peak, 4),
+                               "model": "each SP state and each touched record once"}
+        if name == "pcg":
+            r["bytes_model"] = ("one SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n), "
+                                "s = value bytes; FP32 form + refinements x (12 nnz + 24 n)")
+            r["alg_frac_incl_precond"] = round(alg_precond / (ms * 1e-3) / 1e9 / peak, 4)
+            oc = ncu_onchip("pcg", WORKLOAD)
+            if oc:
+                mhz = oc.get("sm_mhz") or (res.get("clocks") or {}).get("sm_mhz")
+                sms = oc.get("sms", 152)
+                speak = sms * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+                sach = oc["smem_bytes_per_launch"] / (oc["duration_ns"] * 1e-9) / 1e9
+                r["onchip"] = {"bound": "smem", "achieved": round(sach, 1),
+                               "peak": round(speak, 1), "unit": "GB/s",
+                               "frac": round(sach / speak, 4),
+                               "basis": (f"one ncu-captured launch: shared-memory wavefronts x "
+                                         f"128 B over its duration; {sms} SMs x 128 B/clk at "
+                                         f"{mhz:.0f} MHz")}
+                r["limiter"] = oc.get("limiter")
+                r["dram_pct_of_peak_ncu"] = oc.get("dram_pct_of_peak")
+        return r
+
+    roof = kernel_roof(dom)
+    if dom != "pcg" and "pcg" in kernels:
+        roof["solver"] = kernel_roof("pcg")
     return roof, out_k
 
 
