@@ -785,14 +785,23 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PRECONDITIONERS = {0: "Jacobi / whole-matrix Chebyshev", 1: "block-local Chebyshev",
+                   2: "block-local Chebyshev + coarse correction",
+                   3: "Chebyshev + coarse correction over the solver blocks",
+                   4: "multigrid V-cycle"}
+
+
 def arm_summary(r, world):
     """Throughput of a comparison arm from its timed (production) steps."""
     st = r["stats"]
+    tun = r.get("tuning") or {}
+    pre = ("Jacobi" if r["params"].get("pcg_cheb_degree", 0) < 2 and tun.get("pcg_cheb_local") != 4
+           else PRECONDITIONERS.get(tun.get("pcg_cheb_local"), "?"))
     return {"value": round(world * len(r["step_ms"]) / (r["total_ms"] * 1e-3), 3),
             "unit": METRIC, "ms_per_step": round(r["total_ms"] / len(r["step_ms"]), 3),
             "pushes_per_s": round(r["pushes"] / (r["total_ms"] * 1e-3), 1),
             "pcg_iters_mean": round(float(st["pcg_iters"].mean()), 1),
-            "steps": len(r["step_ms"])}
+            "preconditioner": pre, "steps": len(r["step_ms"])}
 
 
 def main():
@@ -830,6 +839,8 @@ def main():
                            f"CUDA events, right after the timed steps",
            "parallelism": f"replicas x{world}"}
     cross = float(st["crossings"].sum())
+    tun = res.get("tuning") or {}
+    cfg["preconditioner"] = PRECONDITIONERS.get(tun.get("pcg_cheb_local"), "?")
     extra = {"pushes_per_s": round(push_rate, 1),
              "pcg_iters_mean": round(float(st["pcg_iters"].mean()), 1),
              "pcg_outer_mean": round(float(st["pcg_outer"].mean()), 2),
