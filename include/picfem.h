@@ -153,6 +153,11 @@ typedef struct {
     int32_t graph;            /* pic_step: 1 replays a captured CUDA graph per
                                  step, 0 not yet captured or params.graph = 0,
                                  -1 the capture was refused (direct launches)  */
+    int32_t mg_levels;        /* multigrid hierarchy built at mesh_load for the
+                                 solver in use (pcg_cheb_local = 4): levels
+                                 below the fine one, 0 when there is none     */
+    int32_t mg_coarse_rows;   /* rows of its coarsest level (the largest over
+                                 the replicas of a batch)                     */
 } pic_info;
 
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -233,8 +238,9 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           finished taking the range's next SPs after each
  *                           round); the SP results are identical
  *   pcg_blocks_per_sm       batch solve (mesh_load_batch): at most this many
- *                           blocks per SM (0 = as many as fit; 0..64); the
- *                           one-system solver ignores it
+ *                           blocks per SM (0 = as many as fit; 0..64), and
+ *                           the same for one system too large for the
+ *                           resident kernels; the resident solver ignores it
  *   pcg_cheb_degree         as pic_params.pcg_cheb_degree (0..32)
  *   pcg_balance             batch solve: 1 (default) shares the blocks out in
  *                           proportion to each replica's slices x the CG
@@ -256,7 +262,18 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           Chebyshev smoothing of degree 3 before and after
  *                           the coarse correction on the fine level and on
  *                           level 1 (built at mesh_load for the resident
- *                           solver; PIC_ERR_ARG where it was not built).  The
+ *                           solver).  The general solver (batches, systems
+ *                           too large for the resident blocks) builds its
+ *                           own hierarchy for 4: the same matching over the
+ *                           whole matrix of each replica, three passes for
+ *                           level 1 and four for each further level until
+ *                           every replica has at most 1024 rows (at most six
+ *                           levels), the coarsest solved with a dense
+ *                           inverse per replica, smoothing of degree
+ *                           pcg_mg_degree0 on the fine level and
+ *                           pcg_mg_degree1 on every coarser one, in FP32 or
+ *                           FP64 with the solver.  PIC_ERR_ARG where no
+ *                           hierarchy was built.  The
  *                           default is 4 where the hierarchy exists and
  *                           pcg_cheb_degree >= 2, else 3 when pcg_cheb_degree
  *                           >= 2, otherwise 0.  All are SPD; the stopping rule
@@ -281,9 +298,13 @@ int mesh_load_batch(pic_ctx ctx, int32_t n_rep, const int32_t *rep_node_off,
  *                           PIC_ERR_TIMEOUT, and the context stays usable
  *   pcg_mg_degree0/1        multigrid V-cycle (pcg_cheb_local = 4): degree of
  *                           the Chebyshev smoothing on the fine level / on
- *                           level 1, before and after the coarse correction
- *                           (1..8; default 3 and 3).  Changes the
- *                           preconditioner, not the stopping rule
+ *                           the coarser levels, before and after the coarse
+ *                           correction
+ *                           (1..8; 0 = the default: 3 and 3 for the
+ *                           resident solver, 1 and 3 for the general one,
+ *                           whose fine-level products stream the matrix
+ *                           from HBM).  Changes the preconditioner, not the
+ *                           stopping rule
  * pic_set_tuning takes effect from the next call and drops captured graphs;
  * PIC_ERR_ARG for a value out of range.  t: HOST.
  */

@@ -76,9 +76,11 @@ def tune(ctx, steps=4, warmup=2, space=None, cache_path=None, use_cache=True, lo
     and return ``(knobs, ms_per_step, trials)``.  The context's state is
     restored to the snapshot afterwards."""
     space = dict(space or SPACE)
-    if ctx.info()["n_rep"] <= 1:
-        space.pop("pcg_blocks_per_sm", None)       # the one-system solver ignores them
-        space.pop("pcg_balance", None)
+    info = ctx.info()
+    if info["n_rep"] <= 1:
+        space.pop("pcg_balance", None)             # one system: nothing to balance
+        if info["pcg_resident"]:
+            space.pop("pcg_blocks_per_sm", None)   # the resident solver ignores it
     if ctx.params["pcg_cheb_degree"] < 2 and "pcg_cheb_degree" in space:
         # a plain Jacobi form stays Jacobi: the degree is part of what it is
         space.pop("pcg_cheb_degree")

@@ -111,6 +111,14 @@ struct pic_ctx_s {
         double *g1d[2] = {nullptr, nullptr};
         unsigned long long *dtag1 = nullptr;
     } mg;
+    // multigrid hierarchy of the general kernels (mg.cu gmg_build; nlev == 0: none)
+    struct {
+        int nlev = 0, coarse_max = 0;
+        const GmgLevel *levels = nullptr;   // [nlev + 1], device
+        const float *inv = nullptr;
+        const long long *ioff = nullptr;
+        const int *cn = nullptr;
+    } gmg;
     // replicas of a batch (1 for a single mesh)
     int n_rep = 1, n_rows = 0;
     int *tet_rep = nullptr, *face_rep = nullptr, *rep_face_off = nullptr;
@@ -139,7 +147,7 @@ struct pic_ctx_s {
     int pgrid = 0;
     // launch tuning (pic_set_tuning)
     int walk_form = WALK_FORM_AUTO, pcg_bps = 0, pcg_balance = 1, cheb_local = 0, sort_cells = 1,
-        halo_sync = 1, wait_limit = 0, mg_deg0 = MG_DEGREE0, mg_deg1 = MG_DEGREE1;
+        halo_sync = 1, wait_limit = 0, mg_deg0 = 0, mg_deg1 = 0;   // 0: the default
     int *scnt = nullptr, *soff = nullptr, *srank = nullptr, *sscan = nullptr;   // sort scratch
     std::vector<int> rep_slice;   // first slice of each replica (batch solve plan)
     int *grp_iters = nullptr;     // iterations of each replica's last solve
@@ -392,6 +400,39 @@ int refresh_field(pic_ctx c, bool end_of_step = false)
     return PIC_OK;
 }
 
+// Smoothing degree of the V-cycle on the fine level (k = 0) or below (k = 1):
+// the tuned value, else the default of the solver in use (the resident one
+// smooths both levels with degree 3; the general one, whose fine-level
+// products stream the matrix from HBM, smooths the fine level with degree 1,
+// a scaled Jacobi step, and the coarser ones with degree 3)
+static int mg_degree(pic_ctx c, int k)
+{
+    const int t = k == 0 ? c->mg_deg0 : c->mg_deg1;
+    if (t > 0)
+        return t;
+    if (c->plan.resident)
+        return k == 0 ? MG_DEGREE0 : MG_DEGREE1;
+    return k == 0 ? GMG_DEGREE0 : GMG_DEGREE1;
+}
+
+// Chebyshev iteration on [lo, hi] (Saad, Alg. 12.1): theta, delta, sigma and
+// the recurrence rho_j = 1 / (2 sigma - rho_j-1), rho_0 = 1 / sigma; the steps
+// d_j+1 = c1[j] d_j + c2[j] D^-1 r_j after d_1 = D^-1 r / theta
+static void cheb_coefficients(double lo, double hi, int n, double *c1, double *c2,
+                              double *inv_theta)
+{
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+    const double sigma = delta > 0 ? theta / delta : 1.0;
+    double rho = 1.0 / sigma;
+    *inv_theta = 1.0 / theta;
+    for (int j = 0; j < n; ++j) {
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        c1[j] = rho_new * rho;
+        c2[j] = delta > 0 ? 2.0 * rho_new / delta : 0.0;
+        rho = rho_new;
+    }
+}
+
 // A solve with a right-hand side of the caller's (the adjoint solves): f =
 // rhs (rows), iterate and result in x (rows, warm start), scattered to the
 // node array out; stopping at relative residual rtol.
@@ -455,21 +496,11 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     g.cheb_a = (c->p.pcg_cheb_degree >= 2 || (c->cheb_local == 4 && c->mg.n1 > 0))
                    ? c->cheb_b / c->p.pcg_cheb_ratio
                    : 0.0;
-    {
-        // Chebyshev iteration on [a, b] (Saad, Alg. 12.1): theta, delta, sigma and
-        // the recurrence rho_j = 1 / (2 sigma - rho_{j-1}), rho_0 = 1 / sigma
-        double theta = 0.5 * (g.cheb_b + g.cheb_a), delta = 0.5 * (g.cheb_b - g.cheb_a);
-        double sigma = delta > 0 ? theta / delta : 1.0, rho = 1.0 / sigma;
-        g.cheb_inv_theta = 1.0 / theta;
-        g.cheb_inv_thetaf = (float)g.cheb_inv_theta;
-        for (int j = 0; j < 32; ++j) {
-            double rho_new = 1.0 / (2.0 * sigma - rho);
-            g.cheb_c1[j] = rho_new * rho;
-            g.cheb_c2[j] = delta > 0 ? 2.0 * rho_new / delta : 0.0;
-            g.cheb_c1f[j] = (float)g.cheb_c1[j];
-            g.cheb_c2f[j] = (float)g.cheb_c2[j];
-            rho = rho_new;
-        }
+    cheb_coefficients(g.cheb_a, g.cheb_b, 32, g.cheb_c1, g.cheb_c2, &g.cheb_inv_theta);
+    g.cheb_inv_thetaf = (float)g.cheb_inv_theta;
+    for (int j = 0; j < 32; ++j) {
+        g.cheb_c1f[j] = (float)g.cheb_c1[j];
+        g.cheb_c2f[j] = (float)g.cheb_c2[j];
     }
     g.d0 = c->d0;
     g.d1 = c->d1;
@@ -497,8 +528,8 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
     if (c->mg.n1 > 0 && c->cheb_local == 4) {
         g.mg_n1 = c->mg.n1;
         g.mg_n2 = c->mg.n2;
-        g.mg_deg0 = c->mg_deg0;
-        g.mg_deg1 = c->mg_deg1;
+        g.mg_deg0 = mg_degree(c, 0);
+        g.mg_deg1 = mg_degree(c, 1);
         g.mg_max_l1_local = c->mg.max_l1_local;
         g.mg_max_l1_own = c->mg.max_l1_own;
         g.mg_max_l2_own = c->mg.max_l2_own;
@@ -528,20 +559,22 @@ int run_pcg(pic_ctx c, pic_step_stats *stats, const unsigned long long *alive,
             g.mg_g1d[k] = c->mg.g1d[k];
         }
         // level-1 Chebyshev coefficients on [lmax1 / ratio, lmax1]
-        const double b1 = c->mg.lmax1, a1 = b1 / c->p.pcg_cheb_ratio;
-        const double theta = 0.5 * (b1 + a1), delta = 0.5 * (b1 - a1);
-        const double sigma = theta / delta;
-        double rho = 1.0 / sigma;
-        g.mg_inv_theta = 1.0 / theta;
+        const double b1 = c->mg.lmax1;
+        cheb_coefficients(b1 / c->p.pcg_cheb_ratio, b1, 32, g.mg_c1, g.mg_c2, &g.mg_inv_theta);
         g.mg_inv_thetaf = (float)g.mg_inv_theta;
         for (int j = 0; j < 32; ++j) {
-            const double rho_new = 1.0 / (2.0 * sigma - rho);
-            g.mg_c1[j] = rho_new * rho;
-            g.mg_c2[j] = 2.0 * rho_new / delta;
             g.mg_c1f[j] = (float)g.mg_c1[j];
             g.mg_c2f[j] = (float)g.mg_c2[j];
-            rho = rho_new;
         }
+    }
+    if (c->gmg.nlev > 0 && c->cheb_local == 4 && !c->plan.resident) {
+        g.gmg_nlev = c->gmg.nlev;
+        g.gmg_deg0 = mg_degree(c, 0);
+        g.gmg_deg1 = mg_degree(c, 1);
+        g.gmg = c->gmg.levels;
+        g.gmg_inv = c->gmg.inv;
+        g.gmg_ioff = c->gmg.ioff;
+        g.gmg_cn = c->gmg.cn;
     }
     g.coarse_inv = c->coarse_inv;
     g.coarse_r = c->coarse_r;
@@ -752,6 +785,112 @@ static int upload_mg(pic_ctx c, const MgHost &m)
     d.max_l1_own = m.max_l1_own;
     d.max_l2_own = m.max_l2_own;
     d.lmax1 = m.lmax1;
+    return PIC_OK;
+}
+
+// the general kernels' hierarchy on the device: level 0 points at the fine
+// matrix and at the solver's own vectors (z, the preconditioner's scratch and
+// its two step buffers), levels 1.. at their own tables and vectors (in the
+// solver's precision, zeroed), the level records and the coarsest inverses
+static int upload_gmg(pic_ctx c, const GmgHost &h)
+{
+    const bool f64 = fp64(c);
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    const int L = (int)h.lev.size() - 1;
+    std::vector<GmgLevel> rec((size_t)L + 1);
+    for (auto &r : rec)
+        r = GmgLevel{};
+    auto coefs = [&](GmgLevel &r, double lmax) {
+        double c1[GMG_MAX_DEG], c2[GMG_MAX_DEG], it;
+        cheb_coefficients(lmax / c->p.pcg_cheb_ratio, lmax, GMG_MAX_DEG, c1, c2, &it);
+        for (int j = 0; j < GMG_MAX_DEG; ++j) {
+            r.c1[j] = c1[j];
+            r.c2[j] = c2[j];
+            r.c1f[j] = (float)c1[j];
+            r.c2f[j] = (float)c2[j];
+        }
+        r.inv_theta = it;
+        r.inv_thetaf = (float)it;
+    };
+    int rc = 0;
+    {
+        GmgLevel &f = rec[0];
+        f.n_slices = c->n_slices;
+        f.sptr = c->slice_ptr;
+        f.col = c->col;
+        f.val32 = c->val32;
+        f.val64 = c->val64;
+        f.dinv32 = c->dinv32;
+        f.dinv64 = c->dinv64;
+        int *gsl = nullptr;
+        if ((rc = upload_vec(c, &gsl, c->rep_slice)))
+            return rc;
+        f.gsl = gsl;
+        f.x = f64 ? (void *)c->z : (void *)c->z32;
+        f.rc = f64 ? (void *)c->ap : (void *)c->ap32;
+        f.d[0] = f64 ? (void *)c->d0 : (void *)c->d32_0;
+        f.d[1] = f64 ? (void *)c->d1 : (void *)c->d32_1;
+        coefs(f, c->cheb_b);
+    }
+    for (int l = 1; l <= L; ++l) {
+        const GmgLevelHost &H = h.lev[l];
+        GmgLevel &r = rec[l];
+        r.n_slices = H.n_slices;
+        int *sptr = nullptr, *col = nullptr, *gsl = nullptr, *agg = nullptr, *mptr = nullptr,
+            *midx = nullptr;
+        if ((rc = upload_vec(c, &gsl, H.gsl)) || (rc = upload_vec(c, &agg, H.agg)) ||
+            (rc = upload_vec(c, &mptr, H.mptr)) || (rc = upload_vec(c, &midx, H.midx)))
+            return rc;
+        r.gsl = gsl;
+        r.agg = agg;
+        r.mptr = mptr;
+        r.midx = midx;
+        if (l < L) {
+            if ((rc = upload_vec(c, &sptr, H.sptr)) || (rc = upload_vec(c, &col, H.col)))
+                return rc;
+            r.sptr = sptr;
+            r.col = col;
+            if (f64) {
+                double *v = nullptr, *d = nullptr;
+                if ((rc = upload_vec(c, &v, H.val)) || (rc = upload_vec(c, &d, H.dinv)))
+                    return rc;
+                r.val64 = v;
+                r.dinv64 = d;
+            } else {
+                float *v = nullptr, *d = nullptr;
+                if ((rc = upload_vec(c, &v, H.val)) || (rc = upload_vec(c, &d, H.dinv)))
+                    return rc;
+                r.val32 = v;
+                r.dinv32 = d;
+            }
+            coefs(r, H.lmax);
+        }
+        const size_t rows = 32 * (size_t)H.n_slices;
+        void **vec[4] = {&r.x, &r.rc, &r.d[0], &r.d[1]};
+        for (void **v : vec) {
+            unsigned char *q = nullptr;
+            CK(dalloc(c, &q, rows * elem));
+            CK(cudaMemset(q, 0, rows * elem));
+            *v = q;
+        }
+    }
+    GmgLevel *dl = nullptr;
+    CK(dalloc(c, &dl, rec.size()));
+    CK(cudaMemcpy(dl, rec.data(), sizeof(GmgLevel) * rec.size(), cudaMemcpyHostToDevice));
+    float *inv = nullptr;
+    long long *ioff = nullptr;
+    int *cn = nullptr;
+    if ((rc = upload_vec(c, &inv, h.inv)) || (rc = upload_vec(c, &ioff, h.ioff)) ||
+        (rc = upload_vec(c, &cn, h.cn)))
+        return rc;
+    c->gmg.levels = dl;
+    c->gmg.inv = inv;
+    c->gmg.ioff = ioff;
+    c->gmg.cn = cn;
+    c->gmg.nlev = L;
+    c->gmg.coarse_max = 0;
+    for (int v : h.cn)
+        c->gmg.coarse_max = std::max(c->gmg.coarse_max, v);
     return PIC_OK;
 }
 
@@ -1533,6 +1672,20 @@ static int load_mesh(pic_ctx c, int32_t R, const int32_t *rno, const int32_t *rt
                 c->agg_inv = ai;
             }
         }
+        // multigrid hierarchy of the general kernels (pcg_cheb_local = 4)
+        c->gmg = {};
+        if (!c->plan.resident) {
+            GmgHost gh;
+            if (gmg_build(sptr.data(), scol.data(), hv.data(), hd.data(), n_slices, R,
+                          rep_slice.data(), MG_PASSES0, MG_PASSES1, GMG_MAX_COARSE,
+                          GMG_MAX_LEVELS, &gh)) {
+                int rc = upload_gmg(c, gh);
+                if (rc)
+                    return rc;
+                if (c->cheb_local == 3)
+                    c->cheb_local = 4;
+            }
+        }
     }
     c->loaded = true;
     c->a = 0;
@@ -1653,8 +1806,8 @@ extern "C" int pic_get_tuning(pic_ctx c, pic_tuning *t)
     t->sort_cells = c->sort_cells;
     t->pcg_halo_sync = c->halo_sync;
     t->wait_limit = c->wait_limit;
-    t->pcg_mg_degree0 = c->mg_deg0;
-    t->pcg_mg_degree1 = c->mg_deg1;
+    t->pcg_mg_degree0 = mg_degree(c, 0);
+    t->pcg_mg_degree1 = mg_degree(c, 1);
     return PIC_OK;
 }
 
@@ -1666,7 +1819,7 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
         t->walk_form > 3 || t->pcg_blocks_per_sm < 0 || t->pcg_blocks_per_sm > 64 ||
         t->pcg_cheb_degree < 0 || t->pcg_cheb_degree > 32 || t->pcg_balance < 0 ||
         t->pcg_balance > 1 || t->pcg_cheb_local < 0 || t->pcg_cheb_local > 4 ||
-        (t->pcg_cheb_local == 4 && c->mg.n1 == 0) ||
+        (t->pcg_cheb_local == 4 && c->mg.n1 == 0 && c->gmg.nlev == 0) ||
         t->sort_cells < 0 || t->sort_cells > 1 || t->pcg_halo_sync < 0 || t->pcg_halo_sync > 1 ||
         t->wait_limit < 0 || t->wait_limit > (1 << 30) || t->pcg_mg_degree0 < 0 ||
         t->pcg_mg_degree0 > 8 || t->pcg_mg_degree1 < 0 || t->pcg_mg_degree1 > 8 ||
@@ -1683,9 +1836,16 @@ extern "C" int pic_set_tuning(pic_ctx c, const pic_tuning *t)
     c->sort_cells = t->sort_cells;
     c->halo_sync = t->pcg_halo_sync;
     c->wait_limit = t->wait_limit;
-    c->mg_deg0 = t->pcg_mg_degree0 > 0 ? t->pcg_mg_degree0 : MG_DEGREE0;
-    c->mg_deg1 = t->pcg_mg_degree1 > 0 ? t->pcg_mg_degree1 : MG_DEGREE1;
+    c->mg_deg0 = t->pcg_mg_degree0;
+    c->mg_deg1 = t->pcg_mg_degree1;
     c->p.pcg_cheb_degree = t->pcg_cheb_degree;
+    // the one-system general solver: its grid follows pcg_blocks_per_sm
+    if (c->loaded && !c->plan.resident && c->plan.n_groups <= 0) {
+        const int grid = pcg_general_grid(c->p.precision, c->n_slices, c->num_sms, c->pcg_bps);
+        if (grid < 1)
+            return fail(c, PIC_ERR_CUDA, "pic_set_tuning: no solver grid");
+        c->plan.grid = grid;
+    }
     // the iteration counts of the last solves stay valid weights
     if (c->loaded && c->plan.n_groups > 0)
         return c->pcg_balance ? balance_batch(c) : replan_batch(c, nullptr);
@@ -1713,6 +1873,8 @@ extern "C" int pic_mesh_info(pic_ctx c, pic_info *info)
     info->n_rows = c->n_rows;
     info->pcg_resident = c->plan.resident ? 1 : 0;
     info->graph = c->graph_state;
+    info->mg_levels = c->plan.resident ? (c->mg.n1 > 0 ? 2 : 0) : c->gmg.nlev;
+    info->mg_coarse_rows = c->plan.resident ? c->mg.n2 : c->gmg.coarse_max;
     return PIC_OK;
 }
 

@@ -108,6 +108,33 @@ constexpr int MG_PASSES1 = 4;
 constexpr int MG_MAX_COARSE = 2048;
 constexpr int MG_DEGREE0 = 3;
 constexpr int MG_DEGREE1 = 3;
+// multigrid hierarchy of the general kernels: at most GMG_MAX_LEVELS levels
+// below the fine one, coarsened until every system has at most
+// GMG_MAX_COARSE rows on the coarsest (solved with a dense inverse); the
+// smoothing degree is at most GMG_MAX_DEG
+constexpr int GMG_MAX_LEVELS = 6;
+constexpr int GMG_MAX_COARSE = 1024;
+constexpr int GMG_MAX_DEG = 8;
+constexpr int GMG_DEGREE0 = 1;
+constexpr int GMG_DEGREE1 = 3;
+
+// One level of the general kernels' V-cycle as the device reads it (an array
+// in device memory, level 0 = the fine matrix).  Rows are laid out in 32-row
+// slices like the fine level, each system's rows in its own slices
+// [gsl[g], gsl[g+1]); padding rows have 1/diagonal 0 and no entries.
+struct GmgLevel {
+    int n_slices;
+    const int *sptr, *col;          // sliced ELLPACK (element offsets, level rows)
+    const float *val32, *dinv32;    // values, 1 / diagonal
+    const double *val64, *dinv64;
+    const int *gsl;                 // [systems + 1] slices of each system
+    const int *agg;                 // next finer level's rows -> this level's (-1: none)
+    const int *mptr, *midx;         // next finer level's rows in each row's aggregate
+    void *x, *rc, *d[2];            // correction, residual, Chebyshev steps (the
+                                    // solver's precision: float or double)
+    double c1[GMG_MAX_DEG], c2[GMG_MAX_DEG], inv_theta;   // Chebyshev coefficients
+    float c1f[GMG_MAX_DEG], c2f[GMG_MAX_DEG], inv_thetaf;
+};
 
 // Step bookkeeping kept on the device, so that a whole step can be captured
 // in a CUDA graph and replayed: the index of the step being run (key of the
@@ -296,6 +323,15 @@ struct PcgArgs {
     double *mg_g1d[2];        // (FP64)
     double mg_c1[32], mg_c2[32], mg_inv_theta;   // level-1 Chebyshev coefficients
     float mg_c1f[32], mg_c2f[32], mg_inv_thetaf;
+    // Multigrid V-cycle of the general kernels (gmg_nlev > 0): levels
+    // gmg[0] (fine) .. gmg[gmg_nlev] (coarsest, solved per system with the
+    // dense inverse gmg_inv + gmg_ioff[g] of order gmg_cn[g]); Chebyshev
+    // smoothing of degree gmg_deg0 on the fine level, gmg_deg1 below
+    int gmg_nlev, gmg_deg0, gmg_deg1;
+    const GmgLevel *gmg;
+    const float *gmg_inv;
+    const long long *gmg_ioff;
+    const int *gmg_cn;
 };
 // Host-side product of mg_build: the multigrid hierarchy of the resident
 // solver (see mg.cu), with the layout of the PcgArgs fields above.
@@ -317,6 +353,30 @@ struct MgHost {
 bool mg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
               int n_slices, int G, int passes0, int passes1, int max_coarse, MgHost *out);
 // dynamic shared memory of the V-cycle's arrays (bytes, elements of `elem` bytes)
+// Host-side product of gmg_build: the general kernels' hierarchy.  lev[0]
+// stands for the fine level (empty); lev[1..L] hold the coarse levels in the
+// device layout of GmgLevel (the coarsest without a matrix); the coarsest
+// level's matrix of each system is inverted (FP64 Cholesky, stored in FP32).
+struct GmgLevelHost {
+    int n_slices = 0;
+    std::vector<int> sptr, col, gsl, agg, mptr, midx;
+    std::vector<double> val, dinv;
+    double lmax = 2.0;
+};
+struct GmgHost {
+    std::vector<GmgLevelHost> lev;
+    std::vector<int> cn;
+    std::vector<long long> ioff;
+    std::vector<float> inv;
+};
+// Build it from the fine matrix (sliced ELLPACK as for mg_build) of n_sys
+// independent systems, system g on slices [sys_slices[g], sys_slices[g+1]):
+// passes0 matching passes for level 1, passes1 for each further level, until
+// every system has at most max_coarse rows (at most max_levels levels).
+// false when that cannot be reached.
+bool gmg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
+               int n_slices, int n_sys, const int *sys_slices, int passes0, int passes1,
+               int max_coarse, int max_levels, GmgHost *out);
 inline size_t mg_smem_bytes(const MgHost &m, size_t elem)
 {
     return elem * ((size_t)m.max_l1_local + 4 * (size_t)m.max_l1_own + (size_t)m.max_l2_own) + 16;
@@ -353,6 +413,9 @@ cudaError_t pcg_plan(const int *slice_ptr_host, const int *col_host, int n_slice
                      const double *grp_work, int blocks_per_sm, PcgLaunch *plan, PcgHalo *halo);
 // the most blocks a batch solve can use (its partial-sum buffer is sized for it)
 int pcg_max_group_blocks(int precision, int num_sms);
+// grid of the one-system general kernels: a slice per warp at most, at most
+// blocks_per_sm blocks per SM (0: as many as fit); 0 on error
+int pcg_general_grid(int precision, int n_slices, int num_sms, int blocks_per_sm);
 cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch &plan, const PcgArgs &a);
 // Grow a resident plan's dynamic shared memory by the multigrid arrays
 // (`extra` bytes); *ok = false (plan unchanged) when the block would no

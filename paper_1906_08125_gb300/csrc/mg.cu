@@ -1,6 +1,8 @@
-// mg.cu -- set-up of the multigrid preconditioner of the resident solver: a
-// three-level V-cycle for M Phi = f (App. B, eq. poisson_mat) built from the
-// matrix alone, at mesh_load.
+// mg.cu -- set-up of the multigrid preconditioners of the solver: a
+// three-level V-cycle for the resident kernels (mg_build) and a V-cycle of
+// as many levels as needed for the general kernels (gmg_build), both for
+// M Phi = f (App. B, eq. poisson_mat) and built from the matrix alone, at
+// mesh_load.
 //
 // Coarse spaces by aggregation.  A pass of pairwise matching (Notay,
 // "An aggregation-based algebraic multigrid method", ETNA 37, 2010) takes the
@@ -20,6 +22,7 @@
 // stored in FP32) is applied row by row by the block that owns the row.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -67,33 +70,52 @@ static int pairwise_pass(const Csr &A, const std::vector<int> &part, std::vector
 
 // Galerkin product P^T A P for the piecewise-constant P of `agg`; an entry
 // exists where some A_ij is stored with a nonzero value (the pattern stays
-// symmetric whatever the rounding of the sums).
+// symmetric whatever the rounding of the sums).  Each coarse row gathers the
+// rows of its aggregate in increasing order and their entries in column
+// order, so every coarse entry is the sum of its fine entries in row-major
+// order; O(nnz) with a marker per coarse column.
 static Csr galerkin(const Csr &A, const std::vector<int> &agg, int na)
 {
-    std::vector<std::pair<long long, double>> e;
-    e.reserve(A.col.size());
+    std::vector<int> mp((size_t)na + 1, 0), mi((size_t)A.n);
     for (int i = 0; i < A.n; ++i)
-        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
-            if (A.val[k] != 0.0)
-                e.emplace_back((long long)agg[i] * na + agg[A.col[k]], A.val[k]);
-    std::stable_sort(e.begin(), e.end(),
-                     [](const std::pair<long long, double> &x, const std::pair<long long, double> &y) {
-                         return x.first < y.first;
-                     });
+        mp[agg[i] + 1] += 1;
+    for (int a = 0; a < na; ++a)
+        mp[a + 1] += mp[a];
+    {
+        std::vector<int> fill(mp.begin(), mp.end() - 1);
+        for (int i = 0; i < A.n; ++i)
+            mi[fill[agg[i]]++] = i;
+    }
     Csr C;
     C.n = na;
     C.ptr.assign((size_t)na + 1, 0);
-    for (size_t k = 0; k < e.size();) {
-        const long long key = e[k].first;
-        double s = 0.0;
-        for (; k < e.size() && e[k].first == key; ++k)
-            s += e[k].second;
-        C.col.push_back((int)(key % na));
-        C.val.push_back(s);
-        C.ptr[key / na + 1] += 1;
+    C.col.reserve(A.col.size() / 2);
+    C.val.reserve(A.col.size() / 2);
+    std::vector<int> mark((size_t)na, -1), cols;
+    std::vector<double> acc((size_t)na, 0.0);
+    for (int a = 0; a < na; ++a) {
+        cols.clear();
+        for (int m = mp[a]; m < mp[a + 1]; ++m) {
+            const int i = mi[m];
+            for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                if (A.val[k] == 0.0)
+                    continue;
+                const int b = agg[A.col[k]];
+                if (mark[b] != a) {
+                    mark[b] = a;
+                    acc[b] = 0.0;
+                    cols.push_back(b);
+                }
+                acc[b] += A.val[k];
+            }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int b : cols) {
+            C.col.push_back(b);
+            C.val.push_back(acc[b]);
+        }
+        C.ptr[a + 1] = (int)C.col.size();
     }
-    for (int i = 0; i < na; ++i)
-        C.ptr[i + 1] += C.ptr[i];
     return C;
 }
 
@@ -261,20 +283,23 @@ static bool dense_spd_inverse(std::vector<double> A, int n, std::vector<float> &
 
 }  // namespace
 
-bool mg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
-              int n_slices, int G, int passes0, int passes1, int max_coarse, MgHost *out)
+// The fine matrix in CSR from its sliced ELLPACK (rows without a diagonal --
+// padding -- are left empty; zero entries are dropped).
+static Csr sell_to_csr(const int *sptr, const int *scol, const double *sval, const double *dinv,
+                       int n_slices)
 {
-    *out = MgHost{};
     const int n = 32 * n_slices;
-    // the fine matrix in CSR (rows without a diagonal -- padding -- are left out)
     Csr A;
     A.n = n;
     A.ptr.assign((size_t)n + 1, 0);
+    A.col.reserve((size_t)sptr[n_slices]);
+    A.val.reserve((size_t)sptr[n_slices]);
+    std::vector<std::pair<int, double>> row;
     for (int s = 0; s < n_slices; ++s) {
         const int w = (sptr[s + 1] - sptr[s]) / 32;
         for (int l = 0; l < 32; ++l) {
             const int i = 32 * s + l;
-            std::vector<std::pair<int, double>> row;
+            row.clear();
             if (dinv[i] != 0.0)
                 for (int k = 0; k < w; ++k) {
                     const size_t e = (size_t)sptr[s] + (size_t)k * 32 + l;
@@ -289,6 +314,15 @@ bool mg_build(const int *sptr, const int *scol, const double *sval, const double
             A.ptr[i + 1] = (int)A.col.size();
         }
     }
+    return A;
+}
+
+bool mg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
+              int n_slices, int G, int passes0, int passes1, int max_coarse, MgHost *out)
+{
+    *out = MgHost{};
+    const int n = 32 * n_slices;
+    Csr A = sell_to_csr(sptr, scol, sval, dinv, n_slices);
     std::vector<int> part((size_t)n), row0_of((size_t)n);
     for (long long b = 0; b < G; ++b) {
         const int s0 = (int)((b * n_slices) / G), s1 = (int)(((b + 1) * n_slices) / G);
@@ -414,6 +448,204 @@ bool mg_build(const int *sptr, const int *scol, const double *sval, const double
             D[(size_t)q * n2 + r] = D[(size_t)r * n2 + q] = s;
         }
     return dense_spd_inverse(std::move(D), n2, m.a2inv);
+}
+
+// ---------------------------------------------------------------------------
+// Hierarchy of the general kernels.  The same matching passes and Galerkin
+// products, applied to the whole matrix (the general kernels have no block
+// ownership: a level's vectors live in global memory), within each system of
+// a batch; as many levels as it takes to bring every system down to
+// max_coarse rows.  Each level is stored like the fine one: 32-row slices,
+// each system's rows padded to whole slices, the matrix in sliced ELLPACK.
+// ---------------------------------------------------------------------------
+bool gmg_build(const int *sptr, const int *scol, const double *sval, const double *dinv,
+               int n_slices, int n_sys, const int *sys_slices, int passes0, int passes1,
+               int max_coarse, int max_levels, GmgHost *out)
+{
+    *out = GmgHost{};
+    if (n_sys < 1 || n_slices < 1)
+        return false;
+    const int n = 32 * n_slices;
+    Csr cur = sell_to_csr(sptr, scol, sval, dinv, n_slices);
+    std::vector<int> part((size_t)n, 0);
+    for (int g = 0; g < n_sys; ++g)
+        for (int i = 32 * sys_slices[g]; i < 32 * sys_slices[g + 1]; ++i)
+            part[i] = g;
+    // row of `cur` -> its row in the stored (padded) layout of its level
+    std::vector<int> pad_of((size_t)n);
+    for (int i = 0; i < n; ++i)
+        pad_of[i] = i;
+    int finer_rows = n;
+    out->lev.resize(1);
+    for (int l = 1; l <= max_levels; ++l) {
+        std::vector<int> agg, cpart;
+        Csr C = coarsen(cur, part, l == 1 ? passes0 : passes1, agg, cpart);
+        // rows without entries (the fine level's padding) are aggregates of
+        // their own: they belong to no aggregate, and are dropped
+        std::vector<int> renum((size_t)C.n, -1);
+        {
+            std::vector<char> keep((size_t)C.n, 0);
+            int live = 0;
+            for (int i = 0; i < cur.n; ++i)
+                if (cur.ptr[i + 1] > cur.ptr[i]) {
+                    keep[agg[i]] = 1;
+                    ++live;
+                }
+            int m = 0;
+            for (int a = 0; a < C.n; ++a)
+                if (keep[a])
+                    renum[a] = m++;
+            if (m < 1 || m >= live)
+                return false;                       // nothing was aggregated
+            if (m < C.n) {
+                Csr B;
+                B.n = m;
+                B.ptr.assign((size_t)m + 1, 0);
+                std::vector<int> bp((size_t)m);
+                for (int a = 0; a < C.n; ++a) {
+                    if (renum[a] < 0)
+                        continue;
+                    bp[renum[a]] = cpart[a];
+                    for (int k = C.ptr[a]; k < C.ptr[a + 1]; ++k) {
+                        B.col.push_back(renum[C.col[k]]);
+                        B.val.push_back(C.val[k]);
+                    }
+                    B.ptr[renum[a] + 1] = (int)B.col.size();
+                }
+                C = std::move(B);
+                cpart = std::move(bp);
+            }
+        }
+        for (int a = 1; a < C.n; ++a)
+            if (cpart[a] < cpart[a - 1])
+                return false;                       // aggregates are numbered system by system
+        GmgLevelHost L;
+        std::vector<int> cnt((size_t)n_sys, 0), first((size_t)n_sys + 1, 0);
+        for (int a = 0; a < C.n; ++a)
+            cnt[cpart[a]] += 1;
+        L.gsl.assign((size_t)n_sys + 1, 0);
+        for (int g = 0; g < n_sys; ++g) {
+            L.gsl[g + 1] = L.gsl[g] + (cnt[g] + 31) / 32;
+            first[g + 1] = first[g] + cnt[g];
+        }
+        L.n_slices = L.gsl[n_sys];
+        const int rows = 32 * L.n_slices;
+        std::vector<int> pidx((size_t)C.n);
+        for (int a = 0; a < C.n; ++a)
+            pidx[a] = 32 * L.gsl[cpart[a]] + (a - first[cpart[a]]);
+        // finer rows -> this level's rows, and the members of each row
+        L.agg.assign((size_t)finer_rows, -1);
+        for (int i = 0; i < cur.n; ++i)
+            if (agg[i] >= 0 && renum[agg[i]] >= 0 && cur.ptr[i + 1] > cur.ptr[i])
+                L.agg[pad_of[i]] = pidx[renum[agg[i]]];
+        L.mptr.assign((size_t)rows + 1, 0);
+        for (int p = 0; p < finer_rows; ++p)
+            if (L.agg[p] >= 0)
+                L.mptr[L.agg[p] + 1] += 1;
+        for (int q = 0; q < rows; ++q)
+            L.mptr[q + 1] += L.mptr[q];
+        L.midx.assign((size_t)L.mptr[rows], 0);
+        {
+            std::vector<int> fill(L.mptr.begin(), L.mptr.end() - 1);
+            for (int p = 0; p < finer_rows; ++p)
+                if (L.agg[p] >= 0)
+                    L.midx[fill[L.agg[p]]++] = p;
+        }
+        bool coarsest = true;
+        for (int g = 0; g < n_sys; ++g)
+            coarsest = coarsest && cnt[g] <= max_coarse;
+        if (!coarsest) {
+            // the level's matrix in sliced ELLPACK (padding entries: column
+            // of the row itself, value 0), 1 / diagonal, Gershgorin bound
+            std::vector<int> src((size_t)rows, -1);
+            for (int a = 0; a < C.n; ++a)
+                src[pidx[a]] = a;
+            L.sptr.assign((size_t)L.n_slices + 1, 0);
+            for (int sl = 0; sl < L.n_slices; ++sl) {
+                int w = 0;
+                for (int k = 0; k < 32; ++k) {
+                    const int a = src[32 * sl + k];
+                    if (a >= 0)
+                        w = std::max(w, C.ptr[a + 1] - C.ptr[a]);
+                }
+                L.sptr[sl + 1] = L.sptr[sl] + 32 * w;
+            }
+            L.col.assign((size_t)L.sptr[L.n_slices], 0);
+            L.val.assign((size_t)L.sptr[L.n_slices], 0.0);
+            L.dinv.assign((size_t)rows, 0.0);
+            for (int sl = 0; sl < L.n_slices; ++sl) {
+                const int w = (L.sptr[sl + 1] - L.sptr[sl]) / 32;
+                for (int k = 0; k < 32; ++k) {
+                    const int q = 32 * sl + k, a = src[q];
+                    const int len = a >= 0 ? C.ptr[a + 1] - C.ptr[a] : 0;
+                    for (int c = 0; c < w; ++c) {
+                        const size_t e = (size_t)L.sptr[sl] + (size_t)c * 32 + k;
+                        if (c < len) {
+                            const int kk = C.ptr[a] + c;
+                            L.col[e] = pidx[C.col[kk]];
+                            L.val[e] = C.val[kk];
+                            if (C.col[kk] == a)
+                                L.dinv[q] = C.val[kk] > 0.0 ? 1.0 / C.val[kk] : 0.0;
+                        } else {
+                            L.col[e] = q;
+                        }
+                    }
+                    if (a >= 0 && !(L.dinv[q] > 0.0))
+                        return false;
+                }
+            }
+            L.lmax = gershgorin(C);
+        }
+        out->lev.push_back(std::move(L));
+        if (coarsest) {
+            // each system's coarsest matrix, inverted (systems in parallel)
+            out->cn = cnt;
+            out->ioff.assign((size_t)n_sys + 1, 0);
+            for (int g = 0; g < n_sys; ++g)
+                out->ioff[g + 1] = out->ioff[g] + (long long)cnt[g] * cnt[g];
+            out->inv.assign((size_t)out->ioff[n_sys], 0.f);
+            std::vector<char> ok((size_t)n_sys, 1);
+            auto work = [&](int t, int nt) {
+                for (int g = t; g < n_sys; g += nt) {
+                    const int m = cnt[g], a0 = first[g];
+                    if (m == 0)
+                        continue;
+                    std::vector<double> D((size_t)m * m, 0.0);
+                    for (int a = a0; a < a0 + m; ++a)
+                        for (int k = C.ptr[a]; k < C.ptr[a + 1]; ++k)
+                            D[(size_t)(a - a0) * m + (C.col[k] - a0)] = C.val[k];
+                    for (int q = 0; q < m; ++q)
+                        for (int r = 0; r < q; ++r) {
+                            const double v = 0.5 * (D[(size_t)q * m + r] + D[(size_t)r * m + q]);
+                            D[(size_t)q * m + r] = D[(size_t)r * m + q] = v;
+                        }
+                    std::vector<float> inv;
+                    if (!dense_spd_inverse(std::move(D), m, inv)) {
+                        ok[g] = 0;
+                        continue;
+                    }
+                    std::copy(inv.begin(), inv.end(), out->inv.begin() + out->ioff[g]);
+                }
+            };
+            int nt = (int)std::thread::hardware_concurrency();
+            nt = std::max(1, std::min(nt, std::min(n_sys, 32)));
+            std::vector<std::thread> th;
+            for (int t = 1; t < nt; ++t)
+                th.emplace_back(work, t, nt);
+            work(0, nt);
+            for (auto &t : th)
+                t.join();
+            for (int g = 0; g < n_sys; ++g)
+                if (!ok[g])
+                    return false;
+            return true;
+        }
+        cur = std::move(C);
+        part = std::move(cpart);
+        pad_of = std::move(pidx);
+        finer_rows = rows;
+    }
+    return false;
 }
 
 }  // namespace pf

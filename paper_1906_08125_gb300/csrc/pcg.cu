@@ -1,7 +1,8 @@
 // pcg.cu -- the space-charge Poisson solve M Phi = f (App. B, eq. poisson_mat)
 // as one persistent cooperative kernel per solve: preconditioned conjugate
-// gradients (Jacobi, or a Chebyshev polynomial in D^-1 M with a two-level
-// coarse correction), warm-started from the previous potential.
+// gradients (Jacobi, a Chebyshev polynomial in D^-1 M with a two-level
+// coarse correction, or an aggregation multigrid V-cycle), warm-started from
+// the previous potential.
 //
 // The matrix is stored as sliced ELLPACK with slices of 32 rows (one warp
 // per slice, one thread per row, columns of a slice interleaved so each load
@@ -15,7 +16,10 @@
 // barrier or, for the Chebyshev steps of the FP32 solve, through tagged
 // words that each block polls for the values it reads; the general kernels
 // (batches of systems, systems too large for the resident blocks) keep the
-// vectors in global memory and synchronise per group of blocks.
+// vectors in global memory and synchronise per group of blocks.  Both have a
+// V-cycle of their own: the resident one keeps its two coarse levels in
+// shared memory, block by block; the general one walks any number of levels
+// whose vectors live in global memory, like the fine level's.
 //
 // A standard CG iteration takes two grid-wide reductions (p.Ap and r.z).
 // Reductions: within the warp, in warp order within the block, then every
@@ -501,15 +505,230 @@ __device__ __forceinline__ ACC sell_row(const PcgArgs &a, const V *__restrict__ 
                            : sell_row_u<ACC, false>(val, a.col, b, width, lane, X);
 }
 
-// FP64 Jacobi-PCG (the plain FP64 form)
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle of the general kernels (z = B r, B symmetric positive
+// definite).  Levels 0 (the fine matrix) .. L (coarsest) in GmgLevel records
+// in device memory, every level's vectors in global memory; the warps of a
+// system stride over that system's slices of each level exactly as over the
+// fine slices, so a warp owns the same rows of a level throughout and reads
+// other warps' values only after a barrier of the system.  On each level
+// above the coarsest: Chebyshev smoothing of D^-1 A_l from zero (the
+// residual rc kept by recurrence), the residual after it, restriction by
+// sums over the aggregates; on the coarsest, x = A_L^-1 b per system (dense
+// inverse); on the way up, x_l += P x_l+1 with the residual rc - A_l P x_l+1
+// (the product gathers x_l+1 through the aggregate map, so the prolonged
+// vector is never stored) and the same Chebyshev steps from there.  Pre- and
+// post-smoothing use the same polynomial, so B is symmetric; P^T A P
+// Galerkin coarse matrices and the exact coarsest solve keep it definite.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ const T *gl_val(const GmgLevel &L);
+template <> __device__ __forceinline__ const float *gl_val<float>(const GmgLevel &L) { return L.val32; }
+template <> __device__ __forceinline__ const double *gl_val<double>(const GmgLevel &L) { return L.val64; }
+template <typename T> __device__ __forceinline__ const T *gl_dinv(const GmgLevel &L);
+template <> __device__ __forceinline__ const float *gl_dinv<float>(const GmgLevel &L) { return L.dinv32; }
+template <> __device__ __forceinline__ const double *gl_dinv<double>(const GmgLevel &L) { return L.dinv64; }
+template <typename T> __device__ __forceinline__ T gl_c1(const GmgLevel &L, int j);
+template <> __device__ __forceinline__ float gl_c1<float>(const GmgLevel &L, int j) { return L.c1f[j]; }
+template <> __device__ __forceinline__ double gl_c1<double>(const GmgLevel &L, int j) { return L.c1[j]; }
+template <typename T> __device__ __forceinline__ T gl_c2(const GmgLevel &L, int j);
+template <> __device__ __forceinline__ float gl_c2<float>(const GmgLevel &L, int j) { return L.c2f[j]; }
+template <> __device__ __forceinline__ double gl_c2<double>(const GmgLevel &L, int j) { return L.c2[j]; }
+template <typename T> __device__ __forceinline__ T gl_ith(const GmgLevel &L);
+template <> __device__ __forceinline__ float gl_ith<float>(const GmgLevel &L) { return L.inv_thetaf; }
+template <> __device__ __forceinline__ double gl_ith<double>(const GmgLevel &L) { return L.inv_theta; }
+
+// this warp's slices of level L (its system's slices, strided by the system's warps)
+#define FOR_LEVEL_SLICES(L, sp, s)                                                          \
+    for (int s = (L).gsl[(sp).g] + (sp).gw, s##_end = (L).gsl[(sp).g + 1]; s < s##_end;      \
+         s += (sp).nw)
+
+// row `lane` of slice s of level L times the vector X
+template <typename T, typename X>
+__device__ __forceinline__ T gl_row(const GmgLevel &L, bool stream, int s, int lane, X x)
+{
+    const int b = L.sptr[s], width = (L.sptr[s + 1] - b) >> 5;
+    return stream ? sell_row_u<T, true>(gl_val<T>(L), L.col, b, width, lane, x)
+                  : sell_row_u<T, false>(gl_val<T>(L), L.col, b, width, lane, x);
+}
+
+// first Chebyshev step from zero: d_0 = D^-1 b / theta, x = d_0, rc = b
+template <typename T, typename B>
+__device__ __forceinline__ void gmg_start(const GmgLevel &L, const Span &sp, int lane, B bfun)
+{
+    const T *dinv = gl_dinv<T>(L);
+    T *x = (T *)L.x, *rc = (T *)L.rc, *d1 = (T *)L.d[1];
+    const T ith = gl_ith<T>(L);
+    FOR_LEVEL_SLICES(L, sp, s)
+    {
+        const int row = 32 * s + lane;
+        const T b = bfun(row);
+        const T d = dinv[row] * b * ith;
+        x[row] = d;
+        rc[row] = b;
+        d1[row] = d;
+    }
+}
+
+// Chebyshev steps 1 .. deg-1 (d_j in d[(j+1)&1], each after a barrier that
+// completes d_j-1); with final_res one more barrier and rc -= A d_deg-1, the
+// residual of x
+template <typename T>
+__device__ bool gmg_steps(const PcgArgs &a, const GmgLevel &L, bool stream, int deg,
+                          const Span &sp, int lane, bool final_res)
+{
+    const T *dinv = gl_dinv<T>(L);
+    T *x = (T *)L.x, *rc = (T *)L.rc;
+    for (int j = 1; j < deg; ++j) {
+        const T *cur = (const T *)L.d[j & 1];
+        T *nxt = (T *)L.d[(j + 1) & 1];
+        const T c1 = gl_c1<T>(L, j - 1), c2 = gl_c2<T>(L, j - 1);
+        if (!grid_sync(a))
+            return false;
+        FOR_LEVEL_SLICES(L, sp, s)
+        {
+            const int row = 32 * s + lane;
+            const T ad = gl_row<T>(L, stream, s, lane, [cur](int c) { return __ldcg(cur + c); });
+            const T r = rc[row] - ad;
+            const T d = c1 * cur[row] + c2 * (dinv[row] * r);
+            x[row] = x[row] + d;
+            rc[row] = r;
+            if (j + 1 < deg || final_res)
+                nxt[row] = d;
+        }
+    }
+    if (final_res) {
+        const T *cur = (const T *)L.d[deg & 1];
+        if (!grid_sync(a))
+            return false;
+        FOR_LEVEL_SLICES(L, sp, s)
+        {
+            const int row = 32 * s + lane;
+            rc[row] = rc[row] - gl_row<T>(L, stream, s, lane, [cur](int c) { return __ldcg(cur + c); });
+        }
+    }
+    return true;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// coarsest level C below F: b = R rc_F, then x = A_C^-1 b, one warp per row
+// of the system's dense inverse
+template <typename T>
+__device__ bool gmg_coarsest(const PcgArgs &a, const GmgLevel &C, const GmgLevel &F,
+                             const Span &sp, int lane)
+{
+    T *b = (T *)C.rc, *x = (T *)C.x;
+    const T *rcf = (const T *)F.rc;
+    if (!grid_sync(a))
+        return false;
+    FOR_LEVEL_SLICES(C, sp, s)
+    {
+        const int row = 32 * s + lane;
+        T v = 0;
+        for (int m = C.mptr[row]; m < C.mptr[row + 1]; ++m)
+            v += __ldcg(rcf + C.midx[m]);
+        b[row] = v;
+    }
+    if (!grid_sync(a))
+        return false;
+    const int n = a.gmg_cn[sp.g], r0 = 32 * C.gsl[sp.g];
+    const float *inv = a.gmg_inv + a.gmg_ioff[sp.g];
+    for (int q = sp.gw; q < n; q += sp.nw) {
+        const float *row = inv + (size_t)q * n;
+        T v = 0;
+        for (int c = lane; c < n; c += 32)
+            v += (T)__ldg(row + c) * __ldcg(b + r0 + c);
+        v = warp_sum_t(v);
+        if (lane == 0)
+            x[r0 + q] = v;
+    }
+    return grid_sync(a);
+}
+
+// level L on the way up from the coarser level C: x += P x_C, rc -= A P x_C,
+// then the smoothing steps from there; a barrier at the end when a finer
+// level reads x next
+template <typename T>
+__device__ bool gmg_up(const PcgArgs &a, const GmgLevel &L, const GmgLevel &C, bool stream,
+                       int deg, const Span &sp, int lane, bool barrier)
+{
+    const T *dinv = gl_dinv<T>(L);
+    T *x = (T *)L.x, *rc = (T *)L.rc, *d1 = (T *)L.d[1];
+    const T *xc = (const T *)C.x;
+    const int *agg = C.agg;
+    const T ith = gl_ith<T>(L);
+    FOR_LEVEL_SLICES(L, sp, s)
+    {
+        const int row = 32 * s + lane;
+        const T ae = gl_row<T>(L, stream, s, lane, [xc, agg](int c) {
+            const int q = __ldg(agg + c);
+            return q >= 0 ? __ldcg(xc + q) : T(0);
+        });
+        const int q = __ldg(agg + row);
+        const T e = q >= 0 ? __ldcg(xc + q) : T(0);
+        const T r = rc[row] - ae;
+        const T d = dinv[row] * r * ith;
+        x[row] = (x[row] + e) + d;
+        rc[row] = r;
+        d1[row] = d;
+    }
+    if (!gmg_steps<T>(a, L, stream, deg, sp, lane, false))
+        return false;
+    return barrier ? grid_sync(a) : true;
+}
+
+// z = B r: b0 = r on the fine rows, the result in the fine level's x; the
+// caller reads z of other rows only after its next barrier
+template <typename T>
+__device__ bool gmg_vcycle(const PcgArgs &a, const Span &sp, int lane, const T *b0)
+{
+    const int nl = a.gmg_nlev;
+    for (int l = 0; l < nl; ++l) {
+        const GmgLevel &L = a.gmg[l];
+        const int deg = l == 0 ? a.gmg_deg0 : a.gmg_deg1;
+        if (l == 0) {
+            gmg_start<T>(L, sp, lane, [b0](int row) { return b0[row]; });
+        } else {
+            if (!grid_sync(a))
+                return false;
+            const T *rcf = (const T *)a.gmg[l - 1].rc;
+            const int *mp = L.mptr, *mi = L.midx;
+            gmg_start<T>(L, sp, lane, [rcf, mp, mi](int row) {
+                T v = 0;
+                for (int m = mp[row]; m < mp[row + 1]; ++m)
+                    v += __ldcg(rcf + mi[m]);
+                return v;
+            });
+        }
+        if (!gmg_steps<T>(a, L, l == 0 && a.stream_matrix, deg, sp, lane, true))
+            return false;
+    }
+    if (!gmg_coarsest<T>(a, a.gmg[nl], a.gmg[nl - 1], sp, lane))
+        return false;
+    for (int l = nl - 1; l >= 0; --l)
+        if (!gmg_up<T>(a, a.gmg[l], a.gmg[l + 1], l == 0 && a.stream_matrix,
+                       l == 0 ? a.gmg_deg0 : a.gmg_deg1, sp, lane, l > 0))
+            return false;
+    return true;
+}
+
+// FP64 PCG (the plain FP64 form): Jacobi, or the multigrid V-cycle where the
+// hierarchy is in use (z = B r after the update of r; the same reductions)
 __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
 {
     grid_sync_init();
     const int lane = threadIdx.x & 31;
     const Span sp = row_span(a);
+    const bool mg = a.gmg_nlev > 0;
     int set = 0;
 
-    // r = f - M x, z = D^-1 r, p_old = 0
+    // r = f - M x, z = B r, p_old = 0
     double acc[3] = {0.0, 0.0, 0.0}, tot[3];
     FOR_SLICES(sp, s)
     {
@@ -520,13 +739,24 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
                                      [xv](int j) { return __ldcg(xv + j); });
         double f = rhs_entry(a, row);
         double r = f - ax;
-        double z = a.dinv64[row] * r;
         a.r[row] = r;
-        a.z[row] = z;
+        if (!mg) {
+            double z = a.dinv64[row] * r;
+            a.z[row] = z;
+            acc[0] += r * z;
+        }
         a.p0[row] = 0.0;
-        acc[0] += r * z;
         acc[1] += r * r;
         acc[2] += f * f;
+    }
+    if (mg) {
+        if (!gmg_vcycle<double>(a, sp, lane, a.r))
+            return;
+        FOR_SLICES(sp, s)
+        {
+            int row = s * 32 + lane;
+            acc[0] += a.r[row] * a.z[row];
+        }
     }
     if (!grid_sum<3>(acc, set, a, tot))
         return;
@@ -567,7 +797,7 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
             return;
         set ^= 1;
         double alpha = pt2[1];
-        // phase B: x += alpha p, r -= alpha Ap, z = D^-1 r
+        // phase B: x += alpha p, r -= alpha Ap, z = B r
         double acc2[2] = {0.0, 0.0}, t3[3];
         FOR_SLICES(sp, s)
         {
@@ -575,11 +805,22 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg64(PcgArgs a)
             double p = pnew[row];
             a.x[row] = a.x[row] + alpha * p;
             double r = a.r[row] - alpha * a.ap[row];
-            double z = a.dinv64[row] * r;
             a.r[row] = r;
-            a.z[row] = z;
-            acc2[0] += r * z;
+            if (!mg) {
+                double z = a.dinv64[row] * r;
+                a.z[row] = z;
+                acc2[0] += r * z;
+            }
             acc2[1] += r * r;
+        }
+        if (mg) {
+            if (!gmg_vcycle<double>(a, sp, lane, a.r))
+                return;
+            FOR_SLICES(sp, s)
+            {
+                int row = s * 32 + lane;
+                acc2[0] += a.r[row] * a.z[row];
+            }
         }
         if (!grid_sum_f<2, 3, PCG_BLOCK>(acc2, set, a, t3, [rz](double *q) { q[2] = q[0] / rz; }))
             return;
@@ -665,6 +906,15 @@ __device__ bool precond_global(const PcgArgs &a, const Span &sp, int lane)
     return true;
 }
 
+// the general FP32 solver's preconditioner: the V-cycle where the hierarchy
+// is in use, else the polynomial (with its coarse correction) or Jacobi
+__device__ __forceinline__ bool precond_general(const PcgArgs &a, const Span &sp, int lane)
+{
+    if (a.gmg_nlev > 0)
+        return gmg_vcycle<float>(a, sp, lane, a.r32);
+    return precond_global(a, sp, lane);
+}
+
 // FP32 PCG inside FP64 iterative refinement (see the resident form below)
 __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
 {
@@ -732,7 +982,7 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
             a.p32_0[row] = 0.f;
         }
         const int it0 = it;
-        if (!precond_global(a, sp, lane))
+        if (!precond_general(a, sp, lane))
             return;
         DF acc2[2] = {{0.f, 0.f}, {0.f, 0.f}};
         double t2[2];
@@ -784,7 +1034,7 @@ __global__ void __launch_bounds__(PCG_BLOCK, 4) k_pcg32ir(PcgArgs a)
                 a.dx32[row] = a.dx32[row] + alpha * pv[row];
                 a.r32[row] = a.r32[row] - alpha * apv[row];
             }
-            if (!precond_global(a, sp, lane))
+            if (!precond_general(a, sp, lane))
                 return;
             DF acc3[2] = {{0.f, 0.f}, {0.f, 0.f}};
             double t3[3];
@@ -2744,22 +2994,25 @@ cudaError_t pcg_plan(const int *slice_ptr, const int *col, int n_slices, int num
         *halo = PcgHalo{};
     }
     // general path: vectors in global memory, any size
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, precision == PIC_PREC_FP64 ? (const void *)k_pcg64 : (const void *)k_pcg32ir,
-        PCG_BLOCK, 0);
-    if (e != cudaSuccess)
-        return e;
-    if (per_sm < 1)
+    plan->grid = pcg_general_grid(precision, n_slices, num_sms, blocks_per_sm);
+    if (plan->grid < 1)
         return cudaErrorInvalidConfiguration;
-    int max_blocks = per_sm * num_sms;
-    int want = (n_slices + PCG_WARPS - 1) / PCG_WARPS;  // one slice per warp
-    int cap = 2 * num_sms;                              // barrier cost grows with blocks
-    plan->grid = want < cap ? (want < 1 ? 1 : want) : cap;
-    if (plan->grid > max_blocks)
-        plan->grid = max_blocks;
     plan->block = PCG_BLOCK;
     return cudaSuccess;
+}
+
+int pcg_general_grid(int precision, int n_slices, int num_sms, int blocks_per_sm)
+{
+    const int max_blocks = pcg_max_group_blocks(precision, num_sms);
+    if (max_blocks < 1)
+        return 0;
+    // as many blocks as fit by default: the products are bound by memory
+    // latency, and every resident warp adds loads in flight (on the 7.9M-tet
+    // tip 4 blocks per SM solve in 0.67x the time of 2, barriers included)
+    const int want = (n_slices + PCG_WARPS - 1) / PCG_WARPS;   // one slice per warp
+    const int cap = blocks_per_sm > 0 ? blocks_per_sm * num_sms : max_blocks;
+    int grid = want < cap ? (want < 1 ? 1 : want) : cap;
+    return grid < max_blocks ? grid : max_blocks;
 }
 
 // dynamic shared memory a resident block may take with the multigrid arrays

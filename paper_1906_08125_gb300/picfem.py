@@ -69,7 +69,7 @@ class MeshInfo(C.Structure):
                 ("pcg_grid", C.c_int32), ("particle_grid", C.c_int32),
                 ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("n_rep", C.c_int32), ("n_rows", C.c_int32), ("pcg_resident", C.c_int32),
-                ("graph", C.c_int32)]
+                ("graph", C.c_int32), ("mg_levels", C.c_int32), ("mg_coarse_rows", C.c_int32)]
 
 
 PROF_MAX = 16
