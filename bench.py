@@ -96,7 +96,7 @@ def ncu_traffic(kernel, workload):
             d = json.load(f)
     except Exception:
         return None
-    e = d.get(kernel)
+    e = d.get(f"{kernel}@{workload}") or d.get(kernel)
     if not e or e.get("source_sha") != source_sha():
         return None
     if e.get("workload") != workload:
@@ -371,13 +371,8 @@ def roofline(res, fp64):
         st, prev = res["stats"], res["prev_alive"]
     s = 8 if fp64 else 4
     rec = 128 if fp64 else 64
-    cheb = res["params"].get("pcg_cheb_degree", 0)
     tun = res.get("tuning") or {}
-    if tun.get("pcg_cheb_local") == 4:
-        # the V-cycle: 2 k0 fine-level products per application (smoothing
-        # before and after, the residual between) plus the CG's own; the
-        # coarse levels' products are under 15 % of a fine one and not counted
-        cheb = 2 * tun.get("pcg_mg_degree0", 3) + 1
+    cheb = precond_products(tun, res["params"])
     alg = {
         "step_fused": sum(bytes_step_fused(int(pa), row, s, info) for pa, row in zip(prev, st)),
         "pcg": sum(bytes_pcg_min(row, info, fp64) for row in st),
@@ -485,11 +480,12 @@ def run_ensemble(n_rep, steps, warmup):
     P.load()
     b, cat = ensemble_inputs(n_rep)
     peak, kind = peaks()
-    # (the batched FP64 solve is Jacobi-PCG: the general FP64 kernels take no
-    # polynomial preconditioner)
+    # FP32+IR and FP64 with the same multigrid V-cycle (the default where
+    # pcg_cheb_degree >= 2), and FP64 with Jacobi
     forms = {"fp32_ir": dict(precision=K.PREC_FP32_IR, pcg_rtol=1e-6, pcg_cheb_degree=6),
+             "fp64_mg": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=6),
              "fp64": dict(precision=K.PREC_FP64, pcg_rtol=1e-6, pcg_cheb_degree=0)}
-    sequential_forms = ("fp32_ir", "fp64")
+    sequential_forms = ("fp32_ir", "fp64_mg", "fp64")
     ev = lambda: torch.cuda.Event(enable_timing=True)
     out = {"replicas": n_rep, "tets": int(b.mesh.n_tets), "nodes": int(b.mesh.n_nodes),
            "emitting_faces": int(b.mesh.n_faces), "sp_start": int(len(cat[3])),
@@ -510,7 +506,7 @@ def run_ensemble(n_rep, steps, warmup):
             state = (c.potential(), c.particles(), c.step_index)
             knobs, _, trials = autotune.tune(
                 c, steps=3, warmup=1, use_cache=False,
-                space={"particle_blocks_per_sm": (8, 16, 24), "pcg_cheb_degree": (4, 6)})
+                space={"particle_blocks_per_sm": (8, 16, 24), "pcg_mg_degree1": (2, 3)})
             entry["tuning"] = knobs
             entry["tuning_trials"] = len(trials)
             c.step(2, stats=False)                  # balance on the tuned solves
@@ -527,13 +523,15 @@ def run_ensemble(n_rep, steps, warmup):
         prof = c.profile_read()
         c.profile(False)
         pcg_ms = prof["pcg"][1] / prof["pcg"][0]
-        cheb = c.tuning()["pcg_cheb_degree"]
+        tun = c.tuning()
+        cheb = precond_products(tun, form)
         outer = int(np.median([s.pcg_outer for s in st]))
         is64 = form["precision"] == K.PREC_FP64
         alg = bytes_batch_pcg(ri, is64, cheb, outer)
         gbs = alg / (pcg_ms * 1e-3) / 1e9
         gbs_pre = bytes_batch_pcg(ri, is64, cheb, outer, minimal=False) / (pcg_ms * 1e-3) / 1e9
-        entry.update({"ms_per_step": round(ms, 3),
+        entry.update({"preconditioner": precond_name(tun, c.info()),
+                      "ms_per_step": round(ms, 3),
                       "replica_cycles_per_s": round(n_rep * 1e3 / ms, 1),
                       "sp_in_flight": int(st[-1].alive),
                       "pcg_ms_per_step": round(pcg_ms, 3),
@@ -632,35 +630,78 @@ def run_large(workload, steps, warmup):
     ctx.poisson_solve()
     ctx.step(warmup, stats=False)
     setup_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    st = ctx.step(steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    ctx.profile(True)
-    ctx.step(2, stats=False)
-    prof = ctx.profile_read()
-    ctx.profile(False)
+    tun = ctx.tuning()
+    snap = ctx.potential(), ctx.particles(), ctx.step_index
+
+    def timed(n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = ctx.step(n)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.step(2, stats=False)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        return st, e0.elapsed_time(e1) / n, prof["pcg"][1] / prof["pcg"][0]
+
+    st, ms, pcg_ms = timed(steps)
+    # the same steps from the same state with the two-level polynomial
+    # preconditioner the V-cycle replaced (context for the solver's speed-up)
+    two = None
+    if tun["pcg_cheb_local"] == 4:
+        ctx.set_tuning(pcg_cheb_local=3)
+        ctx.set_potential(snap[0])
+        ctx.set_particles(*snap[1])
+        ctx.step_index = snap[2]
+        ctx.step(2, stats=False)
+        st2, ms2, pcg2 = timed(5)
+        two = {"steps": 5, "ms_per_step": round(ms2, 3), "pcg_ms_per_step": round(pcg2, 3),
+               "pcg_iters": int(np.median([s.pcg_iters for s in st2]))}
     ctx.close()
-    pcg_ms = prof["pcg"][1] / prof["pcg"][0]
     row = {"pcg_iters": int(np.median([s.pcg_iters for s in st])),
            "pcg_outer": int(np.median([s.pcg_outer for s in st]))}
     alg = bytes_pcg_min(row, info, False)
     peak, kind = peaks()
     gbs = alg / (pcg_ms * 1e-3) / 1e9
-    gbs_pre = bytes_pcg(row, info, False, p["pcg_cheb_degree"]) / (pcg_ms * 1e-3) / 1e9
+    gbs_pre = bytes_pcg(row, info, False, precond_products(tun, p)) / (pcg_ms * 1e-3) / 1e9
     return {"workload": workload, "tets": info["n_tets"], "free_dofs": info["n_free"],
             "nnz": info["nnz"], "resident_solver": bool(info["pcg_resident"]),
+            "preconditioner": precond_name(tun, info),
             "sp_in_flight": int(st[-1].alive), "steps": steps, "warmup": warmup,
             "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 2), "unit": METRIC,
             "pcg_ms_per_step": round(pcg_ms, 3), "pcg_iters": row["pcg_iters"],
+            "pcg_grid": info["pcg_grid"],
             "roofline_pcg": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(gbs / peak, 4),
                              "alg_frac_incl_precond": round(gbs_pre / peak, 4),
                              "traffic": ncu_traffic("pcg", workload), "peak_source": kind},
+            "two_level_precond": two,
             "setup_s": round(setup_s, 1)}
+
+
+def precond_products(tun, p):
+    """Fine-level products per CG iteration, the CG's own included: k for
+    the Chebyshev polynomial of degree k, 2 k0 + 1 for the V-cycle with
+    fine-level smoothing degree k0 (k0 - 1 steps and the residual before the
+    coarse correction, the residual and k0 - 1 steps after it); the coarser
+    levels' products are not counted."""
+    if tun.get("pcg_cheb_local") == 4:
+        return 2 * tun.get("pcg_mg_degree0", 3) + 1
+    return p.get("pcg_cheb_degree", tun.get("pcg_cheb_degree", 0))
+
+
+def precond_name(tun, info):
+    local = tun.get("pcg_cheb_local")
+    if local == 4:
+        return (f"multigrid V-cycle, {info['mg_levels']} levels below the fine one, "
+                f"coarsest {info['mg_coarse_rows']} rows (dense inverse), Chebyshev "
+                f"smoothing degrees {tun['pcg_mg_degree0']} / {tun['pcg_mg_degree1']}")
+    if local == 3 or (local == 0 and tun.get("pcg_cheb_degree", 0) >= 2):
+        return f"Chebyshev({tun['pcg_cheb_degree']}) of D^-1 M" + (
+            " + aggregate coarse correction" if local == 3 else "")
+    return "Jacobi"
 
 
 def run_e2e(res, steps):
