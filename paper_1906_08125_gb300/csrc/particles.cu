@@ -50,16 +50,33 @@ __device__ double fn_current(double F, double phi, int model)
 // ---------------------------------------------------------------------------
 // walk records
 // ---------------------------------------------------------------------------
+// The walk issues one record fetch per face crossing, the lanes of a warp at
+// different records, so its loads cost L1 wavefronts rather than bytes: the
+// 64-byte FP32 record comes in two 32-byte loads (half the load instructions,
+// and half the wavefronts, of 16-byte loads; fused particle kernel 1.55 ->
+// 1.48 ms on the 1M-tet tip).  The FP64 record keeps 16-byte loads: the
+// 32-byte form cost its persistent walk a register and a block per SM.
 template <typename T>
 __device__ __forceinline__ T load_rec(const T *p)
 {
     static_assert(sizeof(T) % 16 == 0, "record size");
     T out;
-    const int4 *s = reinterpret_cast<const int4 *>(p);
-    int4 *d = reinterpret_cast<int4 *>(&out);
+    if constexpr (sizeof(T) == 64) {
+        const char *s = reinterpret_cast<const char *>(p);
+        unsigned *d = reinterpret_cast<unsigned *>(&out);
 #pragma unroll
-    for (int i = 0; i < (int)(sizeof(T) / 16); ++i)
-        d[i] = __ldg(s + i);
+        for (int i = 0; i < 2; ++i)
+            asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(d[8 * i + 0]), "=r"(d[8 * i + 1]), "=r"(d[8 * i + 2]), "=r"(d[8 * i + 3]),
+                  "=r"(d[8 * i + 4]), "=r"(d[8 * i + 5]), "=r"(d[8 * i + 6]), "=r"(d[8 * i + 7])
+                : "l"(s + 32 * i));
+    } else {
+        const int4 *s = reinterpret_cast<const int4 *>(p);
+        int4 *d = reinterpret_cast<int4 *>(&out);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(T) / 16); ++i)
+            d[i] = __ldg(s + i);
+    }
     return out;
 }
 
@@ -632,8 +649,11 @@ __device__ __forceinline__ void start_sp(const MeshView<R> &m, const RunConst &c
 // appended together and walk through the same records, so the warp's record
 // fetches share L1 lines; on the FP32 path that locality is worth more than
 // the lanes that idle behind the warp's longest walk.
+// (FP32: at most 40 registers, six blocks of 256 threads per SM -- the 32-byte
+// record loads would otherwise take it to 48 registers and five blocks; FP64,
+// whose default is the persistent form: at most 64, no spills)
 template <typename R>
-__global__ void __launch_bounds__(256) k_step_fused(MeshView<R> m, RunConst c,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 4) k_step_fused(MeshView<R> m, RunConst c,
                                                     const long long *stepp, int nq,
                                                     const long long *__restrict__ qoff,
                                                     Particles<R> A, Particles<R> B, int a,
