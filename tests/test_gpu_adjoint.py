@@ -94,15 +94,49 @@ def test_adjoint_leaves_the_forward_state(picfem):
     assert np.abs(a.potential() - b.potential()).max() <= 1e-9 * np.abs(b.potential()).max()
 
 
+def same_decisions(a, b):
+    """Two runs took the same discrete decisions (which SPs survive, in which
+    cell, with which ids) when their final states agree on ids and cells."""
+    pa, pb = a.particles(), b.particles()
+    if len(pa[3]) != len(pb[3]):
+        return False
+    oa, ob = np.argsort(pa[3]), np.argsort(pb[3])
+    return bool(np.array_equal(pa[3][oa], pb[3][ob]) and np.array_equal(pa[2][oa], pb[2][ob]))
+
+
+def _fp32_against_fp64(r32, r64, label):
+    """The FP32+IR gradient is the derivative of its own frozen-decision
+    model.  Where its run took every decision of the FP64 run (same collected
+    charge, same surviving SPs in the same cells) the two models are the same
+    and the gradients differ by FP32 rounding of the states only (2^-24 per
+    stored position, velocity and field value, carried through the steps'
+    derivatives): 1e-5 (measured on a GB300: 2e-10 / 1e-9 on the plate, 3.5e-7
+    / 1.5e-6 on the tip).  Where a decision differs (an SP on a face, a
+    quadrangle count rounding the other way) the models differ by whole SPs
+    and the bar is 2 % / 5 %."""
+    (c32, (Q, gE0, gwf)), (c64, (Q64, gE0o, gwfo)) = r32, r64
+    same = Q == Q64 and same_decisions(c32, c64)
+    print(f"{label}: FP32_IR against FP64: same decisions {same}, Q {Q / Q64 - 1 if Q64 else 0.0}, "
+          f"dQ/dE0 {gE0[0] / gE0o[0] - 1}, dQ/dphi {rel(gwf, gwfo)}")
+    if same:
+        assert gE0[0] == pytest.approx(gE0o[0], rel=1e-5)
+        assert rel(gwf, gwfo) <= 1e-5
+    else:
+        assert abs(Q - Q64) <= 2 * abs(Q64) / 100
+        assert gE0[0] == pytest.approx(gE0o[0], rel=2e-2)
+        assert rel(gwf, gwfo) <= 5e-2
+    return same
+
+
 def test_adjoint_fp32ir_close_to_fp64(picfem, oracle_grad):
     (Qo, gE0o, gwfo), tape = oracle_grad
-    c, (Q, gE0, gwf) = gpu_adjoint(picfem, ckpt=4, precision=K.PREC_FP32_IR, pcg_rtol=1e-8,
-                                   pcg_cheb_degree=4)
-    print("FP32_IR adjoint against FP64: Q", Q / tape.Q_recorded - 1, "dQ/dE0",
-          gE0[0] / gE0o - 1, "dQ/dphi", rel(gwf, gwfo))
-    assert abs(Q - tape.Q_recorded) <= 2 * abs(tape.Q_recorded) / 100
-    assert gE0[0] == pytest.approx(gE0o, rel=2e-2)
-    assert rel(gwf, gwfo) <= 5e-2
+    r32 = gpu_adjoint(picfem, ckpt=4, precision=K.PREC_FP32_IR, pcg_rtol=1e-8,
+                      pcg_cheb_degree=4)
+    r64 = gpu_adjoint(picfem, ckpt=4)
+    assert r64[1][0] == pytest.approx(tape.Q_recorded, rel=1e-14)
+    assert r64[1][1][0] == pytest.approx(gE0o, rel=1e-6)
+    # this seeded case takes every decision of the FP64 run, so the tight bar applies
+    assert _fp32_against_fp64(r32, r64, "plate")
 
 
 def test_adjoint_batch_replicas(picfem):
@@ -186,3 +220,9 @@ def test_adjoint_fp64_matches_oracle_on_a_tip(picfem, oracle_mod):
     # the emitting faces on the tip (above the cathode plane) take part
     fz = mesh.xyz[mesh.face_nodes].mean(axis=1)[:, 2]
     assert np.abs(gwfo[fz > 1e-9]).max() > 0
+    # the FP32+IR form on the same tip against this FP64 run
+    c32 = picfem.Context(dict(p, precision=K.PREC_FP32_IR, pcg_rtol=1e-8,
+                              pcg_cheb_degree=4)).mesh_load(mesh)
+    c32.set_particles(*parts)
+    r32 = (c32, c32.adjoint(N_STEPS, ckpt_every=4))
+    _fp32_against_fp64(r32, (c, (Q, gE0, gwf)), "tip")
