@@ -341,9 +341,9 @@ def run_gpu(args, rank, world, form, timed_steps, warmup, prof_steps=None):
 
 
 def ncu_onchip(kernel, workload):
-    """Shared-memory bytes per launch (and the DRAM share of peak) from the
-    committed single-kernel ncu summary, if it was taken on the current
-    kernel source."""
+    """On-chip pipe figures per launch from the committed single-kernel ncu
+    summaries (the solver's shared-memory wavefronts, the particle kernel's
+    L1 data-stage wavefronts), if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "ncu_onchip.json")
     try:
         with open(path) as f:
@@ -357,6 +357,7 @@ def ncu_onchip(kernel, workload):
 
 
 SMEM_BYTES_PER_CLK_PER_SM = 128      # one shared-memory wavefront per clock and SM
+L1_WAVEFRONTS_PER_CLK_PER_SM = 1     # one L1 data-stage wavefront per clock and SM
 
 
 def roofline(res, fp64):
@@ -406,12 +407,27 @@ def roofline(res, fp64):
                        for pa, row in zip(prev, st))
             r["bytes_model"] = ("N 2 (6s + 12) + X (16 + 12 s) + T_occ (48 + 12 s) + 16 N_nodes "
                                 "+ 64 per new SP, X = face crossings (counted)")
-            r["limiter"] = ("latency of the dependent walk-record fetches (one per face "
-                            "crossing, served from L1/L2 for neighbouring SPs)")
+            r["limiter"] = ("the L1 data stage: every face crossing loads a 64-byte walk "
+                            "record per lane, the lanes at different records (ncu: local/global "
+                            "wavefronts near 80 % of peak), with the dependent fetches' latency "
+                            "behind it")
             r["compulsory"] = {"bytes_per_launch": int(comp / kernels[name]["launches"]),
                                "achieved": round(comp / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                                "frac": round(comp / (ms * 1e-3) / 1e9 / peak, 4),
                                "model": "each SP state and each touched record once"}
+            oc = ncu_onchip("step_fused", WORKLOAD)
+            if oc:
+                mhz = oc.get("sm_mhz") or (res.get("clocks") or {}).get("sm_mhz")
+                sms = oc.get("sms", 152)
+                wpeak = sms * L1_WAVEFRONTS_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+                wach = oc["l1_wavefronts_per_launch"] / (oc["duration_ns"] * 1e-9) / 1e9
+                r["onchip"] = {"bound": "l1 data stage", "achieved": round(wach, 1),
+                               "peak": round(wpeak, 1), "unit": "G wavefronts/s",
+                               "frac": round(wach / wpeak, 4),
+                               "frac_ncu": oc.get("l1_wavefronts_pct_of_peak_ncu"),
+                               "basis": (f"one ncu-captured launch: local/global L1 data-stage "
+                                         f"wavefronts over its duration; {sms} SMs x 1 wavefront/clk "
+                                         f"at {mhz:.0f} MHz")}
         if name == "pcg":
             r["bytes_model"] = ("one SpMV per CG iteration: I (nnz (s + 4) + 4 (n + 1) + 80 n), "
                                 "s = value bytes; FP32 form + refinements x (12 nnz + 24 n)")

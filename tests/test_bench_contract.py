@@ -83,6 +83,27 @@ def test_solver_byte_model_structure():
     assert b(10, 2, 6) - b(10, 1, 6) >= 12 * INFO["nnz"]
 
 
+def test_particle_kernel_onchip_roofline(monkeypatch):
+    """When the fused particle kernel dominates, its roofline carries the L1
+    data-stage figure from the committed capture: wavefronts over the
+    captured duration against one wavefront per clock and SM."""
+    monkeypatch.setattr(bench, "peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "ncu_traffic", lambda kernel, workload: None)
+    oc = dict(l1_wavefronts_per_launch=3.0e8, duration_ns=1.5e6, sms=152, sm_mhz=2000,
+              l1_wavefronts_pct_of_peak_ncu=66.0)
+    monkeypatch.setattr(bench, "ncu_onchip", lambda kernel, workload: oc if kernel == "step_fused" else None)
+    st = stats(3)
+    res = dict(info=INFO, stats=st, prof={"pcg": (3, 1.0), "step_fused": (3, 2.0)},
+               prev_alive=np.array([100, 100, 100]), params={"pcg_cheb_degree": 6})
+    roof, _ = bench.roofline(res, fp64=False)
+    assert roof["kernel"] == "step_fused"
+    o = roof["onchip"]
+    assert o["achieved"] == pytest.approx(3.0e8 / 1.5e-3 / 1e9, abs=0.051)
+    assert o["peak"] == pytest.approx(152 * 2.0, abs=0.051)
+    assert o["frac"] == pytest.approx(o["achieved"] / o["peak"], abs=1e-4)
+    assert o["frac_ncu"] == 66.0 and roof["solver"]["kernel"] == "pcg"
+
+
 def test_ncu_traffic_only_with_the_measured_source(monkeypatch):
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
     e = d["pcg"]
