@@ -51,11 +51,11 @@ __device__ double fn_current(double F, double phi, int model)
 // walk records
 // ---------------------------------------------------------------------------
 // The walk issues one record fetch per face crossing, the lanes of a warp at
-// different records, so its loads cost L1 wavefronts rather than bytes: the
-// 64-byte FP32 record comes in two 32-byte loads (half the load instructions,
-// and half the wavefronts, of 16-byte loads; fused particle kernel 1.55 ->
-// 1.48 ms on the 1M-tet tip).  The FP64 record keeps 16-byte loads: the
-// 32-byte form cost its persistent walk a register and a block per SM.
+// different records, and is bound by the L1 data stage that hands the bytes
+// to the lanes: the 64-byte FP32 record comes in two 32-byte loads (fused
+// particle kernel 1.55 -> 1.48 ms on the 1M-tet tip against four 16-byte
+// loads).  The FP64 record keeps 16-byte loads: the 32-byte form cost its
+// persistent walk a register and a block per SM.
 template <typename T>
 __device__ __forceinline__ T load_rec(const T *p)
 {
@@ -78,6 +78,26 @@ __device__ __forceinline__ T load_rec(const T *p)
             d[i] = __ldg(s + i);
     }
     return out;
+}
+
+// The part of an FP32 record a walk step always needs, J^-1 and x0 (the first
+// 48 bytes: one 32-byte and one 16-byte load); the neighbour of the exit face
+// is read on its own once the face is known, and not at all in the last
+// tetrahedron -- the data stage then moves 52 bytes per crossing instead of 64
+// (fused particle kernel 1.48 -> 1.26 ms on the 1M-tet tip).
+__device__ __forceinline__ void load_rec_geometry(const TetRec32 *p, TetRec32 &rec)
+{
+    const char *base = reinterpret_cast<const char *>(p);
+    unsigned *d = reinterpret_cast<unsigned *>(&rec);
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]),
+          "=r"(d[7])
+        : "l"(base));
+    const int4 q = __ldg(reinterpret_cast<const int4 *>(base + 32));
+    d[8] = (unsigned)q.x;
+    d[9] = (unsigned)q.y;
+    d[10] = (unsigned)q.z;
+    d[11] = (unsigned)q.w;
 }
 
 // lambda_k = row_k(J^-1) . (r - x0), k = 1..3; lambda_0 = ((1 - l1) - l2) - l3
@@ -104,7 +124,11 @@ __device__ __forceinline__ int walk_step(const MeshView<R> &m, int walk_max, R r
                                          int &entered, R lam[4], int &steps, int &wraps)
 {
     using T = typename Rec<R>::type;
-    T rec = load_rec(m.rec + t);
+    T rec;
+    if constexpr (sizeof(R) == 4)
+        load_rec_geometry(m.rec + t, rec);      // rec.nb is not loaded
+    else
+        rec = load_rec(m.rec + t);
     barycentric<R>(rec, r, lam);
     int k = -1;
     R mn = 0;
@@ -122,7 +146,11 @@ __device__ __forceinline__ int walk_step(const MeshView<R> &m, int walk_max, R r
     if (steps >= walk_max)
         return FATE_LIMIT;
     ++steps;
-    int p = k == 0 ? rec.nb[0] : k == 1 ? rec.nb[1] : k == 2 ? rec.nb[2] : rec.nb[3];
+    int p;
+    if constexpr (sizeof(R) == 4)
+        p = __ldg(&m.rec[t].nb[k]);
+    else
+        p = k == 0 ? rec.nb[0] : k == 1 ? rec.nb[1] : k == 2 ? rec.nb[2] : rec.nb[3];
     if (p >= 0) {
         t = p >> 2;
         entered = p & 3;
