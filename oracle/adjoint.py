@@ -102,10 +102,18 @@ class Tape:
     Q_recorded: float
 
 
-class Geometry:
-    """P1 data of the oracle's mesh in numpy form."""
+# systems up to this many free DOFs are factored once (sparse LU); larger ones
+# (the 1M-tet tip: a factor of ~600M entries) are solved by the oracle's own
+# Jacobi-PCG to a relative residual of 1e-13 at every solve
+LU_MAX_ROWS = 60_000
+CG_RTOL = 1e-13
 
-    def __init__(self, orc):
+
+class Geometry:
+    """P1 data of the oracle's mesh in numpy form.  direct: True factor M,
+    False solve iteratively, None by size (LU_MAX_ROWS)."""
+
+    def __init__(self, orc, direct=None):
         m = orc.mesh
         self.tet = m.tet.astype(np.int64)
         jinv, x0, _ = orc.geometry()
@@ -116,7 +124,9 @@ class Geometry:
         self.dof = dof.astype(np.int64)               # -1 on Dirichlet nodes
         n = len(rowptr) - 1
         self.M = sp.csr_matrix((val, col, rowptr), shape=(n, n)).tocsc()
-        self.lu = spla.splu(self.M)
+        self.direct = n <= LU_MAX_ROWS if direct is None else bool(direct)
+        self.orc = orc
+        self.lu = spla.splu(self.M) if self.direct else None
         self.fN_unit = fN / orc.params["E0"]          # Neumann load per unit E0
         xyz = m.xyz
         A, B, Cc = (xyz[m.face_nodes[:, k]] for k in range(3))
@@ -125,6 +135,12 @@ class Geometry:
         self.face_tet = m.face_tet.astype(np.int64)
         self.n_nodes = m.n_nodes
         self.free = self.dof >= 0
+
+    def msolve(self, f):
+        """M^-1 f (M symmetric: the forward and the adjoint solves alike)"""
+        if self.direct:
+            return self.lu.solve(f)
+        return self.orc.solve(f, rtol=CG_RTOL)
 
     def lam(self, cell, r):
         """barycentric coordinates N_0..N_3 of points r in tetrahedra cell"""
@@ -140,7 +156,7 @@ class Geometry:
         coef = p["q"] * p["w_sp"] / p["eps0"]
         f = coef * W[self.free] * 2.0 ** -p["quant_bits"] + E0 * self.fN_unit[self.dof[self.free]]
         phi = np.zeros(self.n_nodes)
-        phi[self.free] = self.lu.solve(f)[self.dof[self.free]]
+        phi[self.free] = self.msolve(f)[self.dof[self.free]]
         return phi
 
     def field(self, phi):
@@ -157,7 +173,7 @@ class Geometry:
         fb = np.zeros(self.n_nodes)
         rhs = np.zeros(self.M.shape[0])
         rhs[self.dof[self.free]] = phibar[self.free]
-        fb[self.free] = self.lu.solve(rhs)[self.dof[self.free]]
+        fb[self.free] = self.msolve(rhs)[self.dof[self.free]]
         return fb
 
 
@@ -242,10 +258,10 @@ def replay(g, tape, E0, wf, keep=False):
     return (Q, saved) if keep else Q
 
 
-def prepare(orc, tape):
+def prepare(orc, tape, direct=None):
     """Geometry of the oracle's mesh, and one pass of the smooth model at
     theta0 that fixes the reference emission currents (omega = 1 there)."""
-    g = Geometry(orc)
+    g = Geometry(orc, direct)
     for st in tape.steps:
         st.J_ref = None
     replay(g, tape, tape.E0, tape.wf)

@@ -98,6 +98,8 @@ def lib(parallel: bool = False):
         L.or_push_relocate.argtypes = [P, C.c_int64, C.POINTER(Stats)]
         L.or_deposit.argtypes = [P]
         L.or_poisson_solve.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.or_solve.argtypes = [P, P, P, C.c_double, C.c_int32, C.POINTER(C.c_int32),
+                               C.POINTER(C.c_double)]
         L.or_step.argtypes = [P, C.c_int64, C.POINTER(Stats)]
         L.or_collide.argtypes = [P, C.c_int64]
         L.or_locate.argtypes = [P, C.c_int64, P, P, P, P]
@@ -276,6 +278,16 @@ class Oracle:
         it, rr = C.c_int32(0), C.c_double(0)
         _check(self.L.or_poisson_solve(self.h, C.byref(it), C.byref(rr)), "or_poisson_solve")
         return it.value, rr.value
+
+    def solve(self, f, x0=None, rtol=1e-13, max_iter=200_000):
+        """x with M x = f (free DOFs in the numbering of ``matrix``), Jacobi-PCG
+        from x0 (zero) to the relative residual rtol."""
+        f = np.ascontiguousarray(f, np.float64)
+        x = np.zeros_like(f) if x0 is None else np.array(x0, np.float64, copy=True)
+        it, rr = C.c_int32(0), C.c_double(0)
+        _check(self.L.or_solve(self.h, _p(f), _p(x), float(rtol), int(max_iter), C.byref(it),
+                               C.byref(rr)), "or_solve")
+        return x
 
     def step(self, n=1):
         stats = (Stats * max(1, n))()

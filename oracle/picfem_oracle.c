@@ -749,6 +749,23 @@ static int pcg(or_ctx *c, const double *f, double *x, int32_t *iters,
     return status;
 }
 
+/* M x = f for a right-hand side of the caller's (free DOFs, the numbering of
+ * or_matrix), by the same Jacobi-PCG from the x given, to ||f - M x|| <=
+ * rtol ||f|| (App. B, eq. poisson_mat); used by the reverse pass of the
+ * adjoint reference on systems too large for a direct factorisation */
+int or_solve(or_ctx *c, const double *f, double *x, double rtol, int32_t max_iter,
+             int32_t *iters, double *relres)
+{
+    const double rtol0 = c->p.pcg_rtol;
+    const int32_t max0 = c->p.pcg_max_iter;
+    c->p.pcg_rtol = rtol;
+    c->p.pcg_max_iter = max_iter;
+    int status = pcg(c, f, x, iters, relres);
+    c->p.pcg_rtol = rtol0;
+    c->p.pcg_max_iter = max0;
+    return status;
+}
+
 /* RHS f_i = (q w_sp / eps) sum_j N_i(r_j) + int_{Gamma_1} N_i E0 (eq.
  * poisson_rhs); the particle sum is the fixed-point W_i * 2^-S */
 int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres)

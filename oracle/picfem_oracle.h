@@ -120,6 +120,10 @@ int or_inject(or_ctx *c, int64_t step, int64_t *n_injected);
 int or_push_relocate(or_ctx *c, int64_t step, or_stats *st);
 int or_deposit(or_ctx *c);
 int or_poisson_solve(or_ctx *c, int32_t *iters, double *relres);
+/* M x = f for a caller's right-hand side f (free DOFs in or_matrix's
+ * numbering), Jacobi-PCG from the x given to ||f - M x|| <= rtol ||f|| */
+int or_solve(or_ctx *c, const double *f, double *x, double rtol, int32_t max_iter,
+             int32_t *iters, double *relres);
 int or_step(or_ctx *c, int64_t n_steps, or_stats *stats);
 void or_collide(or_ctx *c, int64_t step);
 

@@ -226,3 +226,49 @@ def test_adjoint_fp64_matches_oracle_on_a_tip(picfem, oracle_mod):
     c32.set_particles(*parts)
     r32 = (c32, c32.adjoint(N_STEPS, ckpt_every=4))
     _fp32_against_fp64(r32, (c, (Q, gE0, gwf)), "tip")
+
+
+def test_adjoint_on_the_full_tip_against_oracle_and_central_differences(picfem, oracle_mod):
+    """The C4 mesh (the 1M-tet tip), FP64, 3 steps of a seeded 3,000-SP
+    population (collected charge and emission from the apex), work functions
+    4.5 +/- 0.1 eV per face: pic_adjoint against the oracle's reverse pass
+    (same collected charge; dQ/dE0 and dQ/dphi within 1e-6), and the oracle's
+    reverse pass at this size against central differences of its smooth model
+    at h = 1e-4 (relative in E0; 1e-4 eV on the face of the largest
+    sensitivity): the reverse pass is pinned at the benchmark's own mesh, not
+    only on the small cases."""
+    import bench
+    from oracle import adjoint as A
+    from oracle import oracle as O
+    mesh, p0, _ = K.workload("tip_1m")
+    mesh.work_function = 4.5 + 0.1 * np.random.default_rng(3).uniform(-1, 1, mesh.n_faces)
+    parts = bench.bench_population(mesh, 3000, seed=17)
+    p = dict(p0, precision=K.PREC_FP64, pcg_rtol=1e-13, pcg_max_iter=200_000,
+             pcg_cheb_degree=0)
+    steps = 3
+    orc = O.Oracle(mesh, p, parallel=True)
+    orc.set_particles(*parts)
+    tape = A.record(orc, steps)
+    g = A.prepare(orc, tape)
+    assert not g.direct                       # iterative solves at this size
+    Qo, gE0o, gwfo = A.gradient(g, tape)
+    assert Qo != 0.0 and gE0o != 0.0
+    h = 1e-4
+    fd = (A.replay(g, tape, tape.E0 * (1 + h), tape.wf)
+          - A.replay(g, tape, tape.E0 * (1 - h), tape.wf)) / (2 * h * tape.E0)
+    assert gE0o == pytest.approx(fd, rel=1e-4)
+    f = int(np.argmax(np.abs(gwfo)))
+    e = np.zeros_like(tape.wf)
+    e[f] = 1.0
+    fdf = (A.replay(g, tape, tape.E0, tape.wf + 1e-4 * e)
+           - A.replay(g, tape, tape.E0, tape.wf - 1e-4 * e)) / 2e-4
+    assert gwfo[f] == pytest.approx(fdf, rel=1e-4)
+    c = picfem.Context(p).mesh_load(mesh)
+    c.set_particles(*parts)
+    Q, gE0, gwf = c.adjoint(steps, ckpt_every=2)
+    c.close()
+    print(f"tip_1m adjoint: Q {Q:.6e} ({Q / Qo - 1:.1e}), dQ/dE0 {gE0[0] / gE0o - 1:.1e}, "
+          f"dQ/dphi {rel(gwf, gwfo):.1e}, FD E0 {gE0o / fd - 1:.1e}, FD face {gwfo[f] / fdf - 1:.1e}")
+    assert Q == pytest.approx(tape.Q_recorded, rel=1e-14)
+    assert gE0[0] == pytest.approx(gE0o, rel=1e-6)
+    assert rel(gwf, gwfo) <= 1e-6

@@ -57,6 +57,22 @@ def test_replay_at_theta0_is_the_recorded_run(run):
     assert Q == pytest.approx(tape.Q_recorded, rel=1e-13)
 
 
+def test_iterative_solves_match_the_factorisation(run):
+    """The reverse pass with the oracle's own Jacobi-PCG at every solve (the
+    path meshes above LU_MAX_ROWS take) gives the collected charge and the
+    gradient of the factored path."""
+    mesh, p, tape, g = run
+    Q1, gE1, gw1 = A.gradient(g, tape)
+    g2 = A.prepare(g.orc, tape, direct=False)
+    assert g.direct and not g2.direct
+    Q2, gE2, gw2 = A.gradient(g2, tape)
+    assert Q2 == pytest.approx(Q1, rel=1e-11)
+    assert gE2 == pytest.approx(gE1, rel=1e-9)
+    assert np.abs(gw2 - gw1).max() <= 1e-9 * np.abs(gw1).max()
+    assert A.replay(g2, tape, tape.E0 * 1.01, tape.wf) == pytest.approx(
+        A.replay(g, tape, tape.E0 * 1.01, tape.wf), rel=1e-11)
+
+
 def test_gradient_matches_central_differences(run):
     mesh, p, tape, g = run
     Q, gE0, gwf = A.gradient(g, tape)
