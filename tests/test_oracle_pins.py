@@ -247,6 +247,23 @@ def test_pcg_against_direct_solve(oracle_mod, tip_small):
     assert np.all(phi[tip_small.dirichlet == 1] == 0.0)
 
 
+def test_solve_with_a_callers_rhs_against_direct_solve(oracle_mod, tip_small):
+    """or_solve (the Poisson PCG for any right-hand side, used by the adjoint
+    reference on large meshes) against a direct solve of the oracle's own
+    matrix, from zero and from a warm start."""
+    o = _oracle(oracle_mod, tip_small, pcg_rtol=1e-6, capacity=5000)
+    dof, rowptr, col, val, _ = o.matrix()
+    n = len(rowptr) - 1
+    M = sp.csr_matrix((val, col, rowptr), shape=(n, n))
+    f = np.random.default_rng(2).standard_normal(n)
+    x = spla.spsolve(M.tocsc(), f)
+    y = o.solve(f, rtol=1e-13)
+    assert np.abs(y - x).max() <= 1e-9 * np.abs(x).max()
+    assert np.linalg.norm(f - M @ y) <= 1e-13 * np.linalg.norm(f)
+    y2 = o.solve(f, x0=x + 1e-3 * np.abs(x).max(), rtol=1e-13)
+    assert np.abs(y2 - x).max() <= 1e-9 * np.abs(x).max()
+
+
 # --------------------------------------------------------------------------
 # walk relocation (Sec. II.B.2): brute force on tiny meshes
 # --------------------------------------------------------------------------
