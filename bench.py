@@ -848,6 +848,35 @@ PRECONDITIONERS = {0: "Jacobi / whole-matrix Chebyshev", 1: "block-local Chebysh
                    4: "multigrid V-cycle"}
 
 
+FP64_FLOPS_PER_CROSSING = 21   # r - x0 (3), three rows of J^-1 (9 mul + 6 add), lambda_0 (3)
+FP64_FLOPS_PER_SP = 20         # kick and drift (12), deposit weights and remainder (8)
+_FP64_RATE = []
+
+
+def fp64_walk_roofline(r):
+    """Roofline of the FP64 fused particle kernel against the measured FP64
+    FMA rate (pic_measure_fp64_rate; the survey asks for the FP64 ALU rate to
+    be measured, since it may bound the FP64 form on this part): its FP64
+    flops (per face crossing and per SP, counted from the step statistics of
+    the profiled pass) over its event time."""
+    from paper_1906_08125_gb300 import picfem
+    if not _FP64_RATE:
+        _FP64_RATE.append(picfem.measure_fp64_rate())
+    rate = _FP64_RATE[0]
+    n, ms = r["prof"]["step_fused"]
+    st, prev = r["prof_stats"], r["prof_prev_alive"]
+    flops = sum(FP64_FLOPS_PER_CROSSING * int(row["crossings"])
+                + FP64_FLOPS_PER_SP * (int(pa) + int(row["injected"]))
+                for pa, row in zip(prev, st))
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "step_fused", "achieved": round(ach, 4),
+            "peak": round(rate, 4), "unit": "TFLOP/s", "frac": round(ach / rate, 4),
+            "peak_source": "measured: pic_measure_fp64_rate (independent FP64 FMA chains, 2 flops each)",
+            "flops_model": f"{FP64_FLOPS_PER_CROSSING} per face crossing + {FP64_FLOPS_PER_SP} per SP",
+            "note": ("the FP64 walk issues its multiplies and adds separately (no contraction, "
+                     "bit-exact with the oracle), so its own arithmetic ceiling is half the FMA rate")}
+
+
 def arm_summary(r, world):
     """Throughput of a comparison arm from its timed (production) steps."""
     st = r["stats"]
@@ -917,6 +946,7 @@ def main():
                         prof_steps=5)
             compare[form] = arm_summary(r, world)
             compare[form]["pcg_ms_per_step"] = round(r["prof"]["pcg"][1] / r["prof"]["pcg"][0], 4)
+            compare[form]["roofline_step_fused"] = fp64_walk_roofline(r)
             r["ctx"].close()
             del r
         for form, c in compare.items():

@@ -497,6 +497,16 @@ int pic_profile_read(pic_ctx ctx, pic_profile_report *out); /* synchronises */
 /* Wait for all queued work; returns the first device-side error, if any. */
 int pic_sync(pic_ctx ctx);
 
+/* Measurement probe, not part of the cycle: the FP64 fused-multiply-add rate
+ * of the current device (2 flops per FMA), measured with a kernel of
+ * independent FMA chains on `stream` (a cudaStream_t, nullable: the default
+ * stream) over `iters` (>= 1) iterations per chain, timed with CUDA events
+ * after one untimed launch; the FP64 form's roofline (the FP64 walk, Sec.
+ * II.B.2) is set against it.  *tflops: HOST, TFLOP/s.  Allocates and frees
+ * its own scratch and synchronises `stream`; PIC_ERR_ARG for iters < 1 or a
+ * null tflops, PIC_ERR_CUDA on a CUDA error. */
+int pic_measure_fp64_rate(void *stream, int32_t iters, double *tflops);
+
 /*
  * pic_pcg_solve_static: Jacobi-preconditioned CG on a caller-supplied sparse
  * symmetric positive definite system A x = b that allocates no device memory

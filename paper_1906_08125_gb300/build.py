@@ -31,6 +31,9 @@ UNITS = {
     "collide.cu": ["--fmad=false"],
     "mg.cu": [],
 }
+# measurement probes, compiled into the same library (not part of the cycle)
+PROBES = os.path.join(HERE, "probes")
+PROBE_UNITS = {"fp64_rate.cu": []}
 
 
 def nvcc() -> str:
@@ -42,6 +45,7 @@ def nvcc() -> str:
 
 def _sources():
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    deps += [os.path.join(PROBES, f) for f in os.listdir(PROBES)]
     deps.append(os.path.join(INCLUDE, "picfem.h"))
     deps.append(os.path.abspath(__file__))
     return deps
@@ -61,9 +65,12 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     cc = nvcc()
     procs = []
     objs = []
-    for unit, flags in UNITS.items():
+    units = [(os.path.join(CSRC, u), f) for u, f in UNITS.items()]
+    units += [(os.path.join(PROBES, u), f) for u, f in PROBE_UNITS.items()]
+    for path, flags in units:
+        unit = os.path.basename(path)
         obj = os.path.join(OUT_DIR, unit.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *flags, *(extra or []), "-c", os.path.join(CSRC, unit), "-o", obj]
+        cmd = [cc, *ARCH, *COMMON, *flags, *(extra or []), "-c", path, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((unit, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

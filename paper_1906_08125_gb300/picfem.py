@@ -29,7 +29,7 @@ EXPORTED = ["pic_create", "pic_destroy", "pic_last_error", "pic_version", "mesh_
             "pic_get_potential_async", "pic_set_potential", "pic_get_field", "pic_get_charge", "pic_num_particles",
             "pic_get_particles", "pic_set_particles", "pic_set_work_function",
             "pic_launch_count", "pic_profile_enable", "pic_profile_read", "pic_sync",
-            "pic_pcg_solve_static"]
+            "pic_pcg_solve_static", "pic_measure_fp64_rate"]
 
 
 class Params(C.Structure):
@@ -142,6 +142,7 @@ def load(build_if_missing: bool = True):
         "pic_profile_read": [P, C.POINTER(ProfileReport)],
         "pic_sync": [P],
         "pic_pcg_solve_static": [I32, P, P, P, P, P, D, I32, C.POINTER(I32), C.POINTER(D), P],
+        "pic_measure_fp64_rate": [P, I32, C.POINTER(D)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -149,6 +150,19 @@ def load(build_if_missing: bool = True):
         fn.restype = C.c_char_p if name in ("pic_last_error", "pic_version") else C.c_int
     _lib = L
     return L
+
+
+def measure_fp64_rate(iters: int = 1 << 14, stream=None) -> float:
+    """The FP64 FMA rate of the current device in TFLOP/s
+    (pic_measure_fp64_rate), on the given torch stream (the current one)."""
+    import torch
+    L = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double(0.0)
+    rc = L.pic_measure_fp64_rate(C.c_void_p(s.cuda_stream), int(iters), C.byref(out))
+    if rc != 0:
+        raise PicError(rc, f"pic_measure_fp64_rate failed ({rc})")
+    return out.value
 
 
 def _ptr(x):
