@@ -104,6 +104,39 @@ def test_particle_kernel_onchip_roofline(monkeypatch):
     assert o["frac_ncu"] == 66.0 and roof["solver"]["kernel"] == "pcg"
 
 
+def test_fp64_walk_roofline_against_the_measured_rate(monkeypatch):
+    """The FP64 arms' fused-kernel roofline: FP64 flops counted from the step
+    statistics (per crossing and per SP) over the kernel's event time, against
+    the rate pic_measure_fp64_rate returns."""
+    import types
+    fake = types.SimpleNamespace(measure_fp64_rate=lambda: 1.25)
+    monkeypatch.setitem(__import__("sys").modules, "paper_1906_08125_gb300.picfem", fake)
+    import paper_1906_08125_gb300
+    monkeypatch.setattr(paper_1906_08125_gb300, "picfem", fake, raising=False)
+    monkeypatch.setattr(bench, "_FP64_RATE", [])
+    st = stats(2)
+    r = dict(prof={"step_fused": (2, 4.0)}, prof_stats=st, prof_prev_alive=np.array([100, 100]))
+    roof = bench.fp64_walk_roofline(r)
+    flops = sum(bench.FP64_FLOPS_PER_CROSSING * 1000 + bench.FP64_FLOPS_PER_SP * (100 + 5)
+                for _ in range(2))
+    assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s" and roof["peak"] == 1.25
+    assert roof["achieved"] == pytest.approx(flops / 4.0e-3 / 1e12, abs=1e-4)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / 1.25, abs=1e-4)
+
+
+def test_preconditioner_products_and_names():
+    """Fine-level products per CG iteration: k for the Chebyshev polynomial
+    of degree k, 2 k0 + 1 for the V-cycle with fine smoothing degree k0."""
+    assert bench.precond_products({"pcg_cheb_local": 4, "pcg_mg_degree0": 3}, {}) == 7
+    assert bench.precond_products({"pcg_cheb_local": 4, "pcg_mg_degree0": 1}, {}) == 3
+    assert bench.precond_products({"pcg_cheb_local": 3}, {"pcg_cheb_degree": 6}) == 6
+    info = {"mg_levels": 3, "mg_coarse_rows": 980}
+    assert "V-cycle, 3 levels" in bench.precond_name(
+        {"pcg_cheb_local": 4, "pcg_mg_degree0": 1, "pcg_mg_degree1": 3}, info)
+    assert bench.precond_name({"pcg_cheb_local": 0, "pcg_cheb_degree": 0}, info) == "Jacobi"
+    assert "coarse correction" in bench.precond_name({"pcg_cheb_local": 3, "pcg_cheb_degree": 6}, info)
+
+
 def test_ncu_traffic_only_with_the_measured_source(monkeypatch):
     d = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
     e = d["pcg"]
