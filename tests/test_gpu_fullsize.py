@@ -172,7 +172,7 @@ def test_teacher_forced_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
     assert worst <= 1e-6
 
 
-SENS_STEPS = int(os.environ.get("PIC_SENS_TIP_STEPS", "8"))
+SENS_STEPS = int(os.environ.get("PIC_SENS_TIP_STEPS", "20"))
 
 
 def test_free_running_bench_fp32ir(picfem, oracle_mod, tip1m, oracle_state):
